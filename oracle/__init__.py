@@ -1,0 +1,15 @@
+"""FP64 CPU oracle for the steady gray-RTE source iteration and GSIS.
+
+TEST INFRASTRUCTURE ONLY: only tests/, __graft_entry__.smoke() and bench.py's
+CPU-baseline leg may import or run anything here.  The oracle shares no code
+with the CUDA library and neither imports the other.
+
+Parity pins (see tests/test_oracle_pins.py): every function here is checked
+against closed forms, invariants or brute force on tiny inputs; none is
+"parity unpinned".
+"""
+from .gsis import (  # noqa: F401
+    angular_source, transport_sweep, alsm_gradient, high_order_terms, geometry, pseudo_time_shift,
+    face_lists, gamma_coefficient, boundary_beta, synthetic_matrix, synthetic_rhs,
+    SyntheticSolver, err_w, si_solve, gsis_solve, gsis_iteration, si_iteration,
+)

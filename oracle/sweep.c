@@ -1,0 +1,158 @@
+/*
+ * ORACLE -- test infrastructure only.  Only tests/, __graft_entry__.smoke()
+ * and bench.py's CPU-baseline leg may load this code; the product path never
+ * does.  It shares no source with the CUDA library.
+ *
+ * One kinetic step of source iteration for the steady gray RTE: for every
+ * discrete ordinate, the cell-centred finite-volume transport equation with
+ * first-order upwind face values is solved exactly by visiting cells in
+ * upwind order, then the angular moments are summed in direction-index order.
+ *
+ *   Eq. (RTE_d) with 1/(c dt) = 0 (steady) and the right-hand side written as
+ *   sigma_t I - S, S = (sigma_s rho^m + q)/(4 pi)  (Eq. (RTE_SI), Sec. 2.2):
+ *       sigma_t I_i + (1/V_i) sum_j I_ij (Omega . A_ij) = S_i
+ *   Eq. (Iij) with psi = 0: I_ij = I_i if Omega.n_ij >= 0, else I_j
+ *   (or the boundary inflow, Eq. (micro_bc) with alpha_w = 0).
+ *   Moments, Eqs. (def_rho), (def_F), (RTE_M0): rho = sum w I,
+ *   F = sum w Omega I, P = sum w Omega Omega I (Sec. 4.1 quadrature sum).
+ *   Boundary kinetic flux F_iw . n = sum_k w_k (Omega_k . n) I_iw,k
+ *   (Sec. 4.4, F_iw^init).
+ *
+ * With a pseudo-time shift (Sec. 4.3) the step is the paper's delta form:
+ * the UW1 residual at the stored I^m (Eq. (RTE_d_res)), then the lower-
+ * triangular increment system with the shifted diagonal (Eqs. (RTE_d_mtx),
+ * (elem_main_shifted)) solved in upwind order, and I^{m+1/2} = I^m + dI.
+ *
+ * Plain FP64, plain loops, no blocking.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* boundary face numbering: W j, E ny+j, S 2ny+i, N 2ny+nx+i */
+
+/* neighbour across face f (0 W, 1 E, 2 S, 3 N) of cell (i,j), or -1 */
+static int neighbour(int nx, int ny, int i, int j, int f)
+{
+    const int c = i + nx * j;
+    if (f == 0) return i > 0 ? c - 1 : -1;
+    if (f == 1) return i < nx - 1 ? c + 1 : -1;
+    if (f == 2) return j > 0 ? c - nx : -1;
+    return j < ny - 1 ? c + nx : -1;
+}
+
+/* boundary face number across face f of cell (i,j) (only on the boundary) */
+static int bface(int nx, int ny, int i, int j, int f)
+{
+    if (f == 0) return j;
+    if (f == 1) return ny + j;
+    if (f == 2) return 2 * ny + i;
+    return 2 * ny + nx + i;
+}
+
+/* upwind value across face f: the neighbour's intensity, or the inflow
+   (Eq. (micro_bc) with alpha_w = 0; vacuum when inflow is NULL) */
+static double upwind(const double* Ik, const double* inflow, int nx, int ny, int K, int k,
+                     int i, int j, int f)
+{
+    const int nb = neighbour(nx, ny, i, j, f);
+    if (nb >= 0) return Ik[nb];
+    return inflow ? inflow[(size_t)bface(nx, ny, i, j, f) * K + k] : 0.0;
+}
+
+int oracle_sweep(int nx, int ny, const double* dx, const double* dy, int K,
+                 const double* mu, const double* eta, const double* w,
+                 const double* sigma_t, const double* S, const double* inflow,
+                 const double* shift, const double* I_prev,
+                 double* I_out, double* rho, double* Fx, double* Fy,
+                 double* Pxx, double* Pxy, double* Pyy, double* fb)
+{
+    const int N = nx * ny;
+    const int nbf = 2 * (nx + ny);
+    double* I = (double*)malloc(sizeof(double) * (size_t)N);
+    double* dI = (double*)malloc(sizeof(double) * (size_t)N);
+    if (!I || !dI) { free(I); free(dI); return -1; }
+    for (int c = 0; c < N; ++c) {
+        rho[c] = 0.0; Fx[c] = 0.0; Fy[c] = 0.0;
+        Pxx[c] = 0.0; Pxy[c] = 0.0; Pyy[c] = 0.0;
+    }
+    for (int f = 0; f < nbf; ++f) fb[f] = 0.0;
+
+    for (int k = 0; k < K; ++k) {
+        const double m = mu[k], e = eta[k];
+        /* upwind visiting order: a cell is visited after the neighbours whose
+           shared face has Omega.n < 0 seen from this cell */
+        const int i0 = (m >= 0.0) ? 0 : nx - 1, di = (m >= 0.0) ? 1 : -1;
+        const int j0 = (e >= 0.0) ? 0 : ny - 1, dj = (e >= 0.0) ? 1 : -1;
+        for (int jj = 0; jj < ny; ++jj) {
+            const int j = j0 + dj * jj;
+            for (int ii = 0; ii < nx; ++ii) {
+                const int i = i0 + di * ii;
+                const int c = i + nx * j;
+                const double V = dx[i] * dy[j];
+                /* the four faces: outward normal and area */
+                const double An[4] = {dy[j], dy[j], dx[i], dx[i]};   /* W E S N */
+                const double on[4] = {-m, m, -e, e};                 /* Omega . n */
+                if (!shift) {
+                    /* exact solve of the cell equation given the upwind values */
+                    double diag = sigma_t[c];
+                    double rhs = S[c];
+                    for (int f = 0; f < 4; ++f) {
+                        const double oa = on[f] * An[f];   /* Omega . A_ij */
+                        if (on[f] >= 0.0) {
+                            diag += oa / V;                 /* outflow: I_ij = I_i */
+                        } else {
+                            rhs -= oa / V * upwind(I, inflow, nx, ny, K, k, i, j, f);
+                        }
+                    }
+                    I[c] = rhs / diag;
+                } else {
+                    /* delta form with the pseudo-time shift (Eqs. (RTE_d_increment),
+                       (delta_Iij), (RTE_d_res), (RTE_d_mtx), (elem_main_shifted)):
+                       residual of the UW1 equation at I^m, then
+                       d_ii dI_i + sum_{inflow j} d_ij dI_j = r_i, I^{m+1/2} = I^m + dI */
+                    const double* Im = I_prev + (size_t)k * N;
+                    double r = S[c] - sigma_t[c] * Im[c];
+                    double dii = shift[c] + sigma_t[c];
+                    double lower = 0.0;
+                    for (int f = 0; f < 4; ++f) {
+                        const double oa = on[f] * An[f];
+                        if (on[f] >= 0.0) {
+                            r -= oa / V * Im[c];
+                            dii += oa / V;
+                        } else {
+                            r -= oa / V * upwind(Im, inflow, nx, ny, K, k, i, j, f);
+                            /* d_ij dI_j with dI on an inflow boundary face = 0 */
+                            const int nb = neighbour(nx, ny, i, j, f);
+                            if (nb >= 0) lower += oa / V * dI[nb];
+                        }
+                    }
+                    dI[c] = (r - lower) / dii;
+                    I[c] = Im[c] + dI[c];
+                }
+            }
+        }
+        for (int c = 0; c < N; ++c) {
+            rho[c] += w[k] * I[c];
+            Fx[c] += w[k] * m * I[c];
+            Fy[c] += w[k] * e * I[c];
+            Pxx[c] += w[k] * m * m * I[c];
+            Pxy[c] += w[k] * m * e * I[c];
+            Pyy[c] += w[k] * e * e * I[c];
+        }
+        /* boundary faces: outgoing uses the boundary cell, incoming the inflow */
+        for (int f = 0; f < nbf; ++f) {
+            int c; double on;
+            if (f < ny) { c = nx * f; on = -m; }
+            else if (f < 2 * ny) { c = (nx - 1) + nx * (f - ny); on = m; }
+            else if (f < 2 * ny + nx) { c = f - 2 * ny; on = -e; }
+            else { c = (f - 2 * ny - nx) + nx * (ny - 1); on = e; }
+            const double Iface = (on >= 0.0) ? I[c] : (inflow ? inflow[(size_t)f * K + k] : 0.0);
+            fb[f] += w[k] * on * Iface;
+        }
+        if (I_out) memcpy(I_out + (size_t)k * N, I, sizeof(double) * (size_t)N);
+    }
+    free(I);
+    free(dI);
+    return 0;
+}
