@@ -1,0 +1,321 @@
+"""Benchmark: time-to-converge and cell-direction update rate of GSIS on one
+GB300, the 256x256 S12 thick-medium / thin-channel workload, FP64.
+
+One step = one complete GSIS solve (transport sweeps of every ordinate with
+fused-order angular moments, adaptive least-squares gradients, high-order
+terms, FP64 synthetic solve, Err) from rho = 0 to Err(rho) < 1e-8, inputs
+resident in HBM.  value = (iterations x cells x directions) / time, summed
+over steps and ranks.  L2 is flushed (512 MiB write) before every step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the reference of this build) on a
+bounded sample of the same workload on the host cores.  Under torchrun every
+rank runs an independent replica (no collective in the data path); rank 0
+prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "cell-direction updates/s and time-to-converge (GSIS vs SI) on 1 GB300; HBM roofline %"
+UNIT = "cell-direction updates/s"
+TOL = 1e-8
+BETA = 10.0   # local pseudo-time control (Sec. 4.3) the 2000/0.2 opacity jump needs
+
+
+def _workload():
+    p = W.config_channel()
+    return p, dict(workload="channel_256x256_S12_seed2", nx=p.nx, ny=p.ny, K=p.K, scheme="gsis",
+                   beta=BETA, tol=TOL, precision="fp64",
+                   l2="flushed before each step (512 MiB write); per-solve working set ~105 MB")
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _clock_sampler():
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+    f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                 "-lms", "200"], stdout=f, stderr=subprocess.DEVNULL)
+    except OSError:
+        proc = None
+    return proc, f
+
+
+def _clock_summary(proc, f, gpu_index):
+    if proc is None:
+        return None
+    proc.terminate()
+    try:
+        proc.wait(5)
+    except subprocess.TimeoutExpired:
+        proc.kill()
+    f.flush()
+    f.seek(0)
+    sm, smax, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in f.read().splitlines():
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 9 or parts[0] != str(gpu_index):
+            continue
+        try:
+            sm.append(float(parts[1]))
+            smax = float(parts[2])
+        except ValueError:
+            continue
+        for n, v in zip(names, parts[5:9]):
+            if v.lower() == "active":
+                reasons.add(n)
+    os.unlink(f.name)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def cpu_baseline_sample(p, iters=2):
+    """The FP64 oracle as it stands, single thread, on a bounded sample:
+    `iters` GSIS iterations of the same workload (first iteration includes
+    the oracle's one-off sparse LU of the synthetic operator)."""
+    import oracle
+    t0 = time.perf_counter()
+    oracle.gsis_solve(p, fixed_iters=iters, beta=BETA)
+    dt = time.perf_counter() - t0
+    return iters * p.N * p.K / dt, dt
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    p, cfg = _workload()
+    import oracle  # noqa: F401  (builds the C sweep on first use)
+    for _ in range(args.warmup):
+        cpu_baseline_sample(p, 1)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        v, dt = cpu_baseline_sample(p, 1)
+        vals.append(v)
+        secs.append(dt)
+    value = args.steps * p.N * p.K / sum(secs)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "one oracle GSIS iteration of the 256x256 S12 channel workload per step "
+                                       "(sparse LU of the synthetic operator included)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2507_03975_gb300 import gsis
+
+    ws, rank, local = _dist()
+    if args.gpus > 1 or ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    p, cfg = _workload()
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
+    sa, ss, q, inflow = t(p.sigma_a), t(p.sigma_s), t(p.q), t(p.inflow.reshape(-1))
+    opt = gsis.default_options(scheme=gsis.SCHEME_GSIS, precision=gsis.FP64, tol=TOL, beta=BETA,
+                               max_iter=5000, check_every=16)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device=dev)   # 512 MiB > L2
+    r = gsis.solve(p.dx, p.dy, p.mu, p.eta, p.w, sa, ss, q, inflow, opt)
+    workspace = r["workspace"]
+    for _ in range(max(0, args.warmup - 1)):
+        gsis.solve(p.dx, p.dy, p.mu, p.eta, p.w, sa, ss, q, inflow, opt, workspace=workspace)
+    torch.cuda.synchronize()
+
+    # ---- timed: K complete solves, inputs resident in HBM
+    gsis.profile_enable(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    proc, cf = _clock_sampler() if rank == 0 else (None, None)
+    step_ms, iters = [], []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = gsis.solve(p.dx, p.dy, p.mu, p.eta, p.w, sa, ss, q, inflow, opt, workspace=workspace)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        iters.append(r["iters"])
+        if r["status"] != gsis.GSIS_OK:
+            raise RuntimeError(f"solve did not converge: status {r['status']}, Err {r['err']}")
+    torch.cuda.synchronize()
+    prof = gsis.profile_read()
+    gsis.profile_enable(False)
+    clocks = _clock_summary(proc, cf, torch.cuda.current_device()) if rank == 0 else None
+    total_ms = sum(step_ms)
+    if dist:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+        dist.barrier()
+    n_ranks = max(ws, 1)
+    units = sum(iters) * p.N * p.K * n_ranks
+    value = units / (total_ms * 1e-3)
+
+    # ---- end to end through the C ABI: pinned host inputs in, result out
+    h_in = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).pin_memory()
+            for a in (p.sigma_a, p.sigma_s, p.q, p.inflow.reshape(-1))]
+    h_rho = torch.empty(p.N, dtype=torch.float64).pin_memory()
+    h_F = torch.empty(2 * p.N, dtype=torch.float64).pin_memory()
+    e2e_ms, e2e_iters = [], []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.fill_(2.0)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        d_in = [h.to(dev, non_blocking=True) for h in h_in]
+        r = gsis.solve(p.dx, p.dy, p.mu, p.eta, p.w, *d_in, opt, workspace=workspace, want_P=False)
+        h_rho.copy_(r["rho"], non_blocking=True)
+        h_F.copy_(r["F"], non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+        e2e_iters.append(r["iters"])
+    h2d = sum(h.numel() * 8 for h in h_in)
+    d2h = (h_rho.numel() + h_F.numel()) * 8
+    e2e_value = sum(e2e_iters) * p.N * p.K / (sum(e2e_ms) * 1e-3) * n_ranks
+
+    # ---- time-to-converge of plain source iteration on the same problem (once)
+    si = None
+    if not args.no_si:
+        opt_si = gsis.default_options(scheme=gsis.SCHEME_SI, precision=gsis.FP64, tol=TOL, max_iter=100000,
+                                      check_every=256)
+        gsis.profile_enable(False)
+        flush.fill_(3.0)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rs = gsis.solve(p.dx, p.dy, p.mu, p.eta, p.w, sa, ss, q, inflow, opt_si, workspace=None)
+        e1.record(stream)
+        e1.synchronize()
+        si = {"s": e0.elapsed_time(e1) * 1e-3, "iters": rs["iters"], "status": rs["status"],
+              "updates_per_s": rs["iters"] * p.N * p.K / (e0.elapsed_time(e1) * 1e-3)}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    # ---- roofline of the dominant kernel class
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    shares = {k: v["total_ms"] for k, v in prof.items()}
+    tot = sum(shares.values()) or 1.0
+    dom = max(shares, key=shares.get)
+    per_iter_upd = p.N * p.K
+    # algorithmic work per launch group ("Kernels and their rooflines")
+    alg = {
+        "sweep": ("alu", 7.0 * per_iter_upd, 1250.0, "GFLOP/s"),     # 3 FMA + 1 MUL per update (pseudo-time on)
+        "moments": ("alu", 6.0 * per_iter_upd, 1250.0, "GFLOP/s"),   # 3 FMA per update (rho, Fx, Fy)
+        "synth": ("hbm", None, hbm, "GB/s"),
+        "hot_rhs": ("hbm", 15 * 8.0 * p.N, hbm, "GB/s"),
+        "update": ("hbm", 6 * 8.0 * p.N, hbm, "GB/s"),
+        "setup": ("hbm", None, hbm, "GB/s"),
+    }
+    bound, work, peak, unit = alg[dom]
+    groups = max(prof[dom]["timed"], 1)
+    avg_ms = prof[dom]["total_ms"] / groups
+    if dom == "synth":
+        # 10 doubles per cell per CG iteration, summed over the iterations each launch did
+        work = None
+    achieved = (work / (avg_ms * 1e-3) / 1e9) if work else None
+    roof = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak,
+            "unit": unit if bound != "alu" else "GFLOP/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "avg_launch_ms": avg_ms, "launch_groups": groups,
+            "share": {k: v / tot for k, v in shares.items()},
+            "peak_source": "measured hbm_gbs (MEASURED_PEAKS.json)" if bound == "hbm"
+            else "nominal FP64 1250 GFLOP/s (GB300 FP64 rate)"}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        v, dt = cpu_baseline_sample(p, 2)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"2 oracle GSIS iterations of the same workload ({dt:.1f} s, includes the oracle's "
+                         "one-off sparse LU)"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": n_ranks, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+            "time_to_converge": {"gsis": {"s": total_ms / args.steps * 1e-3, "iters": iters[0]}, "si": si},
+            "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(sum(v["kernels"] for v in prof.values())),
+            "kernel_ms": {k: v["total_ms"] for k, v in prof.items()},
+            "clocks": clocks}
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-si", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

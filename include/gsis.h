@@ -1,0 +1,225 @@
+/*
+ * gsis.h -- C ABI of libgsis: the general synthetic iterative scheme (GSIS)
+ * and plain source iteration (SI) for the steady gray radiative transfer
+ * equation on one GPU (sm_103a).
+ *
+ * Problem (Sec. 2.1, Eq. (RTE_g) without time derivative and without the
+ * material equation; Sec. 2.2, Eq. (RTE_SI) with hatted = plain cross sections):
+ *
+ *     Omega . grad I + sigma_t I = (sigma_s rho + q) / (4 pi),
+ *     rho = integral of I over the sphere,   sigma_t = sigma_a + sigma_s,
+ *
+ * on a 2D Cartesian mesh, discretised by the cell-centred finite-volume
+ * discrete-ordinate scheme of Sec. 4.1 (Eqs. (RTE_d), (Iij) with first-order
+ * upwind faces), with prescribed intensity entering through the walls and
+ * no reflection (Sec. 4.4, Eq. (micro_bc), alpha_w = 0).
+ *
+ * Conventions shared by every call:
+ *   - cells are row-major: cell c = i + nx*j, i along x (0 <= i < nx);
+ *   - boundary faces: W faces f = j, E faces f = ny + j, S faces
+ *     f = 2*ny + i, N faces f = 2*ny + nx + i (n_bface = 2*(nx+ny));
+ *   - q is the angle-integrated volumetric source (angular source q/4pi);
+ *   - all floating point arguments are float64 (double);
+ *   - "device" pointers are CUDA device (or managed) memory on the current
+ *     device; "host" pointers are ordinary host memory;
+ *   - every call that takes a stream is stream-ordered on that stream
+ *     (cudaStream_t passed as void*, NULL = legacy default stream) and
+ *     returns after its device work is enqueued, except where a call states
+ *     that it synchronises;
+ *   - the library never allocates device memory: scratch comes from the
+ *     caller's workspace, sized by gsis_workspace_bytes();
+ *   - inputs are never modified; outputs are written only on success or on
+ *     GSIS_ERR_MAXITER / GSIS_ERR_STALLED (best iterate so far);
+ *   - errors: a negative gsis_status is returned, nothing is thrown and the
+ *     process never exits; gsis_last_error() gives a per-thread message.
+ */
+#ifndef GSIS_H
+#define GSIS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GSIS_OK = 0,
+    GSIS_ERR_ARG = -1,             /* invalid argument (sizes, NULL, sigma < 0, sum w != 4pi, ...) */
+    GSIS_ERR_CUDA = -2,            /* a CUDA runtime call failed (message in gsis_last_error) */
+    GSIS_ERR_MAXITER = -3,         /* max_iter reached without Err < tol (outputs = last iterate) */
+    GSIS_ERR_DIVERGED = -4,        /* Err became NaN/Inf or exceeded 1e6 */
+    GSIS_ERR_STALLED = -5,         /* Err did not decrease for `stall_window` checks */
+    GSIS_ERR_DEVICE_TIMEOUT = -6,  /* a bounded device-side wait gave up; results invalid */
+    GSIS_ERR_WORKSPACE = -7        /* workspace NULL, too small or misaligned (256 B) */
+} gsis_status;
+
+typedef enum { GSIS_SCHEME_SI = 0, GSIS_SCHEME_GSIS = 1 } gsis_scheme;
+
+/* GSIS_FP64: everything in float64.
+ * GSIS_FP32_SWEEP: the transport sweep and its angular-moment sums run in
+ * float32 (float32 accumulators); the high-order terms, the synthetic solve,
+ * Err and all residual norms stay float64. */
+typedef enum { GSIS_FP64 = 0, GSIS_FP32_SWEEP = 1 } gsis_precision;
+
+/* Mesh: nx*ny cells; dx[nx], dy[ny] are HOST arrays of positive widths,
+ * copied during the call. */
+typedef struct {
+    int nx, ny;
+    const double* dx;
+    const double* dy;
+} gsis_mesh;
+
+/* Discrete ordinates (Sec. 4.1): K directions with x/y cosines mu[k],
+ * eta[k] (mu^2 + eta^2 <= 1) and weights w[k] > 0 with sum w = 4 pi
+ * (checked to 1e-10 relative).  HOST arrays, copied during the call. */
+typedef struct {
+    int K;
+    const double* mu;
+    const double* eta;
+    const double* w;
+} gsis_quadrature;
+
+typedef struct {
+    int scheme;            /* gsis_scheme */
+    int precision;         /* gsis_precision */
+    double tol;            /* stop when Err(rho) < tol (Eq. (Err_W)); default 1e-8 */
+    int max_iter;          /* iteration cap; default 100000 */
+    int fixed_iters;       /* > 0: run exactly this many iterations, ignore tol */
+    double synth_rtol;     /* synthetic solve: stop at ||b - D rho|| <= synth_rtol ||b||; default 1e-12 */
+    int synth_max_iter;    /* synthetic solve iteration cap; default 20000 */
+    double cfl_p;          /* global pseudo-time control CFL_p (Eq. (cfl_pse)); <= 0: off (default) */
+    double beta;           /* local pseudo-time control beta (Eq. (tau_pse)); <= 0: off (default) */
+    int check_every;       /* iterations between host reads of the device status; default 16 */
+    int stall_window;      /* GSIS_ERR_STALLED after this many checks without a new minimum of Err; 0 = off */
+    double wait_limit_s;   /* bound of every device-side wait, seconds; default 2.0 */
+} gsis_options;
+
+/* Fills *opt with the defaults listed above (scheme GSIS, precision FP64). */
+void gsis_default_options(gsis_options* opt);
+
+/*
+ * Level-symmetric S_order discrete-ordinate set for 2D (Sec. 4.1 names S_n
+ * sets; the points follow mu_i^2 = mu_1^2 + (i-1) 2(1 - 3 mu_1^2)/(order-2),
+ * weights from the even moment conditions; the z > 0 hemisphere is kept with
+ * doubled weights).  order in {4,6,...,16}; K = order(order+2)/2.
+ * mu, eta, w: HOST arrays of capacity >= K, or all NULL to query *K only.
+ * Directions are grouped by quadrant (+,+), (-,+), (+,-), (-,-).
+ * Returns GSIS_OK or GSIS_ERR_ARG.
+ */
+int gsis_quadrature_level_symmetric(int order, double* mu, double* eta, double* w, int* K);
+
+/* Bytes of device workspace needed by gsis_solve / gsis_transport_sweep /
+ * gsis_synthetic_step for this mesh, quadrature and options (the maximum
+ * over the three).  Returns GSIS_OK or GSIS_ERR_ARG. */
+int gsis_workspace_bytes(const gsis_mesh* mesh, const gsis_quadrature* quad,
+                         const gsis_options* opt, size_t* bytes);
+
+/*
+ * Solve the steady problem by SI (Sec. 2.2, Eq. (SI_update)) or GSIS
+ * (Sec. 3.1, Eqs. (GSIS_HoT), (GSIS_M0), (GSIS_update), discretised as in
+ * Secs. 4.2-4.4 and 5), starting from rho^0 = 0, until Err(rho) < tol.
+ *
+ * sigma_a, sigma_s, q: device [N] (N = nx*ny), sigma_a >= 0, sigma_s >= 0,
+ *   sigma_a + sigma_s > 0.
+ * inflow: device [n_bface * K] (face-major: inflow[f*K + k]) intensity
+ *   entering through boundary face f in direction k (read only where
+ *   Omega_k . n_f < 0), or NULL for vacuum walls.
+ * rho: device [N] out, energy density rho^{m+1}.
+ * F: device [2N] out (F_x block then F_y block), first moment of I^{m+1}.
+ * P: device [3N] out (P_xx, P_xy, P_yy blocks), second moment of I^{m+1}
+ *   (for GSIS the isotropic correction of Eq. (GSIS_update) adds
+ *   (rho^{m+1} - rho^{m+1/2})/3 to P_xx and P_yy), or NULL.
+ * history: HOST [max_iter] out, Err after each iteration, or NULL.
+ * iters_out, err_out: HOST out (may be NULL): iterations done, final Err.
+ * workspace: device, >= gsis_workspace_bytes(), 256-byte aligned, owned by
+ *   the caller and not used concurrently by another call.
+ * This call SYNCHRONISES the stream (it reads the convergence status back
+ * every opt->check_every iterations).
+ * Returns GSIS_OK, GSIS_ERR_MAXITER, GSIS_ERR_DIVERGED, GSIS_ERR_STALLED,
+ * GSIS_ERR_DEVICE_TIMEOUT, GSIS_ERR_ARG, GSIS_ERR_WORKSPACE or GSIS_ERR_CUDA.
+ */
+int gsis_solve(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis_options* opt,
+               const double* sigma_a, const double* sigma_s, const double* q,
+               const double* inflow, double* rho, double* F, double* P,
+               double* history, int* iters_out, double* err_out,
+               void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * One kinetic step (Sec. 4.1; Eq. (RTE_SI) with source S = (sigma_s rho_in + q)/4pi):
+ * the exact first-order-upwind sweep of every ordinate and its angular
+ * moments (Eqs. (def_rho), (def_F), (RTE_M0)) plus the kinetic net flux
+ * F_iw . n of every boundary face (Sec. 4.4, F_iw^init).
+ * rho_in: device [N].  rho_half: device [N] out.  F_half: device [2N] out.
+ * P_half: device [3N] out or NULL.  bflux: device [n_bface] out or NULL
+ * (outward normal component, sum_k w_k (Omega_k . n) I_face,k).
+ * opt: only opt->precision and opt->wait_limit_s are read (no pseudo-time).
+ * Stream-ordered; does not synchronise.
+ */
+int gsis_transport_sweep(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis_options* opt,
+                         const double* sigma_a, const double* sigma_s, const double* q,
+                         const double* inflow, const double* rho_in,
+                         double* rho_half, double* F_half, double* P_half, double* bflux,
+                         void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * One synthetic step of GSIS (Sec. 3.1 and 4.2): adaptive least-squares
+ * gradient of rho_half (Sec. 5.2, Eqs. (shifted_j), (new_vector), (LSF_mdf)),
+ * high-order terms HoT = F_half + grad(rho_half)/(3 sigma_t) (Eq. (GSIS_HoT)),
+ * right-hand side with face-averaged HoT (Eq. (Fij_d)) and the boundary flux
+ * of Eqs. (macro_bc_delta_flux), (macro_bc_delta_flux2), and the solve of
+ * the finite-volume synthetic equation (Eqs. (MSE_d1), (Gamma_ij_def),
+ * (elem_mtx_M), (Gamma_ij_com2)) for rho_out, starting from rho_guess
+ * (device [N], may alias nothing else, NULL = start from rho_half).
+ * rho_half: device [N], F_half: device [2N], bflux: device [n_bface] in.
+ * rho_out: device [N] out.  hot: device [2N] out or NULL.  rhs: device [N]
+ * out or NULL (b of D rho = b, multiplied by the cell volume).
+ * synth_iters_out: HOST out or NULL.  SYNCHRONISES the stream.
+ */
+int gsis_synthetic_step(const gsis_mesh* mesh, const gsis_options* opt,
+                        const double* sigma_a, const double* sigma_s, const double* q,
+                        const double* rho_half, const double* F_half, const double* bflux,
+                        const double* rho_guess, double* rho_out, double* hot, double* rhs,
+                        int* synth_iters_out,
+                        void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Instrumentation (not part of the method): every call counts the kernels it
+ * launches per class; after gsis_profile_enable(1) each class launch is also
+ * bracketed by CUDA events on the caller's stream and its device time is
+ * accumulated when the call synchronises.  Host-global, not thread-safe
+ * against concurrent calls.
+ */
+typedef enum {
+    GSIS_KCLASS_SETUP = 0,   /* per-call set-up: coefficients, operator, 1/d table, state init */
+    GSIS_KCLASS_SWEEP = 1,   /* the transport sweep */
+    GSIS_KCLASS_MOMENTS = 2, /* angular moments + boundary fluxes (2 kernels per launch group) */
+    GSIS_KCLASS_HOT_RHS = 3, /* ALSM gradient, HoT, synthetic right-hand side (2 kernels) */
+    GSIS_KCLASS_SYNTH = 4,   /* synthetic solve */
+    GSIS_KCLASS_UPDATE = 5,  /* Err, convergence decision, next source */
+    GSIS_KCLASS_COUNT = 6
+} gsis_kernel_class;
+
+typedef struct {
+    long long kernels;   /* kernels launched in this class */
+    long long groups;    /* launch groups (class calls) */
+    long long timed;     /* groups with a device time */
+    double total_ms;     /* summed device time of the timed groups */
+} gsis_kernel_stats;
+
+/* enable != 0: time later launches; always resets the counters. */
+int gsis_profile_enable(int enable);
+
+/* Copies min(n, GSIS_KCLASS_COUNT) entries (indexed by gsis_kernel_class). */
+int gsis_profile_read(gsis_kernel_stats* out, int n);
+
+/* Static description of a status code (never NULL). */
+const char* gsis_status_string(int status);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char* gsis_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSIS_H */

@@ -1,0 +1,636 @@
+// Kinetic step of SI / GSIS: the first-order-upwind discrete-ordinate sweep
+// (Sec. 4.1, Eqs. (RTE_d), (Iij) with psi = 0, Eq. (RTE_SI) steady) and its
+// angular moments (Eqs. (def_rho), (def_F), (RTE_M0)), plus the per-problem
+// set-up of the coefficients every iteration reuses.
+//
+// Sweep layout.  Work unit = (direction s, band of 32 rows).  A warp owns one
+// unit: lane l owns row 32*band + l (counted from the upwind wall) and walks
+// the row from the upwind wall, one cell per step, lane l lagging lane l-1 by
+// one step, so the upwind south value is the value lane l-1 produced one step
+// earlier (one warp shuffle) and the upwind west value is the lane's own
+// previous result (a register).  Lane 0 takes its south value from the band
+// below, published through a global edge row and a release/acquire counter,
+// or from the inflow on the first band.  Units are handed out in band-major
+// order by an atomic counter to persistent CTAs, so a unit only ever waits on
+// a unit that a running warp already owns (no deadlock); every wait is
+// bounded and reports kErrTimeout instead of hanging.
+//
+// Results are staged in shared memory and written as full 128-byte row
+// segments; all intensities of the last sweep stay in HBM as I[s][cell]
+// (needed by the moment reduction, the pseudo-time delta form of Sec. 4.3
+// and the final second moment).
+#include <cuda_runtime.h>
+
+#include "gsis_internal.cuh"
+
+namespace gsis {
+
+namespace {
+
+constexpr double kFourPi = 12.566370614359172953850573533118;
+
+// --------------------------------------------------------------- set-up
+// |mu_s|/dx_i and |eta_s|/dy_j per sorted direction (both precisions).
+__global__ void coef_kernel(int nx, int ny, int K, const double* __restrict__ dx,
+                            const double* __restrict__ dy, const double* __restrict__ qmu,
+                            const double* __restrict__ qeta, double* acoef, double* bcoef,
+                            float* acoef_f, float* bcoef_f)
+{
+    const int tot_a = K * nx, tot = K * (nx + ny);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
+        if (t < tot_a) {
+            const int s = t / nx, i = t - s * nx;
+            const double v = fabs(qmu[s]) / dx[i];
+            acoef[t] = v;
+            if (acoef_f) acoef_f[t] = (float)v;
+        } else {
+            const int u = t - tot_a;
+            const int s = u / ny, j = u - s * ny;
+            const double v = fabs(qeta[s]) / dy[j];
+            bcoef[u] = v;
+            if (bcoef_f) bcoef_f[u] = (float)v;
+        }
+    }
+}
+
+// Per cell: sigma_t, pseudo-time shift (Eqs. (cfl_pse), (tau_pse),
+// dx_ref = min(dx_i, dy_j)), the finite-volume synthetic operator
+// (Eqs. (elem_mtx_M), (Gamma_ij_com2) on the Cartesian mesh:
+// Gamma = 2 / (3 (sigma_i h_i + sigma_j h_j)); boundary
+// beta = 2/(3 sigma_i h_i) + 1/4 from Eq. (macro_bc_delta_flux)), input checks.
+__global__ void cell_setup_kernel(int nx, int ny, const double* __restrict__ dx,
+                                  const double* __restrict__ dy, const double* __restrict__ sa,
+                                  const double* __restrict__ ss, const double* __restrict__ q,
+                                  double cfl_p, double beta, double* sigt, float* sigt_f,
+                                  double* shift, float* shift_f, double* diag, double* cx,
+                                  double* cy, int* err)
+{
+    const int N = nx * ny;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+        const int j = c / nx, i = c - j * nx;
+        const double a = sa[c], s = ss[c], st = a + s;
+        if (!(a >= 0.0) || !(s >= 0.0) || !(st > 0.0) || !isfinite(st) || !isfinite(q[c]))
+            atomicOr(err, kErrBadInput);
+        sigt[c] = st;
+        if (sigt_f) sigt_f[c] = (float)st;
+        const double hx = dx[i], hy = dy[j];
+        // neighbour optical distances |sigma_i r^L - sigma_j r^R|
+        double th = 0.0;
+        double gE = 0.0, gW = 0.0, gN = 0.0, gS = 0.0;
+        if (i + 1 < nx) {
+            const double o = 0.5 * (st * hx + (sa[c + 1] + ss[c + 1]) * dx[i + 1]);
+            th = fmax(th, o);
+            gE = 1.0 / (3.0 * o);
+        }
+        if (i > 0) {
+            const double o = 0.5 * (st * hx + (sa[c - 1] + ss[c - 1]) * dx[i - 1]);
+            th = fmax(th, o);
+            gW = 1.0 / (3.0 * o);
+        }
+        if (j + 1 < ny) {
+            const double o = 0.5 * (st * hy + (sa[c + nx] + ss[c + nx]) * dy[j + 1]);
+            th = fmax(th, o);
+            gN = 1.0 / (3.0 * o);
+        }
+        if (j > 0) {
+            const double o = 0.5 * (st * hy + (sa[c - nx] + ss[c - nx]) * dy[j - 1]);
+            th = fmax(th, o);
+            gS = 1.0 / (3.0 * o);
+        }
+        const double ref = fmin(hx, hy);
+        double sh = 0.0;
+        if (cfl_p > 0.0) sh += 1.0 / (cfl_p * ref);
+        if (beta > 0.0) sh += th / (beta * ref);
+        shift[c] = sh;
+        if (shift_f) shift_f[c] = (float)sh;
+        // D = V sigma_a + sum_int A Gamma + sum_bnd A beta
+        double d = hx * hy * a + hy * (gE + gW) + hx * (gN + gS);
+        const double bx = 2.0 / (3.0 * st * hx) + 0.25, by = 2.0 / (3.0 * st * hy) + 0.25;
+        if (i == 0) d += hy * bx;
+        if (i == nx - 1) d += hy * bx;
+        if (j == 0) d += hx * by;
+        if (j == ny - 1) d += hx * by;
+        diag[c] = d;
+        cx[c] = hy * gE;
+        cy[c] = hx * gN;
+    }
+}
+
+// 1 / (sigma_t + shift + |mu|/dx + |eta|/dy) in sweep order (FP64 sweep).
+__global__ void recip_kernel(int nx, int ny, int K, int nb, const int* __restrict__ perm,
+                             const double* __restrict__ qmu, const double* __restrict__ qeta,
+                             const double* __restrict__ acoef, const double* __restrict__ bcoef,
+                             const double* __restrict__ sigt, const double* __restrict__ shift,
+                             double* rsw)
+{
+    const int ns = nx + 31;
+    const size_t tot = (size_t)K * nb * ns * 32;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < tot;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const int lane = (int)(t & 31);
+        size_t u = t >> 5;
+        const int step = (int)(u % ns);
+        u /= ns;
+        const int band = (int)(u % nb);
+        const int s = (int)(u / nb);
+        const int c = step - lane, jl = band * 32 + lane;
+        double v = 0.0;
+        if (c >= 0 && c < nx && jl < ny) {
+            const int i = qmu[s] >= 0.0 ? c : nx - 1 - c;
+            const int j = qeta[s] >= 0.0 ? jl : ny - 1 - jl;
+            const int cell = i + nx * j;
+            v = 1.0 / (sigt[cell] + shift[cell] + acoef[(size_t)s * nx + i] + bcoef[(size_t)s * ny + j]);
+        }
+        rsw[t] = v;
+    }
+}
+
+__global__ void fill_kernel(double* a, size_t n, double v)
+{
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+        a[t] = v;
+}
+
+__global__ void fillf_kernel(float* a, size_t n, float v)
+{
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+        a[t] = v;
+}
+
+// Angular source of the next sweep from rho (Eq. (RTE_SI)):
+// src = (sigma_s rho + q)/4pi  (no pseudo-time correction; used by the
+// stand-alone kinetic step and at start-up).
+__global__ void source_kernel(int N, const double* __restrict__ ss, const double* __restrict__ q,
+                              const double* __restrict__ rho, double* src, float* src_f)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+        const double v = (ss[c] * rho[c] + q[c]) / kFourPi;
+        src[c] = v;
+        if (src_f) src_f[c] = (float)v;
+    }
+}
+
+// --------------------------------------------------------------- sweep
+template <typename T>
+struct SweepArgs {
+    int nx, ny, N, K, nb, nsteps;
+    const T* acoef; const T* bcoef;
+    const double* rsw;
+    const T* sigt; const T* shift; const T* src;
+    T* I; T* edge;
+    unsigned long long* flags;
+    unsigned long long epoch_hi;
+    const double* inflow;
+    const int* perm; const double* qmu; const double* qeta;
+    unsigned long long* tasks;
+    int* err; const int* done;
+    long long wait_cycles;
+};
+
+__device__ __forceinline__ double rcp_t(double d) { return 1.0 / d; }
+__device__ __forceinline__ float rcp_t(float d) { return __frcp_rn(d); }
+
+template <typename T, bool PT, bool PRE>
+__global__ void __launch_bounds__(kSweepWarps * 32)
+sweep_kernel(const SweepArgs<T> a)
+{
+    constexpr int SEG = 128 / (int)sizeof(T);   // columns per 128-byte row segment
+    constexpr int RING = 4 * SEG;               // staged columns per row
+    constexpr int LAG = (31 + SEG - 1) / SEG;   // segments a row band lags behind lane 0
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* stage = reinterpret_cast<T*>(smem_raw) + (threadIdx.x >> 5) * (32 * RING);
+    const int lane = threadIdx.x & 31;
+    const int nx = a.nx, ny = a.ny, K = a.K, nb = a.nb;
+    const unsigned ntasks = (unsigned)(K * nb);
+
+    int stop = 0;
+    if (lane == 0) stop = ld_volatile_int(a.done);
+    if (__shfl_sync(kFull, stop, 0)) return;
+
+    for (;;) {
+        unsigned task = 0;
+        int bad = 0;
+        if (lane == 0) {
+            task = (unsigned)atomicAdd(a.tasks, 1ull);
+            bad = ld_volatile_int(a.err);
+        }
+        task = __shfl_sync(kFull, task, 0);
+        bad = __shfl_sync(kFull, bad, 0);
+        if (task >= ntasks || bad) return;
+        const int band = (int)(task / (unsigned)K);
+        const int s = (int)(task - (unsigned)band * (unsigned)K);
+        const bool xpos = a.qmu[s] >= 0.0, ypos = a.qeta[s] >= 0.0;
+        const int k = a.perm[s];
+        const int jl = band * 32 + lane;
+        const bool row_ok = jl < ny;
+        const int j = ypos ? jl : ny - 1 - jl;
+        const size_t rowoff = (size_t)(row_ok ? j : 0) * nx;
+        const T bj = row_ok ? a.bcoef[(size_t)s * ny + j] : T(0);
+        const T* arow = a.acoef + (size_t)s * nx;
+        T* Is = a.I + (size_t)s * a.N;
+        const double* rrow = PRE ? a.rsw + ((size_t)s * nb + band) * (size_t)a.nsteps * 32 : nullptr;
+        T* edge_out = a.edge + ((size_t)s * nb + band) * nx;
+        const T* edge_in = a.edge + ((size_t)s * nb + band - 1) * nx;
+        unsigned long long* flag_out = a.flags + (size_t)s * nb + band;
+        const unsigned long long* flag_in = a.flags + (size_t)s * nb + band - 1;
+
+        T IW = T(0);
+        if (row_ok && a.inflow) {
+            const int f = xpos ? j : ny + j;
+            IW = (T)a.inflow[(size_t)f * K + k];
+        }
+        T Iprev = T(0), edge_reg = T(0);
+        int flushed = 0;
+
+        auto flush = [&](int g) {
+            constexpr int RPI = 32 / SEG;
+            const int cc = lane % SEG, rr = lane / SEG;
+            const int c = g * SEG + cc;
+#pragma unroll
+            for (int r0 = 0; r0 < 32; r0 += RPI) {
+                const int r = r0 + rr;
+                const int jr = band * 32 + r;
+                if (c < nx && jr < ny) {
+                    const int jj = ypos ? jr : ny - 1 - jr;
+                    const int ii = xpos ? c : nx - 1 - c;
+                    Is[(size_t)jj * nx + ii] = stage[r * RING + (c & (RING - 1))];
+                }
+            }
+        };
+
+        for (int t0 = 0; t0 < a.nsteps; t0 += SEG) {
+            // south values of lane 0 for columns t0 .. t0+SEG-1, one per lane
+            if (t0 < nx) {
+                edge_reg = T(0);
+                if (band == 0) {
+                    if (a.inflow && lane < SEG && t0 + lane < nx) {
+                        const int c = t0 + lane;
+                        const int i = xpos ? c : nx - 1 - c;
+                        const int f = ypos ? 2 * ny + i : 2 * ny + nx + i;
+                        edge_reg = (T)a.inflow[(size_t)f * K + k];
+                    }
+                } else {
+                    int ok = 1;
+                    if (lane == 0) {
+                        const unsigned long long need = a.epoch_hi | (unsigned long long)min(nx, t0 + SEG);
+                        ok = wait_at_least(flag_in, need, a.wait_cycles, a.err) ? 1 : 0;
+                    }
+                    ok = __shfl_sync(kFull, ok, 0);
+                    if (!ok) return;
+                    if (lane < SEG && t0 + lane < nx) edge_reg = __ldcg(edge_in + t0 + lane);
+                }
+            }
+#pragma unroll 4
+            for (int tt = 0; tt < SEG; ++tt) {
+                const int t = t0 + tt;
+                if (t >= a.nsteps) break;
+                T Isouth = __shfl_up_sync(kFull, Iprev, 1);
+                const T e = __shfl_sync(kFull, edge_reg, tt);
+                if (lane == 0) Isouth = e;
+                const int c = t - lane;
+                T Inew = T(0);
+                if (row_ok && c >= 0 && c < nx) {
+                    const int i = xpos ? c : nx - 1 - c;
+                    const size_t cell = rowoff + i;
+                    T sv = a.src[cell];
+                    if (PT) sv = fma(a.shift[cell], Is[cell], sv);
+                    const T ai = arow[i];
+                    T acc = fma(ai, IW, sv);
+                    acc = fma(bj, Isouth, acc);
+                    T rinv;
+                    if (PRE) {
+                        rinv = (T)rrow[(size_t)t * 32 + lane];
+                    } else {
+                        T d = a.sigt[cell] + ai + bj;
+                        if (PT) d += a.shift[cell];
+                        rinv = rcp_t(d);
+                    }
+                    Inew = acc * rinv;
+                    IW = Inew;
+                    stage[lane * RING + (c & (RING - 1))] = Inew;
+                    if (lane == 31 && band < nb - 1) edge_out[c] = Inew;
+                }
+                Iprev = Inew;
+            }
+            if (band < nb - 1 && lane == 31) {
+                const int cols = min(nx, t0 + SEG - 31);
+                if (cols > 0) {
+                    __threadfence();
+                    st_release_u64(flag_out, a.epoch_hi | (unsigned long long)cols);
+                }
+            }
+            __syncwarp();
+            const int last_complete = t0 / SEG - LAG;
+            while (flushed <= last_complete && flushed * SEG < nx) {
+                flush(flushed);
+                ++flushed;
+            }
+            __syncwarp();
+        }
+        while (flushed * SEG < nx) {
+            flush(flushed);
+            ++flushed;
+        }
+        __syncwarp();
+    }
+}
+
+// --------------------------------------------------------------- moments
+template <typename T>
+struct MomArgs {
+    int nx, ny, N, K;
+    const T* I;
+    const int* sidx;
+    const double* mu; const double* eta; const double* w;   // original order
+    double* rho; double* Fx; double* Fy;                    // may be null (F)
+    double* Pxx; double* Pxy; double* Pyy;                  // may be null
+    const double* rho_new;                                  // GSIS correction of P (or null)
+    unsigned long long* tasks;                              // sweep counter to re-arm
+    const int* done;
+};
+
+// Per cell, in original direction order k = 0..K-1:
+// rho = sum w I, F = sum w Omega I, P = sum w Omega Omega I.
+template <typename T, bool WITH_F, bool WITH_P>
+__global__ void __launch_bounds__(kRedBlock) moments_kernel(const MomArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* cf = reinterpret_cast<T*>(smem_raw);                     // [K][6]
+    int* sk = reinterpret_cast<int*>(cf + 6 * a.K);             // [K]
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.tasks = 0ull;    // re-arm the sweep task counter
+    if (a.done && ld_volatile_int(a.done)) return;
+    for (int k = threadIdx.x; k < a.K; k += blockDim.x) {
+        const double w = a.w[k], m = a.mu[k], e = a.eta[k];
+        cf[6 * k + 0] = (T)w;
+        cf[6 * k + 1] = (T)(w * m);
+        cf[6 * k + 2] = (T)(w * e);
+        cf[6 * k + 3] = (T)(w * m * m);
+        cf[6 * k + 4] = (T)(w * m * e);
+        cf[6 * k + 5] = (T)(w * e * e);
+        sk[k] = a.sidx[k];
+    }
+    __syncthreads();
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < a.N; c += gridDim.x * blockDim.x) {
+        T r = T(0), fx = T(0), fy = T(0), pxx = T(0), pxy = T(0), pyy = T(0);
+        for (int k = 0; k < a.K; ++k) {
+            const T v = a.I[(size_t)sk[k] * a.N + c];
+            r = fma(cf[6 * k + 0], v, r);
+            if (WITH_F) {
+                fx = fma(cf[6 * k + 1], v, fx);
+                fy = fma(cf[6 * k + 2], v, fy);
+            }
+            if (WITH_P) {
+                pxx = fma(cf[6 * k + 3], v, pxx);
+                pxy = fma(cf[6 * k + 4], v, pxy);
+                pyy = fma(cf[6 * k + 5], v, pyy);
+            }
+        }
+        if (a.rho) a.rho[c] = (double)r;
+        if (WITH_F) {
+            a.Fx[c] = (double)fx;
+            a.Fy[c] = (double)fy;
+        }
+        if (WITH_P) {
+            double dxx = (double)pxx, dyy = (double)pyy;
+            if (a.rho_new) {   // moments of I + (rho_new - rho_half)/4pi: + drho/3 on the diagonal
+                const double d = (a.rho_new[c] - (double)r) / 3.0;
+                dxx += d;
+                dyy += d;
+            }
+            a.Pxx[c] = dxx;
+            a.Pxy[c] = (double)pxy;
+            a.Pyy[c] = dyy;
+        }
+    }
+}
+
+// Kinetic net flux through every boundary face, sum_k w_k (Omega_k . n) I_face,k
+// (outgoing: boundary cell intensity, incoming: inflow).
+template <typename T>
+__global__ void bflux_kernel(int nx, int ny, int K, const T* __restrict__ I, const int* __restrict__ sidx,
+                             const double* __restrict__ mu, const double* __restrict__ eta,
+                             const double* __restrict__ w, const double* __restrict__ inflow,
+                             double* fb, const int* done)
+{
+    if (done && ld_volatile_int(done)) return;
+    const int nbf = 2 * (nx + ny), N = nx * ny;
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nbf; f += gridDim.x * blockDim.x) {
+        int c, axis;
+        double sgn;
+        if (f < ny) { c = nx * f; axis = 0; sgn = -1.0; }
+        else if (f < 2 * ny) { c = nx - 1 + nx * (f - ny); axis = 0; sgn = 1.0; }
+        else if (f < 2 * ny + nx) { c = f - 2 * ny; axis = 1; sgn = -1.0; }
+        else { c = (f - 2 * ny - nx) + nx * (ny - 1); axis = 1; sgn = 1.0; }
+        T acc = T(0);
+        for (int k = 0; k < K; ++k) {
+            const double on = sgn * (axis == 0 ? mu[k] : eta[k]);
+            T Iface;
+            if (on >= 0.0) Iface = I[(size_t)sidx[k] * N + c];
+            else Iface = inflow ? (T)inflow[(size_t)f * K + k] : T(0);
+            acc = fma((T)(w[k] * on), Iface, acc);
+        }
+        fb[f] = (double)acc;
+    }
+}
+
+int grid_for(long long n, int block, int cap)
+{
+    long long g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+template <typename T>
+size_t sweep_smem();
+
+template <typename T, bool PT, bool PRE>
+cudaError_t launch_sweep_t(Plan& P, cudaStream_t st)
+{
+    SweepArgs<T> a{};
+    a.nx = P.nx; a.ny = P.ny; a.N = P.N; a.K = P.K; a.nb = P.nb; a.nsteps = P.nx + 31;
+    if constexpr (sizeof(T) == 8) {
+        a.acoef = P.acoef; a.bcoef = P.bcoef; a.sigt = P.sigt; a.shift = P.shift; a.src = P.src;
+    } else {
+        a.acoef = P.acoef_f; a.bcoef = P.bcoef_f; a.sigt = P.sigt_f; a.shift = P.shift_f; a.src = P.src_f;
+    }
+    a.rsw = P.rsw;
+    a.I = static_cast<T*>(P.I);
+    a.edge = static_cast<T*>(P.edge);
+    a.flags = P.flags;
+    P.epoch += 1;
+    a.epoch_hi = P.epoch << 20;
+    a.inflow = P.inflow;
+    a.perm = P.perm; a.qmu = P.qmu; a.qeta = P.qeta;
+    a.tasks = &P.status->sweep_tasks;
+    a.err = &P.status->error;
+    a.done = &P.status->done;
+    a.wait_cycles = P.wait_cycles;
+    sweep_kernel<T, PT, PRE><<<P.sweep_grid, kSweepWarps * 32, sweep_smem<T>(), st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+size_t moments_smem(int K)
+{
+    return (size_t)K * (6 * sizeof(T) + sizeof(int)) + 16;
+}
+
+template <typename T>
+cudaError_t launch_moments_t(const Plan& P, bool with_F, bool with_P, double* rho_out, double* Fout,
+                             double* Pout, bool gsis_correct, double* fb_out, bool force, cudaStream_t st)
+{
+    MomArgs<T> a{};
+    a.nx = P.nx; a.ny = P.ny; a.N = P.N; a.K = P.K;
+    a.I = static_cast<const T*>(P.I);
+    a.sidx = P.sidx;
+    a.mu = P.omu;
+    a.eta = P.oeta;
+    a.w = P.ow;
+    a.rho = rho_out;
+    a.Fx = Fout ? Fout : P.Fx;
+    a.Fy = Fout ? Fout + P.N : P.Fy;
+    if (with_P) { a.Pxx = Pout; a.Pxy = Pout + P.N; a.Pyy = Pout + 2 * (size_t)P.N; }
+    a.rho_new = gsis_correct ? P.rho_m : nullptr;
+    a.tasks = &P.status->sweep_tasks;
+    a.done = force ? nullptr : &P.status->done;
+    const size_t smem = moments_smem<T>(P.K);
+    const int grid = grid_for(P.N, kRedBlock, P.num_sms * 8);
+    if (with_P) moments_kernel<T, true, true><<<grid, kRedBlock, smem, st>>>(a);
+    else if (with_F) moments_kernel<T, true, false><<<grid, kRedBlock, smem, st>>>(a);
+    else moments_kernel<T, false, false><<<grid, kRedBlock, smem, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    bflux_kernel<T><<<grid_for(P.nbf, 128, 64), 128, 0, st>>>(
+        P.nx, P.ny, P.K, static_cast<const T*>(P.I), P.sidx, a.mu, a.eta, a.w, P.inflow, fb_out, a.done);
+    return cudaGetLastError();
+}
+
+template <typename T>
+size_t sweep_smem()
+{
+    return (size_t)kSweepWarps * 32 * 4 * (128 / sizeof(T)) * sizeof(T);
+}
+
+template <typename T>
+cudaError_t prepare_t(int K)
+{
+    cudaError_t e;
+    const int ss = (int)sweep_smem<T>(), ms = (int)moments_smem<T>(K);
+    if ((e = cudaFuncSetAttribute(sweep_kernel<T, false, sizeof(T) == 8>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, ss)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(sweep_kernel<T, true, sizeof(T) == 8>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, ss)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(moments_kernel<T, true, true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, ms)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(moments_kernel<T, true, false>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, ms)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(moments_kernel<T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ms);
+}
+
+template <typename T, bool PT>
+int sweep_occupancy()
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<T, PT, sizeof(T) == 8>, kSweepWarps * 32,
+                                                      sweep_smem<T>()) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+}  // namespace
+
+int device_sm_count()
+{
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    return n;
+}
+
+cudaError_t launch_setup(const Plan& P, cudaStream_t st)
+{
+    const int tot = P.K * (P.nx + P.ny);
+    coef_kernel<<<grid_for(tot, 256, 1024), 256, 0, st>>>(
+        P.nx, P.ny, P.K, P.dx, P.dy, P.qmu, P.qeta, const_cast<double*>(P.acoef),
+        const_cast<double*>(P.bcoef), P.fp32 ? const_cast<float*>(P.acoef_f) : nullptr,
+        P.fp32 ? const_cast<float*>(P.bcoef_f) : nullptr);
+    return cudaGetLastError();
+}
+
+// Per-cell set-up and the FP64 reciprocal table (pseudo-time controls given).
+cudaError_t launch_cell_setup(const Plan& P, double cfl_p, double beta, cudaStream_t st)
+{
+    cell_setup_kernel<<<grid_for(P.N, 256, P.num_sms * 8), 256, 0, st>>>(
+        P.nx, P.ny, P.dx, P.dy, P.sigma_a, P.sigma_s, P.q, cfl_p, beta, P.sigt,
+        P.fp32 ? P.sigt_f : nullptr, P.shift, P.fp32 ? P.shift_f : nullptr, P.diag, P.cx, P.cy,
+        &P.status->error);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (!P.fp32) {
+        const size_t tot = (size_t)P.K * P.nb * (P.nx + 31) * 32;
+        recip_kernel<<<grid_for((long long)tot, 256, P.num_sms * 16), 256, 0, st>>>(
+            P.nx, P.ny, P.K, P.nb, P.perm, P.qmu, P.qeta, P.acoef, P.bcoef, P.sigt, P.shift,
+            const_cast<double*>(P.rsw));
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+cudaError_t launch_init_state(const Plan& P, cudaStream_t st)
+{
+    const int g = grid_for(P.N, 256, P.num_sms * 8);
+    fill_kernel<<<g, 256, 0, st>>>(P.rho_m, P.N, 0.0);
+    fill_kernel<<<g, 256, 0, st>>>(P.rho_h, P.N, 0.0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (P.pt) {   // I^0 = 0 (the delta form reads it)
+        const size_t n = (size_t)P.K * P.N;
+        if (P.fp32) fillf_kernel<<<grid_for((long long)n, 256, P.num_sms * 16), 256, 0, st>>>(static_cast<float*>(P.I), n, 0.f);
+        else fill_kernel<<<grid_for((long long)n, 256, P.num_sms * 16), 256, 0, st>>>(static_cast<double*>(P.I), n, 0.0);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return launch_source_from(P, P.rho_m, st);
+}
+
+cudaError_t launch_source_from(const Plan& P, const double* rho_in, cudaStream_t st)
+{
+    source_kernel<<<grid_for(P.N, 256, P.num_sms * 8), 256, 0, st>>>(P.N, P.sigma_s, P.q, rho_in, P.src,
+                                                                    P.fp32 ? P.src_f : nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep(Plan& P, cudaStream_t st)
+{
+    if (P.fp32) {
+        return P.pt ? launch_sweep_t<float, true, false>(P, st) : launch_sweep_t<float, false, false>(P, st);
+    }
+    return P.pt ? launch_sweep_t<double, true, true>(P, st) : launch_sweep_t<double, false, true>(P, st);
+}
+
+// Moments of the last sweep into the given outputs: rho always, F when
+// with_F (Fout or the plan's F arrays), P when with_P (plus drho/3 on the
+// diagonal when gsis_correct), boundary fluxes into fb_out.  force: run even
+// after the device has stopped the iteration (final outputs).
+cudaError_t launch_moments_to(const Plan& P, bool with_F, bool with_P, double* rho_out, double* Fout,
+                              double* Pout, bool gsis_correct, double* fb_out, bool force, cudaStream_t st)
+{
+    if (P.fp32)
+        return launch_moments_t<float>(P, with_F, with_P, rho_out, Fout, Pout, gsis_correct, fb_out, force, st);
+    return launch_moments_t<double>(P, with_F, with_P, rho_out, Fout, Pout, gsis_correct, fb_out, force, st);
+}
+
+cudaError_t prepare_kernels(int K, int fp32, int pt)
+{
+    (void)pt;
+    return fp32 ? prepare_t<float>(K) : prepare_t<double>(K);
+}
+
+int sweep_max_active_blocks(int fp32, int pt)
+{
+    if (fp32) return pt ? sweep_occupancy<float, true>() : sweep_occupancy<float, false>();
+    return pt ? sweep_occupancy<double, true>() : sweep_occupancy<double, false>();
+}
+
+}  // namespace gsis

@@ -1,0 +1,279 @@
+"""Python binding of libgsis (include/gsis.h): argument marshalling only.
+
+Device arrays are torch tensors (float64, contiguous, on the current CUDA
+device); host arrays (mesh spacings, quadrature) are numpy arrays.  Every
+computation happens in the CUDA library; if it is not built or cannot be
+loaded, every call raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+GSIS_OK = 0
+GSIS_ERR_ARG = -1
+GSIS_ERR_CUDA = -2
+GSIS_ERR_MAXITER = -3
+GSIS_ERR_DIVERGED = -4
+GSIS_ERR_STALLED = -5
+GSIS_ERR_DEVICE_TIMEOUT = -6
+GSIS_ERR_WORKSPACE = -7
+
+SCHEME_SI = 0
+SCHEME_GSIS = 1
+FP64 = 0
+FP32_SWEEP = 1
+
+_P = ctypes.POINTER(ctypes.c_double)
+
+
+class GsisError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"gsis status {status}: {message}")
+        self.status = status
+
+
+class Mesh(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("dx", _P), ("dy", _P)]
+
+
+class Quadrature(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int), ("mu", _P), ("eta", _P), ("w", _P)]
+
+
+KERNEL_CLASSES = ("setup", "sweep", "moments", "hot_rhs", "synth", "update")
+
+
+class KernelStats(ctypes.Structure):
+    _fields_ = [("kernels", ctypes.c_longlong), ("groups", ctypes.c_longlong),
+                ("timed", ctypes.c_longlong), ("total_ms", ctypes.c_double)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("scheme", ctypes.c_int), ("precision", ctypes.c_int), ("tol", ctypes.c_double),
+        ("max_iter", ctypes.c_int), ("fixed_iters", ctypes.c_int), ("synth_rtol", ctypes.c_double),
+        ("synth_max_iter", ctypes.c_int), ("cfl_p", ctypes.c_double), ("beta", ctypes.c_double),
+        ("check_every", ctypes.c_int), ("stall_window", ctypes.c_int), ("wait_limit_s", ctypes.c_double),
+    ]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False) -> ctypes.CDLL:
+    """Load the in-tree libgsis.so (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        if not build_if_missing:
+            raise RuntimeError(f"libgsis is not built ({_build.LIB}); run __graft_entry__.build()")
+        _build.build()
+    lib = ctypes.CDLL(_build.LIB)
+    vp, sz = ctypes.c_void_p, ctypes.c_size_t
+    Mp, Qp, Op = ctypes.POINTER(Mesh), ctypes.POINTER(Quadrature), ctypes.POINTER(Options)
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib.gsis_default_options.argtypes = [Op]
+    lib.gsis_default_options.restype = None
+    lib.gsis_quadrature_level_symmetric.argtypes = [ctypes.c_int, _P, _P, _P, ip]
+    lib.gsis_workspace_bytes.argtypes = [Mp, Qp, Op, ctypes.POINTER(sz)]
+    lib.gsis_solve.argtypes = [Mp, Qp, Op, vp, vp, vp, vp, vp, vp, vp, _P, ip, _P, vp, sz, vp]
+    lib.gsis_transport_sweep.argtypes = [Mp, Qp, Op, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+    lib.gsis_synthetic_step.argtypes = [Mp, Op, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, ip, vp, sz, vp]
+    lib.gsis_profile_enable.argtypes = [ctypes.c_int]
+    lib.gsis_profile_enable.restype = ctypes.c_int
+    lib.gsis_profile_read.argtypes = [ctypes.POINTER(KernelStats), ctypes.c_int]
+    lib.gsis_profile_read.restype = ctypes.c_int
+    lib.gsis_status_string.argtypes = [ctypes.c_int]
+    lib.gsis_status_string.restype = ctypes.c_char_p
+    lib.gsis_last_error.argtypes = []
+    lib.gsis_last_error.restype = ctypes.c_char_p
+    for name in ("gsis_quadrature_level_symmetric", "gsis_workspace_bytes", "gsis_solve",
+                 "gsis_transport_sweep", "gsis_synthetic_step"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    return load().gsis_status_string(status).decode()
+
+
+def last_error() -> str:
+    return load().gsis_last_error().decode()
+
+
+def _raise(rc: int, hard=(GSIS_ERR_ARG, GSIS_ERR_CUDA, GSIS_ERR_WORKSPACE, GSIS_ERR_DEVICE_TIMEOUT)):
+    if rc in hard:
+        raise GsisError(rc, last_error() or status_string(rc))
+    return rc
+
+
+def profile_enable(enable: bool = True) -> None:
+    """gsis_profile_enable: reset the per-class counters; time later launches."""
+    _raise(load().gsis_profile_enable(1 if enable else 0))
+
+
+def profile_read() -> dict:
+    """gsis_profile_read: {class: dict(kernels, groups, timed, total_ms)}."""
+    arr = (KernelStats * len(KERNEL_CLASSES))()
+    _raise(load().gsis_profile_read(arr, len(KERNEL_CLASSES)))
+    return {n: dict(kernels=a.kernels, groups=a.groups, timed=a.timed, total_ms=a.total_ms)
+            for n, a in zip(KERNEL_CLASSES, arr)}
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    load().gsis_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def quadrature_level_symmetric(order: int):
+    lib = load()
+    K = ctypes.c_int(0)
+    _raise(lib.gsis_quadrature_level_symmetric(order, None, None, None, ctypes.byref(K)))
+    mu, eta, w = (np.zeros(K.value) for _ in range(3))
+    _raise(lib.gsis_quadrature_level_symmetric(order, _hp(mu), _hp(eta), _hp(w), ctypes.byref(K)))
+    return mu, eta, w
+
+
+def _hp(a: np.ndarray):
+    return a.ctypes.data_as(_P)
+
+
+def _host(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _dev(t, n=None, name="array"):
+    """Device pointer of a float64 contiguous CUDA tensor (or None)."""
+    if t is None:
+        return None
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+    if n is not None and t.numel() < n:
+        raise ValueError(f"{name} has {t.numel()} elements, needs {n}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class _Args:
+    """Keeps the host arrays alive while the C structs point at them."""
+
+    def __init__(self, dx, dy, mu=None, eta=None, w=None):
+        self.dx, self.dy = _host(dx), _host(dy)
+        self.mesh = Mesh(len(self.dx), len(self.dy), _hp(self.dx), _hp(self.dy))
+        self.quad = None
+        if mu is not None:
+            self.mu, self.eta, self.w = _host(mu), _host(eta), _host(w)
+            self.quad = Quadrature(len(self.mu), _hp(self.mu), _hp(self.eta), _hp(self.w))
+
+
+def workspace_bytes(dx, dy, mu=None, eta=None, w=None, options: Options | None = None) -> int:
+    a = _Args(dx, dy, mu, eta, w)
+    o = options or default_options()
+    n = ctypes.c_size_t(0)
+    _raise(load().gsis_workspace_bytes(ctypes.byref(a.mesh), ctypes.byref(a.quad) if a.quad else None,
+                                       ctypes.byref(o), ctypes.byref(n)))
+    return int(n.value)
+
+
+def _workspace(nbytes, workspace, device):
+    import torch
+    if workspace is None or workspace.numel() < nbytes:
+        workspace = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=device)
+    return workspace
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def solve(dx, dy, mu, eta, w, sigma_a, sigma_s, q, inflow=None, options: Options | None = None,
+          want_P=True, workspace=None, stream=None):
+    """gsis_solve: returns dict(rho, F, P, iters, err, history, status, workspace)."""
+    import torch
+    a = _Args(dx, dy, mu, eta, w)
+    o = options or default_options()
+    N, K = a.mesh.nx * a.mesh.ny, a.quad.K
+    dev = sigma_a.device
+    rho = torch.empty(N, dtype=torch.float64, device=dev)
+    F = torch.empty(2 * N, dtype=torch.float64, device=dev)
+    P = torch.empty(3 * N, dtype=torch.float64, device=dev) if want_P else None
+    nh = max(o.max_iter, o.fixed_iters, 1)
+    hist = np.zeros(nh)
+    iters, err = ctypes.c_int(0), ctypes.c_double(0.0)
+    nbytes = workspace_bytes(a.dx, a.dy, a.mu, a.eta, a.w, o)
+    workspace = _workspace(nbytes, workspace, dev)
+    rc = load().gsis_solve(
+        ctypes.byref(a.mesh), ctypes.byref(a.quad), ctypes.byref(o),
+        _dev(sigma_a, N, "sigma_a"), _dev(sigma_s, N, "sigma_s"), _dev(q, N, "q"),
+        _dev(inflow, 2 * (a.mesh.nx + a.mesh.ny) * K, "inflow"),
+        _dev(rho), _dev(F), _dev(P), _hp(hist), ctypes.byref(iters), ctypes.byref(err),
+        ctypes.c_void_p(workspace.data_ptr()), ctypes.c_size_t(workspace.numel()), _stream(stream))
+    _raise(rc)
+    return dict(rho=rho, F=F, P=P, iters=iters.value, err=err.value, history=hist[:iters.value],
+                status=rc, workspace=workspace)
+
+
+def transport_sweep(dx, dy, mu, eta, w, sigma_a, sigma_s, q, rho_in, inflow=None,
+                    options: Options | None = None, want_P=True, workspace=None, stream=None):
+    """gsis_transport_sweep: returns dict(rho, F, P, bflux)."""
+    import torch
+    a = _Args(dx, dy, mu, eta, w)
+    o = options or default_options()
+    N, K = a.mesh.nx * a.mesh.ny, a.quad.K
+    dev = sigma_a.device
+    rho = torch.empty(N, dtype=torch.float64, device=dev)
+    F = torch.empty(2 * N, dtype=torch.float64, device=dev)
+    P = torch.empty(3 * N, dtype=torch.float64, device=dev) if want_P else None
+    fb = torch.empty(2 * (a.mesh.nx + a.mesh.ny), dtype=torch.float64, device=dev)
+    nbytes = workspace_bytes(a.dx, a.dy, a.mu, a.eta, a.w, o)
+    workspace = _workspace(nbytes, workspace, dev)
+    rc = load().gsis_transport_sweep(
+        ctypes.byref(a.mesh), ctypes.byref(a.quad), ctypes.byref(o),
+        _dev(sigma_a, N, "sigma_a"), _dev(sigma_s, N, "sigma_s"), _dev(q, N, "q"),
+        _dev(inflow, 2 * (a.mesh.nx + a.mesh.ny) * K, "inflow"), _dev(rho_in, N, "rho_in"),
+        _dev(rho), _dev(F), _dev(P), _dev(fb), ctypes.c_void_p(workspace.data_ptr()),
+        ctypes.c_size_t(workspace.numel()), _stream(stream))
+    _raise(rc)
+    return dict(rho=rho, F=F, P=P, bflux=fb, workspace=workspace)
+
+
+def synthetic_step(dx, dy, sigma_a, sigma_s, q, rho_half, F_half, bflux, rho_guess=None,
+                   options: Options | None = None, workspace=None, stream=None):
+    """gsis_synthetic_step: returns dict(rho, hot, rhs, synth_iters)."""
+    import torch
+    a = _Args(dx, dy)
+    o = options or default_options()
+    N = a.mesh.nx * a.mesh.ny
+    dev = sigma_a.device
+    rho = torch.empty(N, dtype=torch.float64, device=dev)
+    hot = torch.empty(2 * N, dtype=torch.float64, device=dev)
+    rhs = torch.empty(N, dtype=torch.float64, device=dev)
+    it = ctypes.c_int(0)
+    nbytes = workspace_bytes(a.dx, a.dy, options=o)
+    workspace = _workspace(nbytes, workspace, dev)
+    rc = load().gsis_synthetic_step(
+        ctypes.byref(a.mesh), ctypes.byref(o), _dev(sigma_a, N, "sigma_a"), _dev(sigma_s, N, "sigma_s"),
+        _dev(q, N, "q"), _dev(rho_half, N, "rho_half"), _dev(F_half, 2 * N, "F_half"),
+        _dev(bflux, 2 * (a.mesh.nx + a.mesh.ny), "bflux"), _dev(rho_guess, N, "rho_guess"),
+        _dev(rho), _dev(hot), _dev(rhs), ctypes.byref(it), ctypes.c_void_p(workspace.data_ptr()),
+        ctypes.c_size_t(workspace.numel()), _stream(stream))
+    _raise(rc)
+    return dict(rho=rho, hot=hot, rhs=rhs, synth_iters=it.value, workspace=workspace)
