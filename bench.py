@@ -163,9 +163,9 @@ def run_ours(args):
                                max_iter=5000, check_every=16)
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device=dev)   # 512 MiB > L2
-    r = gsis.solve(p.dx, p.dy, p.mu, p.eta, p.w, sa, ss, q, inflow, opt)
-    workspace = r["workspace"]
-    for _ in range(max(0, args.warmup - 1)):
+    nbytes = gsis.workspace_bytes(p.dx, p.dy, p.mu, p.eta, p.w, opt)
+    workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
         gsis.solve(p.dx, p.dy, p.mu, p.eta, p.w, sa, ss, q, inflow, opt, workspace=workspace)
     torch.cuda.synchronize()
 
@@ -208,7 +208,7 @@ def run_ours(args):
     h_rho = torch.empty(p.N, dtype=torch.float64).pin_memory()
     h_F = torch.empty(2 * p.N, dtype=torch.float64).pin_memory()
     e2e_ms, e2e_iters = [], []
-    for _ in range(max(1, min(args.steps, 3))):
+    for _ in range(0 if args.no_e2e else max(1, min(args.steps, 3))):
         flush.fill_(2.0)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -224,7 +224,7 @@ def run_ours(args):
         e2e_iters.append(r["iters"])
     h2d = sum(h.numel() * 8 for h in h_in)
     d2h = (h_rho.numel() + h_F.numel()) * 8
-    e2e_value = sum(e2e_iters) * p.N * p.K / (sum(e2e_ms) * 1e-3) * n_ranks
+    e2e_value = (sum(e2e_iters) * p.N * p.K / (sum(e2e_ms) * 1e-3) * n_ranks) if e2e_ms else None
 
     # ---- time-to-converge of plain source iteration on the same problem (once)
     si = None
@@ -309,6 +309,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-si", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
