@@ -183,6 +183,32 @@ int gsis_synthetic_step(const gsis_mesh* mesh, const gsis_options* opt,
                         void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * gsis_transport_sweep() for callers that cannot allocate device memory.
+ * The paper has no counterpart: this is an interface convenience.
+ *
+ * Callers without a device allocator of their own (a plain C host program
+ * that links only this library, a plug-in whose host application owns all
+ * device memory through its own pool) pass only their inputs and outputs;
+ * the scratch is one static device array of GSIS_STATIC_SCRATCH_BYTES
+ * (32 MiB) inside the library.  Every GPU on which the library's kernels are
+ * loaded keeps that array reserved until the process exits.
+ * Arguments, layouts and results are those of gsis_transport_sweep().
+ * Problems whose gsis_workspace_bytes() exceeds the array are rejected with
+ * GSIS_ERR_WORKSPACE before any device work.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress, once per
+ * device): make that first call before any stream capture.  All calls share
+ * the one array, which keeps the last call's contents (each call clears what
+ * must start at zero); calls that overlap on the GPU race on it.  The call
+ * allocates no device memory (no cudaMalloc/cudaFree).  Stream-ordered.
+ */
+#define GSIS_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int gsis_transport_sweep_static(const gsis_mesh* mesh, const gsis_quadrature* quad,
+                                const gsis_options* opt, const double* sigma_a,
+                                const double* sigma_s, const double* q, const double* inflow,
+                                const double* rho_in, double* rho_half, double* F_half,
+                                double* P_half, double* bflux, void* stream);
+
+/*
  * Instrumentation (not part of the method): every call counts the kernels it
  * launches per class; after gsis_profile_enable(1) each class launch is also
  * bracketed by CUDA events on the caller's stream and its device time is

@@ -320,6 +320,12 @@ Sizes sizes_of(const gsis_mesh* m, const gsis_quadrature* q, const gsis_options*
 
 }  // namespace
 
+void gsis::set_last_error(int code, const char* msg)
+{
+    (void)code;
+    g_last_error = msg ? msg : "";
+}
+
 extern "C" {
 
 void gsis_default_options(gsis_options* o)

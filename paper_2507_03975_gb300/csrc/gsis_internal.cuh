@@ -111,6 +111,7 @@ cudaError_t launch_synthetic_solve(const Plan& P, const double* guess, double* o
 cudaError_t launch_update(const Plan& P, const double* rho_new, cudaStream_t st);
 
 int device_sm_count();
+void set_last_error(int code, const char* msg);   // message returned by gsis_last_error()
 
 // ------------------------------------------------------------ device helpers
 #ifdef __CUDACC__

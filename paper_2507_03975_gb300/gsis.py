@@ -89,6 +89,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.gsis_solve.argtypes = [Mp, Qp, Op, vp, vp, vp, vp, vp, vp, vp, _P, ip, _P, vp, sz, vp]
     lib.gsis_transport_sweep.argtypes = [Mp, Qp, Op, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
     lib.gsis_synthetic_step.argtypes = [Mp, Op, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, ip, vp, sz, vp]
+    lib.gsis_transport_sweep_static.argtypes = [Mp, Qp, Op, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.gsis_transport_sweep_static.restype = ctypes.c_int
     lib.gsis_profile_enable.argtypes = [ctypes.c_int]
     lib.gsis_profile_enable.restype = ctypes.c_int
     lib.gsis_profile_read.argtypes = [ctypes.POINTER(KernelStats), ctypes.c_int]
@@ -253,6 +255,29 @@ def transport_sweep(dx, dy, mu, eta, w, sigma_a, sigma_s, q, rho_in, inflow=None
         ctypes.c_size_t(workspace.numel()), _stream(stream))
     _raise(rc)
     return dict(rho=rho, F=F, P=P, bflux=fb, workspace=workspace)
+
+
+def transport_sweep_static(dx, dy, mu, eta, w, sigma_a, sigma_s, q, rho_in, inflow=None,
+                           options: Options | None = None, want_P=True, stream=None):
+    """gsis_transport_sweep_static: the kinetic step with the library's static
+    device scratch (no workspace, no device allocation by the library);
+    returns dict(rho, F, P, bflux)."""
+    import torch
+    a = _Args(dx, dy, mu, eta, w)
+    o = options or default_options()
+    N, K = a.mesh.nx * a.mesh.ny, a.quad.K
+    dev = sigma_a.device
+    rho = torch.empty(N, dtype=torch.float64, device=dev)
+    F = torch.empty(2 * N, dtype=torch.float64, device=dev)
+    P = torch.empty(3 * N, dtype=torch.float64, device=dev) if want_P else None
+    fb = torch.empty(2 * (a.mesh.nx + a.mesh.ny), dtype=torch.float64, device=dev)
+    rc = load().gsis_transport_sweep_static(
+        ctypes.byref(a.mesh), ctypes.byref(a.quad), ctypes.byref(o),
+        _dev(sigma_a, N, "sigma_a"), _dev(sigma_s, N, "sigma_s"), _dev(q, N, "q"),
+        _dev(inflow, 2 * (a.mesh.nx + a.mesh.ny) * K, "inflow"), _dev(rho_in, N, "rho_in"),
+        _dev(rho), _dev(F), _dev(P), _dev(fb), _stream(stream))
+    _raise(rc)
+    return dict(rho=rho, F=F, P=P, bflux=fb)
 
 
 def synthetic_step(dx, dy, sigma_a, sigma_s, q, rho_half, F_half, bflux, rho_guess=None,
