@@ -37,12 +37,17 @@ METRIC = "cell-direction updates/s and time-to-converge (GSIS vs SI) on 1 GB300;
 UNIT = "cell-direction updates/s"
 TOL = 1e-8
 BETA = 10.0   # local pseudo-time control (Sec. 4.3) the 2000/0.2 opacity jump needs
+SYNTH_CAP = 5  # inner iterations of the synthetic solve per GSIS iteration (capped sub-iterations, Sec. 4.2)
 
 
-def _workload():
+def _workload(args=None):
     p = W.config_channel()
+    cap = getattr(args, "synth_cap", SYNTH_CAP) if args is not None else SYNTH_CAP
     return p, dict(workload="channel_256x256_S12_seed2", nx=p.nx, ny=p.ny, K=p.K, scheme="gsis",
                    beta=BETA, tol=TOL, precision="fp64",
+                   synthetic=f"FP64 iterative refinement, FP32 multigrid-CG inner iterations capped at {cap} "
+                             "per GSIS iteration (warm-started; same fixed point)" if cap > 0 else
+                             "solved to relative residual 1e-12",
                    l2="flushed before each step (512 MiB write); per-solve working set ~105 MB")
 
 
@@ -156,11 +161,13 @@ def run_ours(args):
         dist = None
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
-    p, cfg = _workload()
+    p, cfg = _workload(args)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
     sa, ss, q, inflow = t(p.sigma_a), t(p.sigma_s), t(p.q), t(p.inflow.reshape(-1))
+    cap = args.synth_cap
     opt = gsis.default_options(scheme=gsis.SCHEME_GSIS, precision=gsis.FP64, tol=TOL, beta=BETA,
-                               max_iter=5000, check_every=16)
+                               max_iter=5000, check_every=16,
+                               synth_max_iter=cap if cap > 0 else 20000)
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device=dev)   # 512 MiB > L2
     nbytes = gsis.workspace_bytes(p.dx, p.dy, p.mu, p.eta, p.w, opt)
@@ -175,7 +182,7 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     proc, cf = _clock_sampler() if rank == 0 else (None, None)
-    step_ms, iters = [], []
+    step_ms, iters, inner = [], [], []
     for _ in range(args.steps):
         flush.fill_(1.0)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -186,6 +193,7 @@ def run_ours(args):
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
         iters.append(r["iters"])
+        inner.append(r["synth_inner_iters"])
         if r["status"] != gsis.GSIS_OK:
             raise RuntimeError(f"solve did not converge: status {r['status']}, Err {r['err']}")
     torch.cuda.synchronize()
@@ -248,36 +256,38 @@ def run_ours(args):
             dist.destroy_process_group()
         return 0
 
-    # ---- roofline of the dominant kernel class
+    # ---- roofline of the dominant kernel class (algorithmic work per launch)
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
+    FP64_PEAK = 1250.0   # GFLOP/s, GB300 FP64 rate (FMA microbenchmark: 1252)
     shares = {k: v["total_ms"] for k, v in prof.items()}
     tot = sum(shares.values()) or 1.0
-    dom = max(shares, key=shares.get)
-    per_iter_upd = p.N * p.K
-    # algorithmic work per launch group ("Kernels and their rooflines")
-    alg = {
-        "sweep": ("alu", 7.0 * per_iter_upd, 1250.0, "GFLOP/s"),     # 3 FMA + 1 MUL per update (pseudo-time on)
-        "moments": ("alu", 6.0 * per_iter_upd, 1250.0, "GFLOP/s"),   # 3 FMA per update (rho, Fx, Fy)
-        "synth": ("hbm", None, hbm, "GB/s"),
-        "hot_rhs": ("hbm", 15 * 8.0 * p.N, hbm, "GB/s"),
-        "update": ("hbm", 6 * 8.0 * p.N, hbm, "GB/s"),
-        "setup": ("hbm", None, hbm, "GB/s"),
-    }
-    bound, work, peak, unit = alg[dom]
-    groups = max(prof[dom]["timed"], 1)
-    avg_ms = prof[dom]["total_ms"] / groups
-    if dom == "synth":
-        # 10 doubles per cell per CG iteration, summed over the iterations each launch did
-        work = None
-    achieved = (work / (avg_ms * 1e-3) / 1e9) if work else None
-    roof = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak,
-            "unit": unit if bound != "alu" else "GFLOP/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": None,
-            "avg_launch_ms": avg_ms, "launch_groups": groups,
-            "share": {k: v / tot for k, v in shares.items()},
-            "peak_source": "measured hbm_gbs (MEASURED_PEAKS.json)" if bound == "hbm"
-            else "nominal FP64 1250 GFLOP/s (GB300 FP64 rate)"}
+    upd = p.N * p.K
+    inner_per_call = sum(inner) / max(1, sum(iters))
+
+    def model(cls):
+        g = max(prof[cls]["timed"], 1)
+        avg_ms = prof[cls]["total_ms"] / g
+        if cls == "sweep":       # 3 FMA + 1 MUL per update with the pseudo-time delta form
+            work, bound, peak, unit = 7.0 * upd, "alu", FP64_PEAK, "GFLOP/s"
+        elif cls == "moments":   # rho, Fx, Fy: 3 FMA per update
+            work, bound, peak, unit = 6.0 * upd, "alu", FP64_PEAK, "GFLOP/s"
+        elif cls == "synth":     # 200 B/cell per FP32 MG-CG iteration + 64 B/cell FP64 refinement
+            work, bound, peak, unit = (200.0 * inner_per_call + 64.0) * p.N, "hbm", hbm, "GB/s"
+        elif cls == "hot_rhs":
+            work, bound, peak, unit = 15 * 8.0 * p.N, "hbm", hbm, "GB/s"
+        else:
+            work, bound, peak, unit = 6 * 8.0 * p.N, "hbm", hbm, "GB/s"
+        ach = work / (avg_ms * 1e-3) / 1e9
+        return {"bound": bound, "kernel": cls, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+                "avg_launch_ms": avg_ms, "launch_groups": g}
+
+    dom = max(("sweep", "moments", "synth"), key=lambda k: shares[k])
+    roof = model(dom)
+    roof.update({"traffic": None, "share": {k: v / tot for k, v in shares.items()},
+                 "peak_source": ("measured hbm_gbs (MEASURED_PEAKS.json)" if roof["bound"] == "hbm"
+                                 else "GB300 FP64 rate 1.25 TFLOP/s (nominal; FMA microbenchmark 1.25)"),
+                 "others": {k: model(k) for k in ("sweep", "moments", "synth") if k != dom}})
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -289,7 +299,8 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": n_ranks, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
-            "time_to_converge": {"gsis": {"s": total_ms / args.steps * 1e-3, "iters": iters[0]}, "si": si},
+            "time_to_converge": {"gsis": {"s": total_ms / args.steps * 1e-3, "iters": iters[0],
+                                          "synth_inner_iters": inner[0]}, "si": si},
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(sum(v["kernels"] for v in prof.values())),
@@ -310,6 +321,8 @@ def main():
     ap.add_argument("--no-si", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--synth-cap", type=int, default=SYNTH_CAP,
+                    help="inner iterations of the synthetic solve per GSIS iteration (0: solve to 1e-12)")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

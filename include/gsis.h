@@ -238,6 +238,17 @@ int gsis_profile_enable(int enable);
 /* Copies min(n, GSIS_KCLASS_COUNT) entries (indexed by gsis_kernel_class). */
 int gsis_profile_read(gsis_kernel_stats* out, int n);
 
+/* Summary of the last gsis_solve() on this host thread (instrumentation). */
+typedef struct {
+    int iters;                    /* outer iterations done */
+    long long synth_inner_iters;  /* FP32 multigrid-CG iterations summed over the synthetic solves */
+    double err;                   /* final Err(rho) */
+    double synth_relres;          /* last synthetic relative residual (-1: budget spent, not evaluated) */
+} gsis_solve_info;
+
+/* Copies the summary of the last gsis_solve() of this thread; GSIS_ERR_ARG if out is NULL. */
+int gsis_last_solve_info(gsis_solve_info* out);
+
 /* Static description of a status code (never NULL). */
 const char* gsis_status_string(int status);
 

@@ -23,6 +23,7 @@ using namespace gsis;
 namespace {
 
 thread_local std::string g_last_error;
+thread_local gsis_solve_info g_last_info{};
 
 int fail(int code, const char* fmt, ...)
 {
@@ -157,6 +158,35 @@ size_t layout(const Sizes& z, char* base, Plan* P)
     double** syn[] = {&p.diag, &p.cx, &p.cy, &p.hotx, &p.hoty, &p.b, &p.x, &p.r, &p.z, &p.p, &p.qv};
     for (double** d : syn) *d = reinterpret_cast<double*>(take(N * sizeof(double)));
     p.partials = reinterpret_cast<double*>(take(11 * (size_t)kMaxCgBlocks * sizeof(double)));
+    // multigrid hierarchy: 2x2 aggregation down to a single cell
+    {
+        MgPlan& g = p.mg;
+        int lx = z.nx, ly = z.ny, l = 0;
+        for (;;) {
+            g.nx[l] = lx;
+            g.ny[l] = ly;
+            const size_t n = (size_t)lx * ly;
+            g.d64[l] = reinterpret_cast<double*>(take(n * sizeof(double)));
+            g.cx64[l] = reinterpret_cast<double*>(take(n * sizeof(double)));
+            g.cy64[l] = reinterpret_cast<double*>(take(n * sizeof(double)));
+            g.d[l] = reinterpret_cast<float*>(take(n * sizeof(float)));
+            g.cx[l] = reinterpret_cast<float*>(take(n * sizeof(float)));
+            g.cy[l] = reinterpret_cast<float*>(take(n * sizeof(float)));
+            g.x[l] = reinterpret_cast<float*>(take(n * sizeof(float)));
+            g.t[l] = reinterpret_cast<float*>(take(n * sizeof(float)));
+            g.r[l] = reinterpret_cast<float*>(take(n * sizeof(float)));
+            ++l;
+            if (n == 1 || l == kMaxLevels) break;
+            lx = (lx + 1) / 2;
+            ly = (ly + 1) / 2;
+        }
+        g.nl = l;
+        g.local_from = l - 1;
+        for (int k = 0; k < l; ++k)
+            if ((size_t)g.nx[k] * g.ny[k] <= 4 * (size_t)kMgBlock) { g.local_from = k; break; }
+        float** v[] = {&g.r0, &g.dl, &g.s, &g.p, &g.q};
+        for (float** f : v) *f = reinterpret_cast<float*>(take(N * sizeof(float)));
+    }
     p.hist = reinterpret_cast<double*>(take((size_t)std::max(1, z.hist) * sizeof(double)));
     return off;
 }
@@ -253,8 +283,7 @@ int prepare(Plan& P, const gsis_mesh* mesh, const gsis_quadrature* quad, const g
         P.sweep_grid = (int)std::max(1LL, std::min<long long>((long long)per_sm * P.num_sms,
                                                             (units + kSweepWarps - 1) / kSweepWarps));
     }
-    const int cg_per_sm = std::max(1, cg_max_active_blocks());
-    P.cg_grid = std::max(1, std::min({cg_per_sm * P.num_sms, kMaxCgBlocks, (P.N + kRedBlock - 1) / kRedBlock}));
+    P.mg.cluster = mg_cluster_size();
     P.red_grid = std::max(1, std::min({P.num_sms * 8, kMaxCgBlocks, (P.N + kRedBlock - 1) / kRedBlock}));
 
     CK(cudaMemsetAsync(P.status, 0, sizeof(Status), st));
@@ -292,6 +321,8 @@ int prepare(Plan& P, const gsis_mesh* mesh, const gsis_quadrature* quad, const g
         TIMED(GSIS_KCLASS_SETUP, 1, launch_setup(P, st));
     }
     TIMED(GSIS_KCLASS_SETUP, P.fp32 ? 1 : 2, launch_cell_setup(P, opt->cfl_p, opt->beta, st));
+    if (P.scheme == GSIS_SCHEME_GSIS || P.K == 0)
+        TIMED(GSIS_KCLASS_SETUP, P.mg.nl, launch_mg_setup(P, st));
     return GSIS_OK;
 }
 
@@ -362,6 +393,13 @@ const char* gsis_status_string(int s)
 }
 
 const char* gsis_last_error(void) { return g_last_error.c_str(); }
+
+int gsis_last_solve_info(gsis_solve_info* out)
+{
+    if (!out) return GSIS_ERR_ARG;
+    *out = g_last_info;
+    return GSIS_OK;
+}
 
 int gsis_profile_enable(int enable)
 {
@@ -448,6 +486,10 @@ int gsis_solve(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis_op
     if ((rc = read_status(S, P, st))) return rc;
     if (history && S.iter > 0)
         CK(cudaMemcpy(history, P.hist, (size_t)S.iter * sizeof(double), cudaMemcpyDeviceToHost));
+    g_last_info.iters = S.iter;
+    g_last_info.synth_inner_iters = S.synth_iters_total;
+    g_last_info.err = S.err;
+    g_last_info.synth_relres = S.synth_relres;
     if (iters_out) *iters_out = S.iter;
     if (err_out) *err_out = S.err;
     if (S.reason == kDiverged) return fail(GSIS_ERR_DIVERGED, "Err = %g after %d iterations", S.err, S.iter);

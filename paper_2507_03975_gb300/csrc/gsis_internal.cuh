@@ -15,7 +15,9 @@ constexpr int kMaxK = 4096;            // directions per quadrature (host-side c
 constexpr int kMaxSide = (1 << 20) - 1; // cells per mesh side (edge-flag encoding)
 constexpr int kSweepWarps = 4;          // warps per sweep CTA
 constexpr int kRedBlock = 256;          // threads per reduction / stencil block
-constexpr int kMaxCgBlocks = 1024;      // cooperative synthetic-solve CTAs (partials capacity)
+constexpr int kMaxCgBlocks = 1024;      // partials capacity of the fixed-order grid reductions
+constexpr int kMaxLevels = 24;          // multigrid levels (2x2 aggregation down to one cell)
+constexpr int kMgBlock = 1024;          // threads per CTA of the synthetic-solve cluster
 
 // device error bits (Status::error)
 constexpr int kErrTimeout = 1;
@@ -40,6 +42,16 @@ struct Status {
     long long synth_iters_total;      // summed over the solve
     double err;                       // last Err(rho)
     double synth_relres;              // last synthetic relative residual
+};
+
+// Multigrid hierarchy of the synthetic operator (level 0 = the mesh).
+struct MgPlan {
+    int nl, local_from, cluster;
+    int nx[kMaxLevels], ny[kMaxLevels];
+    double* d64[kMaxLevels]; double* cx64[kMaxLevels]; double* cy64[kMaxLevels];
+    float* d[kMaxLevels]; float* cx[kMaxLevels]; float* cy[kMaxLevels];
+    float* x[kMaxLevels]; float* t[kMaxLevels]; float* r[kMaxLevels];
+    float* r0; float* dl; float* s; float* p; float* q;
 };
 
 // Everything a kernel needs, carved from the caller's workspace (device
@@ -90,6 +102,7 @@ struct Plan {
     double* partials;               // reductions scratch
     double* hist;                   // [max_iter]
     Status* status;
+    MgPlan mg;
 };
 
 // ------------------------------------------------------------ launchers
@@ -103,11 +116,12 @@ cudaError_t launch_moments_to(const Plan& P, bool with_F, bool with_P, double* r
                               cudaStream_t st);                    // rho, F, (P), boundary flux
 cudaError_t prepare_kernels(int K, int fp32, int pt);
 int sweep_max_active_blocks(int fp32, int pt);
-int cg_max_active_blocks();
 cudaError_t launch_source_from(const Plan& P, const double* rho_in, cudaStream_t st);
 cudaError_t launch_hot_rhs(const Plan& P, const double* rho_h, const double* Fx, const double* Fy,
                            const double* fb, cudaStream_t st);
+cudaError_t launch_mg_setup(const Plan& P, cudaStream_t st);
 cudaError_t launch_synthetic_solve(const Plan& P, const double* guess, double* out, cudaStream_t st);
+int mg_cluster_size();
 cudaError_t launch_update(const Plan& P, const double* rho_new, cudaStream_t st);
 
 int device_sm_count();

@@ -190,18 +190,56 @@ struct SweepArgs {
 __device__ __forceinline__ double rcp_t(double d) { return 1.0 / d; }
 __device__ __forceinline__ float rcp_t(float d) { return __frcp_rn(d); }
 
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Shared-memory plan of one sweep warp (all sizes in elements of T unless
+// noted).  Per-lane windows hold, for the SEG steps of a chunk, the cell data
+// of the lane's own row (padded rows: conflict-free column access); the
+// column-coefficient window covers the SEG + 31 columns the skewed lanes
+// touch in a chunk; the 1/d table chunk is SEG x 32 doubles in step order.
 template <typename T, bool PT, bool PRE>
-__global__ void __launch_bounds__(kSweepWarps * 32)
+struct SweepSmem {
+    static constexpr int SEG = 128 / (int)sizeof(T);
+    static constexpr int RING = 4 * SEG;
+    static constexpr int RS = SEG + 1;
+    static constexpr int AW = SEG + 32;
+    static constexpr int NW = (PRE ? 1 : 2) + (PT ? 2 : 0);   // src, [sigt], [shift, I^m]
+    static constexpr int W_SRC = 0;                           // window slots
+    static constexpr int W_SIGT = 1;                          // FP32 only (no 1/d table)
+    static constexpr int W_SHIFT = PRE ? 1 : 2;               // pseudo-time only
+    static constexpr int W_IOLD = PRE ? 2 : 3;                // pseudo-time only
+    static constexpr int STAGE = 32 * RING;
+    static constexpr int WIN = 32 * RS;
+    static constexpr size_t warp_bytes =
+        sizeof(T) * (size_t)(STAGE + 2 * NW * WIN + 2 * AW) + (PRE ? 2 * (size_t)SEG * 32 * sizeof(double) : 0);
+    static constexpr size_t bytes = kSweepWarps * ((warp_bytes + 15) / 16 * 16);
+};
+
+template <typename T, bool PT, bool PRE>
+__global__ void __launch_bounds__(kSweepWarps * 32, 1)
 sweep_kernel(const SweepArgs<T> a)
 {
-    constexpr int SEG = 128 / (int)sizeof(T);   // columns per 128-byte row segment
-    constexpr int RING = 4 * SEG;               // staged columns per row
+    using SM = SweepSmem<T, PT, PRE>;
+    constexpr int SEG = SM::SEG, RING = SM::RING, RS = SM::RS, AW = SM::AW, NW = SM::NW;
     constexpr int LAG = (31 + SEG - 1) / SEG;   // segments a row band lags behind lane 0
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* stage = reinterpret_cast<T*>(smem_raw) + (threadIdx.x >> 5) * (32 * RING);
+    unsigned char* wbase = smem_raw + (threadIdx.x >> 5) * ((SM::warp_bytes + 15) / 16 * 16);
+    double* win_r = reinterpret_cast<double*>(wbase);                       // [2][SEG*32] (PRE)
+    T* stage = reinterpret_cast<T*>(wbase + (PRE ? 2 * SEG * 32 * sizeof(double) : 0));
+    T* win = stage + SM::STAGE;                                             // [2][NW][32*RS]
+    T* win_a = win + 2 * NW * SM::WIN;                                      // [2][AW]
     const int lane = threadIdx.x & 31;
     const int nx = a.nx, ny = a.ny, K = a.K, nb = a.nb;
     const unsigned ntasks = (unsigned)(K * nb);
+    const int nchunks = (a.nsteps + SEG - 1) / SEG;
 
     int stop = 0;
     if (lane == 0) stop = ld_volatile_int(a.done);
@@ -224,7 +262,6 @@ sweep_kernel(const SweepArgs<T> a)
         const int jl = band * 32 + lane;
         const bool row_ok = jl < ny;
         const int j = ypos ? jl : ny - 1 - jl;
-        const size_t rowoff = (size_t)(row_ok ? j : 0) * nx;
         const T bj = row_ok ? a.bcoef[(size_t)s * ny + j] : T(0);
         const T* arow = a.acoef + (size_t)s * nx;
         T* Is = a.I + (size_t)s * a.N;
@@ -233,6 +270,45 @@ sweep_kernel(const SweepArgs<T> a)
         const T* edge_in = a.edge + ((size_t)s * nb + band - 1) * nx;
         unsigned long long* flag_out = a.flags + (size_t)s * nb + band;
         const unsigned long long* flag_in = a.flags + (size_t)s * nb + band - 1;
+        const T* wsrc[NW];
+        wsrc[SM::W_SRC] = a.src;
+        if (!PRE) wsrc[SM::W_SIGT] = a.sigt;
+        if (PT) {
+            wsrc[SM::W_SHIFT] = a.shift;
+            wsrc[SM::W_IOLD] = Is;
+        }
+
+        // Issue the asynchronous copies of chunk m into buffer b.
+        auto prefetch = [&](int m, int b) {
+            const int t0 = m * SEG;
+            T* wb = win + b * NW * SM::WIN;
+            // row r of the band needs columns t0 - r .. t0 - r + SEG - 1: the
+            // warp copies 32/SEG rows per instruction, SEG consecutive cells each
+            constexpr int RPI = 32 / SEG;
+            const int kk = lane % SEG;
+#pragma unroll 4
+            for (int r0 = 0; r0 < 32; r0 += RPI) {
+                const int r = r0 + lane / SEG;
+                const int jr = band * 32 + r;
+                const int c = t0 + kk - r;
+                if (jr < ny && c >= 0 && c < nx) {
+                    const size_t cell = (size_t)(ypos ? jr : ny - 1 - jr) * nx + (xpos ? c : nx - 1 - c);
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) cp_async<sizeof(T)>(wb + w * SM::WIN + r * RS + kk, wsrc[w] + cell);
+                }
+            }
+            T* ab = win_a + b * AW;
+            for (int u = lane; u < SEG + 31; u += 32) {
+                const int c = t0 - 31 + u;
+                if (c >= 0 && c < nx) cp_async<sizeof(T)>(ab + u, arow + (xpos ? c : nx - 1 - c));
+            }
+            if (PRE) {
+                const int nv = min(SEG, a.nsteps - t0) * 32;   // doubles, multiple of 32
+                double* rb = win_r + b * SEG * 32;
+                for (int v = 2 * lane; v < nv; v += 64) cp_async<16>(rb + v, rrow + (size_t)t0 * 32 + v);
+            }
+            cp_async_commit();
+        };
 
         T IW = T(0);
         if (row_ok && a.inflow) {
@@ -258,7 +334,11 @@ sweep_kernel(const SweepArgs<T> a)
             }
         };
 
-        for (int t0 = 0; t0 < a.nsteps; t0 += SEG) {
+        prefetch(0, 0);
+        for (int m = 0; m < nchunks; ++m) {
+            const int t0 = m * SEG, b = m & 1;
+            if (m + 1 < nchunks) prefetch(m + 1, b ^ 1);
+            else cp_async_commit();   // empty group keeps the wait count uniform
             // south values of lane 0 for columns t0 .. t0+SEG-1, one per lane
             if (t0 < nx) {
                 edge_reg = T(0);
@@ -276,10 +356,18 @@ sweep_kernel(const SweepArgs<T> a)
                         ok = wait_at_least(flag_in, need, a.wait_cycles, a.err) ? 1 : 0;
                     }
                     ok = __shfl_sync(kFull, ok, 0);
-                    if (!ok) return;
+                    if (!ok) {
+                        cp_async_wait<0>();   // no copy of ours stays in flight
+                        return;
+                    }
                     if (lane < SEG && t0 + lane < nx) edge_reg = __ldcg(edge_in + t0 + lane);
                 }
             }
+            cp_async_wait<1>();   // chunk m has landed
+            __syncwarp();
+            const T* wb = win + b * NW * SM::WIN + lane * RS;
+            const T* ab = win_a + b * AW + 31 - lane;
+            const double* rb = win_r + b * SEG * 32 + lane;
 #pragma unroll 4
             for (int tt = 0; tt < SEG; ++tt) {
                 const int t = t0 + tt;
@@ -290,21 +378,23 @@ sweep_kernel(const SweepArgs<T> a)
                 const int c = t - lane;
                 T Inew = T(0);
                 if (row_ok && c >= 0 && c < nx) {
-                    const int i = xpos ? c : nx - 1 - c;
-                    const size_t cell = rowoff + i;
-                    T sv = a.src[cell];
-                    if (PT) sv = fma(a.shift[cell], Is[cell], sv);
-                    const T ai = arow[i];
-                    T acc = fma(ai, IW, sv);
-                    acc = fma(bj, Isouth, acc);
+                    T sv = wb[SM::W_SRC * SM::WIN + tt];
+                    const T ai = ab[tt];
                     T rinv;
                     if (PRE) {
-                        rinv = (T)rrow[(size_t)t * 32 + lane];
+                        if (PT) sv = fma(wb[SM::W_SHIFT * SM::WIN + tt], wb[SM::W_IOLD * SM::WIN + tt], sv);
+                        rinv = (T)rb[tt * 32];
                     } else {
-                        T d = a.sigt[cell] + ai + bj;
-                        if (PT) d += a.shift[cell];
+                        T d = wb[SM::W_SIGT * SM::WIN + tt] + ai + bj;
+                        if (PT) {
+                            const T sh = wb[SM::W_SHIFT * SM::WIN + tt];
+                            sv = fma(sh, wb[SM::W_IOLD * SM::WIN + tt], sv);
+                            d += sh;
+                        }
                         rinv = rcp_t(d);
                     }
+                    T acc = fma(ai, IW, sv);
+                    acc = fma(bj, Isouth, acc);
                     Inew = acc * rinv;
                     IW = Inew;
                     stage[lane * RING + (c & (RING - 1))] = Inew;
@@ -320,13 +410,14 @@ sweep_kernel(const SweepArgs<T> a)
                 }
             }
             __syncwarp();
-            const int last_complete = t0 / SEG - LAG;
+            const int last_complete = m - LAG;
             while (flushed <= last_complete && flushed * SEG < nx) {
                 flush(flushed);
                 ++flushed;
             }
             __syncwarp();
         }
+        cp_async_wait<0>();
         while (flushed * SEG < nx) {
             flush(flushed);
             ++flushed;
@@ -372,6 +463,7 @@ __global__ void __launch_bounds__(kRedBlock) moments_kernel(const MomArgs<T> a)
     __syncthreads();
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < a.N; c += gridDim.x * blockDim.x) {
         T r = T(0), fx = T(0), fy = T(0), pxx = T(0), pxy = T(0), pyy = T(0);
+#pragma unroll 4
         for (int k = 0; k < a.K; ++k) {
             const T v = a.I[(size_t)sk[k] * a.N + c];
             r = fma(cf[6 * k + 0], v, r);
@@ -405,16 +497,19 @@ __global__ void __launch_bounds__(kRedBlock) moments_kernel(const MomArgs<T> a)
 }
 
 // Kinetic net flux through every boundary face, sum_k w_k (Omega_k . n) I_face,k
-// (outgoing: boundary cell intensity, incoming: inflow).
+// (outgoing: boundary cell intensity, incoming: inflow).  One warp per face;
+// lane l sums k = l, l+32, ... in order, then a fixed shuffle tree.
 template <typename T>
-__global__ void bflux_kernel(int nx, int ny, int K, const T* __restrict__ I, const int* __restrict__ sidx,
-                             const double* __restrict__ mu, const double* __restrict__ eta,
-                             const double* __restrict__ w, const double* __restrict__ inflow,
-                             double* fb, const int* done)
+__global__ void __launch_bounds__(256) bflux_kernel(int nx, int ny, int K, const T* __restrict__ I,
+                                                    const int* __restrict__ sidx, const double* __restrict__ mu,
+                                                    const double* __restrict__ eta, const double* __restrict__ w,
+                                                    const double* __restrict__ inflow, double* fb, const int* done)
 {
     if (done && ld_volatile_int(done)) return;
     const int nbf = 2 * (nx + ny), N = nx * ny;
-    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nbf; f += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int f = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; f < nbf; f += warps) {
         int c, axis;
         double sgn;
         if (f < ny) { c = nx * f; axis = 0; sgn = -1.0; }
@@ -422,14 +517,15 @@ __global__ void bflux_kernel(int nx, int ny, int K, const T* __restrict__ I, con
         else if (f < 2 * ny + nx) { c = f - 2 * ny; axis = 1; sgn = -1.0; }
         else { c = (f - 2 * ny - nx) + nx * (ny - 1); axis = 1; sgn = 1.0; }
         T acc = T(0);
-        for (int k = 0; k < K; ++k) {
+        for (int k = lane; k < K; k += 32) {
             const double on = sgn * (axis == 0 ? mu[k] : eta[k]);
             T Iface;
             if (on >= 0.0) Iface = I[(size_t)sidx[k] * N + c];
             else Iface = inflow ? (T)inflow[(size_t)f * K + k] : T(0);
             acc = fma((T)(w[k] * on), Iface, acc);
         }
-        fb[f] = (double)acc;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+        if (lane == 0) fb[f] = (double)acc;
     }
 }
 
@@ -441,7 +537,7 @@ int grid_for(long long n, int block, int cap)
     return (int)g;
 }
 
-template <typename T>
+template <typename T, bool PT>
 size_t sweep_smem();
 
 template <typename T, bool PT, bool PRE>
@@ -466,7 +562,7 @@ cudaError_t launch_sweep_t(Plan& P, cudaStream_t st)
     a.err = &P.status->error;
     a.done = &P.status->done;
     a.wait_cycles = P.wait_cycles;
-    sweep_kernel<T, PT, PRE><<<P.sweep_grid, kSweepWarps * 32, sweep_smem<T>(), st>>>(a);
+    sweep_kernel<T, PT, PRE><<<P.sweep_grid, kSweepWarps * 32, sweep_smem<T, PT>(), st>>>(a);
     return cudaGetLastError();
 }
 
@@ -501,26 +597,26 @@ cudaError_t launch_moments_t(const Plan& P, bool with_F, bool with_P, double* rh
     else moments_kernel<T, false, false><<<grid, kRedBlock, smem, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    bflux_kernel<T><<<grid_for(P.nbf, 128, 64), 128, 0, st>>>(
+    bflux_kernel<T><<<grid_for((long long)P.nbf * 32, 256, P.num_sms * 4), 256, 0, st>>>(
         P.nx, P.ny, P.K, static_cast<const T*>(P.I), P.sidx, a.mu, a.eta, a.w, P.inflow, fb_out, a.done);
     return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, bool PT>
 size_t sweep_smem()
 {
-    return (size_t)kSweepWarps * 32 * 4 * (128 / sizeof(T)) * sizeof(T);
+    return SweepSmem<T, PT, sizeof(T) == 8>::bytes;
 }
 
 template <typename T>
 cudaError_t prepare_t(int K)
 {
     cudaError_t e;
-    const int ss = (int)sweep_smem<T>(), ms = (int)moments_smem<T>(K);
-    if ((e = cudaFuncSetAttribute(sweep_kernel<T, false, sizeof(T) == 8>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, ss)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(sweep_kernel<T, true, sizeof(T) == 8>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, ss)) != cudaSuccess) return e;
+    const int ms = (int)moments_smem<T>(K);
+    if ((e = cudaFuncSetAttribute(sweep_kernel<T, false, sizeof(T) == 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sweep_smem<T, false>())) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(sweep_kernel<T, true, sizeof(T) == 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sweep_smem<T, true>())) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(moments_kernel<T, true, true>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, ms)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(moments_kernel<T, true, false>,
@@ -533,7 +629,7 @@ int sweep_occupancy()
 {
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<T, PT, sizeof(T) == 8>, kSweepWarps * 32,
-                                                      sweep_smem<T>()) != cudaSuccess)
+                                                      sweep_smem<T, PT>()) != cudaSuccess)
         return 0;
     return n;
 }

@@ -11,17 +11,11 @@
 //    F_iw^init + beta (rho_i - rho_i^{m+1/2}) (Eqs. (macro_bc_delta_flux),
 //    (macro_bc_delta_flux2)):
 //      b_i = V_i q_i - sum_int A (HoT_i + HoT_j)/2 . n - sum_bnd A (F_iw.n - beta rho_i^{m+1/2}).
-//  * Solve D rho = b (Eqs. (MSE_d1), (elem_mtx_M)), D symmetric positive
-//    definite 5-point, by Jacobi-preconditioned conjugate gradients in ONE
-//    cooperative kernel; every reduction is a fixed-order sum, so results are
-//    bit-reproducible and every CTA takes the same branch.
+//  * (the solve of D rho = b is in mg.cu)
 //  * Err(rho) (Eq. (Err_W)), convergence decision, next angular source.
-#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "gsis_internal.cuh"
-
-namespace cg = cooperative_groups;
 
 namespace gsis {
 
@@ -100,128 +94,6 @@ __global__ void rhs_kernel(int nx, int ny, const double* __restrict__ dx, const 
         if (j == 0) v -= hx * (fb[2 * ny + i] - by * rh);
         if (j == ny - 1) v -= hx * (fb[2 * ny + nx + i] - by * rh);
         b[c] = v;
-    }
-}
-
-struct CgArgs {
-    int nx, ny, N, max_iter;
-    double rtol;
-    const double* diag; const double* cx; const double* cy; const double* b;
-    const double* guess;
-    double* x; double* r; double* z; double* p; double* qv;
-    double* partials;           // [3 slots][3][gridDim]
-    Status* status;
-};
-
-__device__ __forceinline__ double apply_D(const double* __restrict__ diag, const double* __restrict__ cx,
-                                          const double* __restrict__ cy, const double* v, int c, int nx,
-                                          int ny)
-{
-    const int j = c / nx, i = c - j * nx;
-    double y = diag[c] * __ldcg(v + c);
-    if (i + 1 < nx) y -= cx[c] * __ldcg(v + c + 1);
-    if (i > 0) y -= cx[c - 1] * __ldcg(v + c - 1);
-    if (j + 1 < ny) y -= cy[c] * __ldcg(v + c + nx);
-    if (j > 0) y -= cy[c - nx] * __ldcg(v + c - nx);
-    return y;
-}
-
-// Writes the block sums of (a0, a1, a2) into slot `slot`, synchronises the
-// grid and returns the global fixed-order sums (same bits in every CTA).
-__device__ __forceinline__ void grid_sum3(cg::grid_group& grid, double* partials, int slot, double a0,
-                                          double a1, double a2, double* sm, double out[3])
-{
-    const int G = gridDim.x;
-    double* base = partials + (size_t)slot * 3 * G;
-    a0 = block_sum(a0, sm);
-    a1 = block_sum(a1, sm);
-    a2 = block_sum(a2, sm);
-    if (threadIdx.x == 0) {
-        base[blockIdx.x] = a0;
-        base[G + blockIdx.x] = a1;
-        base[2 * G + blockIdx.x] = a2;
-    }
-    grid.sync();
-    __shared__ double res[3];
-    if (threadIdx.x < 32) {
-        const double s0 = warp_sum_array(base, G);
-        const double s1 = warp_sum_array(base + G, G);
-        const double s2 = warp_sum_array(base + 2 * G, G);
-        if (threadIdx.x == 0) {
-            res[0] = s0;
-            res[1] = s1;
-            res[2] = s2;
-        }
-    }
-    __syncthreads();
-    out[0] = res[0];
-    out[1] = res[1];
-    out[2] = res[2];
-    __syncthreads();
-}
-
-__global__ void __launch_bounds__(kRedBlock) cg_kernel(const CgArgs a)
-{
-    cg::grid_group grid = cg::this_grid();
-    __shared__ double sm[33];
-    if (ld_volatile_int(&a.status->done)) return;   // uniform: set by an earlier kernel
-    const int N = a.N, nx = a.nx, ny = a.ny;
-    const int t0 = blockIdx.x * blockDim.x + threadIdx.x, ts = gridDim.x * blockDim.x;
-    for (int c = t0; c < N; c += ts) a.x[c] = a.guess[c];
-    grid.sync();
-    double loc0 = 0.0, loc1 = 0.0, loc2 = 0.0, sums[3];
-    for (int c = t0; c < N; c += ts) {
-        const double rc = a.b[c] - apply_D(a.diag, a.cx, a.cy, a.x, c, nx, ny);
-        const double zc = rc / a.diag[c];
-        a.r[c] = rc;
-        a.z[c] = zc;
-        a.p[c] = zc;
-        loc0 += rc * zc;
-        loc1 += rc * rc;
-        loc2 += a.b[c] * a.b[c];
-    }
-    int slot = 0;
-    grid_sum3(grid, a.partials, slot, loc0, loc1, loc2, sm, sums);   // also publishes p
-    double rz = sums[0], rr = sums[1];
-    const double bb = sums[2];
-    const double stop2 = a.rtol * a.rtol * bb;
-    int it = 0;
-    while (rr > stop2 && it < a.max_iter && rz > 0.0) {
-        // q = D p, p.q
-        loc0 = 0.0;
-        for (int c = t0; c < N; c += ts) {
-            const double qc = apply_D(a.diag, a.cx, a.cy, a.p, c, nx, ny);
-            a.qv[c] = qc;
-            loc0 += __ldcg(a.p + c) * qc;
-        }
-        slot = (slot + 1) % 3;
-        grid_sum3(grid, a.partials, slot, loc0, 0.0, 0.0, sm, sums);
-        const double alpha = rz / sums[0];
-        loc0 = 0.0;
-        loc1 = 0.0;
-        for (int c = t0; c < N; c += ts) {
-            const double pc = __ldcg(a.p + c);
-            a.x[c] += alpha * pc;
-            const double rc = a.r[c] - alpha * a.qv[c];
-            const double zc = rc / a.diag[c];
-            a.r[c] = rc;
-            a.z[c] = zc;
-            loc0 += rc * zc;
-            loc1 += rc * rc;
-        }
-        slot = (slot + 1) % 3;
-        grid_sum3(grid, a.partials, slot, loc0, loc1, 0.0, sm, sums);
-        const double beta = sums[0] / rz;
-        rz = sums[0];
-        rr = sums[1];
-        for (int c = t0; c < N; c += ts) a.p[c] = a.z[c] + beta * __ldcg(a.p + c);
-        grid.sync();
-        ++it;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        a.status->synth_iters = it;
-        a.status->synth_iters_total += it;
-        a.status->synth_relres = bb > 0.0 ? sqrt(rr / bb) : 0.0;
     }
 }
 
@@ -313,25 +185,6 @@ cudaError_t launch_hot_rhs(const Plan& P, const double* rho_h, const double* Fx,
     rhs_kernel<<<g, 256, 0, st>>>(P.nx, P.ny, P.dx, P.dy, P.sigt, P.q, rho_h, P.hotx, P.hoty, fb, P.b,
                                   &P.status->done);
     return cudaGetLastError();
-}
-
-cudaError_t launch_synthetic_solve(const Plan& P, const double* guess, double* out, cudaStream_t st)
-{
-    CgArgs a{};
-    a.nx = P.nx; a.ny = P.ny; a.N = P.N; a.max_iter = P.synth_max_iter; a.rtol = P.synth_rtol;
-    a.diag = P.diag; a.cx = P.cx; a.cy = P.cy; a.b = P.b; a.guess = guess;
-    a.x = out; a.r = P.r; a.z = P.z; a.p = P.p; a.qv = P.qv;
-    a.partials = P.partials;
-    a.status = P.status;
-    void* args[] = {&a};
-    return cudaLaunchCooperativeKernel((void*)cg_kernel, dim3(P.cg_grid), dim3(kRedBlock), args, 0, st);
-}
-
-int cg_max_active_blocks()
-{
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cg_kernel, kRedBlock, 0) != cudaSuccess) return 0;
-    return n;
 }
 
 cudaError_t launch_update(const Plan& P, const double* rho_new, cudaStream_t st)

@@ -53,6 +53,11 @@ class KernelStats(ctypes.Structure):
                 ("timed", ctypes.c_longlong), ("total_ms", ctypes.c_double)]
 
 
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("synth_inner_iters", ctypes.c_longlong),
+                ("err", ctypes.c_double), ("synth_relres", ctypes.c_double)]
+
+
 class Options(ctypes.Structure):
     _fields_ = [
         ("scheme", ctypes.c_int), ("precision", ctypes.c_int), ("tol", ctypes.c_double),
@@ -91,6 +96,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.gsis_synthetic_step.argtypes = [Mp, Op, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, ip, vp, sz, vp]
     lib.gsis_transport_sweep_static.argtypes = [Mp, Qp, Op, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.gsis_transport_sweep_static.restype = ctypes.c_int
+    lib.gsis_last_solve_info.argtypes = [ctypes.POINTER(SolveInfo)]
+    lib.gsis_last_solve_info.restype = ctypes.c_int
     lib.gsis_profile_enable.argtypes = [ctypes.c_int]
     lib.gsis_profile_enable.restype = ctypes.c_int
     lib.gsis_profile_read.argtypes = [ctypes.POINTER(KernelStats), ctypes.c_int]
@@ -229,8 +236,11 @@ def solve(dx, dy, mu, eta, w, sigma_a, sigma_s, q, inflow=None, options: Options
         _dev(rho), _dev(F), _dev(P), _hp(hist), ctypes.byref(iters), ctypes.byref(err),
         ctypes.c_void_p(workspace.data_ptr()), ctypes.c_size_t(workspace.numel()), _stream(stream))
     _raise(rc)
+    info = SolveInfo()
+    load().gsis_last_solve_info(ctypes.byref(info))
     return dict(rho=rho, F=F, P=P, iters=iters.value, err=err.value, history=hist[:iters.value],
-                status=rc, workspace=workspace)
+                status=rc, workspace=workspace, synth_inner_iters=int(info.synth_inner_iters),
+                synth_relres=info.synth_relres)
 
 
 def transport_sweep(dx, dy, mu, eta, w, sigma_a, sigma_s, q, rho_in, inflow=None,
