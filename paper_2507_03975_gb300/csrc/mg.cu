@@ -95,6 +95,7 @@ struct MgLevelDev {
 struct MgArgs {
     int nl, local_from;
     MgLevelDev lv[kMaxLevels];
+    int loff[kMaxLevels];   // float offsets of the local levels in dynamic shared memory
     int nx, ny, N;
     const double* diag; const double* cx; const double* cy;
     const double* b; const double* guess; double* x;
@@ -154,16 +155,11 @@ class ClusterCtx {
         (void)local_from;
     }
     __device__ void sync() { cl_.sync(); }
+    __device__ int rank() const { return rank_; }
     __device__ Range range(bool local) const
     {
         if (local) return Range{(int)threadIdx.x, (int)blockDim.x, rank_ == 0};
         return Range{rank_ * (int)blockDim.x + (int)threadIdx.x, nblk_ * (int)blockDim.x, true};
-    }
-    // barrier matching the level's distribution
-    __device__ void level_sync(bool local)
-    {
-        if (local) __syncthreads();
-        else cl_.sync();
     }
     // Fixed-order cluster-wide sums of two floats / two doubles; every CTA
     // gets the same bits.  Slots rotate so that no second barrier is needed.
@@ -237,25 +233,97 @@ class ClusterCtx {
     int rank_, nblk_;
 };
 
-// z = M^{-1} s: one V-cycle; input in lv[0].r, output in lv[0].t.
-__device__ void vcycle(const MgArgs& a, ClusterCtx& cx)
+__device__ __forceinline__ float apply_S(const MgLevelDev& L, const float* v, int c)
+{
+    const int j = c / L.nx, i = c - j * L.nx;
+    float y = L.d[c] * v[c];
+    if (i + 1 < L.nx) y -= L.cx[c] * v[c + 1];
+    if (i > 0) y -= L.cx[c - 1] * v[c - 1];
+    if (j + 1 < L.ny) y -= L.cy[c] * v[c + L.nx];
+    if (j > 0) y -= L.cy[c - L.nx] * v[c - L.nx];
+    return y;
+}
+
+// V-cycle over levels [l0, nl) inside one CTA, all data in its shared memory
+// (S[l] point into it): input S[l0].r, output S[l0].t.
+__device__ void vcycle_local(const MgLevelDev* S, int l0, int nl, int nu, float om, float alpha)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int l = l0; l < nl - 1; ++l) {
+        const MgLevelDev& L = S[l];
+        const int n = L.nx * L.ny;
+        float* cur = L.x;
+        float* oth = L.t;
+        for (int c = tid; c < n; c += nt) cur[c] = om * L.r[c] / L.d[c];
+        for (int k = 1; k < nu; ++k) {
+            __syncthreads();
+            for (int c = tid; c < n; c += nt) oth[c] = cur[c] + om * (L.r[c] - apply_S(L, cur, c)) / L.d[c];
+            float* tmp = cur;
+            cur = oth;
+            oth = tmp;
+        }
+        __syncthreads();
+        const MgLevelDev& C = S[l + 1];
+        const int nc = C.nx * C.ny;
+        for (int cc = tid; cc < nc; cc += nt) {
+            const int J = cc / C.nx, I = cc - J * C.nx;
+            float sum = 0.f;
+            for (int q = 0; q < 4; ++q) {
+                const int i = 2 * I + (q & 1), j = 2 * J + (q >> 1);
+                if (i < L.nx && j < L.ny) {
+                    const int c = j * L.nx + i;
+                    sum += L.r[c] - apply_S(L, cur, c);
+                }
+            }
+            C.r[cc] = sum;
+        }
+        __syncthreads();
+    }
+    {
+        const MgLevelDev& L = S[nl - 1];
+        for (int c = tid; c < L.nx * L.ny; c += nt) L.t[c] = L.r[c] / L.d[c];
+        __syncthreads();
+    }
+    for (int l = nl - 2; l >= l0; --l) {
+        const MgLevelDev& L = S[l];
+        const MgLevelDev& C = S[l + 1];
+        const int n = L.nx * L.ny;
+        float* cur = (nu % 2) ? L.x : L.t;
+        float* oth = (nu % 2) ? L.t : L.x;
+        for (int c = tid; c < n; c += nt) {
+            const int j = c / L.nx, i = c - j * L.nx;
+            cur[c] += alpha * C.t[(j / 2) * C.nx + i / 2];
+        }
+        for (int k = 0; k < nu; ++k) {
+            __syncthreads();
+            for (int c = tid; c < n; c += nt) oth[c] = cur[c] + om * (L.r[c] - apply_S(L, cur, c)) / L.d[c];
+            float* tmp = cur;
+            cur = oth;
+            oth = tmp;
+        }
+        __syncthreads();
+    }
+}
+
+// z = M^{-1} s: one V-cycle; input in lv[0].r, output in lv[0].t.  Levels
+// above local_from are spread over the cluster (L2 data, cluster barriers);
+// the rest run in CTA 0 on its shared-memory copy S.
+__device__ void vcycle(const MgArgs& a, const MgLevelDev* S, ClusterCtx& cx)
 {
     constexpr int U = 4;
-    const int nl = a.nl;
+    const int nl = a.nl, lf = a.local_from;
     const float om = a.omega;
-    // ---- down
-    for (int l = 0; l < nl - 1; ++l) {
+    const Range R = cx.range(false);
+    // ---- down over the distributed levels
+    for (int l = 0; l < lf; ++l) {
         const MgLevelDev& L = a.lv[l];
-        const bool local = l >= a.local_from;
-        if (l == a.local_from) cx.sync();   // hand the restricted residual to CTA 0
-        const Range R = cx.range(local);
         const int n = L.nx * L.ny;
         float* cur = L.x;
         float* oth = L.t;
         for_cells<U>(R, n, [&](int c) { return om * ld(L.r + c) / L.d[c]; },
                      [&](int c, float v) { cur[c] = v; });
         for (int k = 1; k < a.nu; ++k) {
-            cx.level_sync(local);
+            cx.sync();
             float* src = cur;
             for_cells<U>(R, n,
                          [&](int c) { return ld(src + c) + om * (ld(L.r + c) - apply_A(L, src, c)) / L.d[c]; },
@@ -264,14 +332,10 @@ __device__ void vcycle(const MgArgs& a, ClusterCtx& cx)
             cur = oth;
             oth = tmp;
         }
-        cx.level_sync(local);
-        // restrict the residual: coarse cell = sum of its children's residuals
+        cx.sync();
         const MgLevelDev& C = a.lv[l + 1];
-        const bool clocal = (l + 1) >= a.local_from;
-        const Range RC = cx.range(clocal && local);
-        const int nc = C.nx * C.ny;
         const float* fin = cur;
-        for_cells<U>(RC, nc,
+        for_cells<U>(R, C.nx * C.ny,
                      [&](int cc) {
                          const int J = cc / C.nx, I = cc - J * C.nx;
                          float sum = 0.f;
@@ -286,25 +350,24 @@ __device__ void vcycle(const MgArgs& a, ClusterCtx& cx)
                          return sum;
                      },
                      [&](int cc, float v) { C.r[cc] = v; });
-        cx.level_sync(local);
+        cx.sync();   // the coarse residual is read by other threads next
     }
-    // ---- coarsest: exact (a single cell or the last level), result in t
-    {
-        const MgLevelDev& L = a.lv[nl - 1];
-        const bool local = (nl - 1) >= a.local_from;
-        if ((nl - 1) == a.local_from) cx.sync();
-        const Range R = cx.range(local);
-        for_cells<U>(R, L.nx * L.ny, [&](int c) { return ld(L.r + c) / L.d[c]; },
-                     [&](int c, float v) { L.t[c] = v; });
-        cx.level_sync(local);
+    if (lf == 0) cx.sync();   // level 0 itself is local: make the input visible to CTA 0
+    // ---- local levels in CTA 0's shared memory
+    if (cx.rank() == 0) {
+        const MgLevelDev& G = a.lv[lf];
+        const MgLevelDev& L = S[lf];
+        const int n = G.nx * G.ny;
+        for (int c = threadIdx.x; c < n; c += blockDim.x) L.r[c] = ld(G.r + c);
+        __syncthreads();
+        vcycle_local(S, lf, nl, a.nu, om, a.alpha);
+        for (int c = threadIdx.x; c < n; c += blockDim.x) G.t[c] = L.t[c];
     }
-    // ---- up
-    for (int l = nl - 2; l >= 0; --l) {
+    cx.sync();
+    // ---- up over the distributed levels
+    for (int l = lf - 1; l >= 0; --l) {
         const MgLevelDev& L = a.lv[l];
         const MgLevelDev& C = a.lv[l + 1];
-        const bool local = l >= a.local_from;
-        if (l == a.local_from - 1) cx.sync();   // coarse correction leaves CTA 0
-        const Range R = cx.range(local);
         const int n = L.nx * L.ny;
         float* cur = (a.nu % 2) ? L.x : L.t;   // buffer holding the pre-smoothed iterate
         float* oth = (a.nu % 2) ? L.t : L.x;
@@ -318,7 +381,7 @@ __device__ void vcycle(const MgArgs& a, ClusterCtx& cx)
                          [&](int c, float v) { dst[c] = v; });
         }
         for (int k = 0; k < a.nu; ++k) {
-            cx.level_sync(local);
+            cx.sync();
             float* src = cur;
             float* dst = oth;
             for_cells<U>(R, n,
@@ -328,9 +391,8 @@ __device__ void vcycle(const MgArgs& a, ClusterCtx& cx)
             cur = oth;
             oth = tmp;
         }
-        cx.level_sync(local);
+        cx.sync();
     }
-    if (a.local_from == 0) cx.sync();   // level 0 ran in CTA 0: publish z to the cluster
 }
 
 __global__ void __launch_bounds__(kMgBlock) mg_solve_kernel(const MgArgs a)
@@ -338,8 +400,29 @@ __global__ void __launch_bounds__(kMgBlock) mg_solve_kernel(const MgArgs a)
     constexpr int U = 4;   // cells per thread whose loads are in flight together
     __shared__ float slots_f[6];
     __shared__ double slots_d[6];
+    extern __shared__ __align__(16) float mg_smem[];
     ClusterCtx cx(a.local_from);
     if (ld_volatile_int(&a.status->done)) return;   // same value in every CTA (set by an earlier kernel)
+    // shared-memory copy of the local levels (used by CTA 0 only)
+    __shared__ MgLevelDev S[kMaxLevels];
+    if (threadIdx.x == 0)
+        for (int l = a.local_from; l < a.nl; ++l) {
+            const int n = a.lv[l].nx * a.lv[l].ny;
+            float* base = mg_smem + a.loff[l];
+            S[l] = MgLevelDev{a.lv[l].nx, a.lv[l].ny, base, base + n, base + 2 * n, base + 3 * n, base + 4 * n,
+                              base + 5 * n};
+        }
+    if (cx.rank() == 0)
+        for (int l = a.local_from; l < a.nl; ++l) {
+            const int n = a.lv[l].nx * a.lv[l].ny;
+            float* base = mg_smem + a.loff[l];
+            for (int c = threadIdx.x; c < n; c += blockDim.x) {
+                base[c] = a.lv[l].d[c];
+                base[n + c] = a.lv[l].cx[c];
+                base[2 * n + c] = a.lv[l].cy[c];
+            }
+        }
+    __syncthreads();
     int rotf = 0, rotd = 0;
     const Range G = cx.range(false);
     const int N = a.N, nx = a.nx, ny = a.ny;
@@ -396,7 +479,7 @@ __global__ void __launch_bounds__(kMgBlock) mg_solve_kernel(const MgArgs a)
             a.s[c] = r;
             L0.r[c] = r;
         }
-        vcycle(a, cx);
+        vcycle(a, S, cx);
         float f2[2];
         {
             float l0 = 0.f, l1 = 0.f;
@@ -448,7 +531,7 @@ __global__ void __launch_bounds__(kMgBlock) mg_solve_kernel(const MgArgs a)
             ++total;
             cx.sum2f(lss, 0.f, f2, slots_f, rotf);
             if (f2[0] <= istop || total >= a.max_iter) break;
-            vcycle(a, cx);
+            vcycle(a, S, cx);
             float lrz = 0.f;
             for (int c = G.start; c < N; c += stride) lrz += a.s[c] * ld(L0.t + c);
             cx.sum2f(lrz, 0.f, f2, slots_f, rotf);
@@ -512,9 +595,19 @@ cudaError_t launch_synthetic_solve(const Plan& P, const double* guess, double* o
     a.omega = 0.8f;
     a.alpha = 1.8f;
     a.status = P.status;
+    int off = 0;
+    for (int l = P.mg.local_from; l < P.mg.nl; ++l) {
+        a.loff[l] = off;
+        off += 6 * P.mg.nx[l] * P.mg.ny[l];
+        off = (off + 3) / 4 * 4;
+    }
+    const size_t smem = (size_t)off * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(mg_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(P.mg.cluster);
     cfg.blockDim = dim3(kMgBlock);
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;

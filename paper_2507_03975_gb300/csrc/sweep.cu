@@ -278,10 +278,39 @@ sweep_kernel(const SweepArgs<T> a)
             wsrc[SM::W_IOLD] = Is;
         }
 
+        // Cell index of (band row r, sweep column c) is affine in r and c:
+        // cell = base0 + r * dr + c * dc.
+        const bool full_rows = band * 32 + 32 <= ny;
+        const int dr = ypos ? nx : -nx, dc = xpos ? 1 : -1;
+        const int base0 = (ypos ? band * 32 : ny - 1 - band * 32) * nx + (xpos ? 0 : nx - 1);
+
         // Issue the asynchronous copies of chunk m into buffer b.
         auto prefetch = [&](int m, int b) {
             const int t0 = m * SEG;
             T* wb = win + b * NW * SM::WIN;
+            if (full_rows && t0 >= 31 && t0 + SEG <= nx) {
+                // interior chunk: every row window lies inside the mesh
+                constexpr int RPI = 32 / SEG;
+                const int kk = lane % SEG, r = lane / SEG;
+                int cell = base0 + r * dr + (t0 + kk - r) * dc;
+                const int dcell = RPI * (dr - dc);
+                T* dst = wb + r * RS + kk;
+#pragma unroll 4
+                for (int r0 = 0; r0 < 32; r0 += RPI) {
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) cp_async<sizeof(T)>(dst + w * SM::WIN, wsrc[w] + cell);
+                    cell += dcell;
+                    dst += RPI * RS;
+                }
+                T* ab = win_a + b * AW;
+                for (int u = lane; u < SEG + 31; u += 32) cp_async<sizeof(T)>(ab + u, arow + (xpos ? t0 - 31 + u : nx - 1 - (t0 - 31 + u)));
+                if (PRE) {
+                    double* rb = win_r + b * SEG * 32;
+                    for (int v = 2 * lane; v < SEG * 32; v += 64) cp_async<16>(rb + v, rrow + (size_t)t0 * 32 + v);
+                }
+                cp_async_commit();
+                return;
+            }
             // row r of the band needs columns t0 - r .. t0 - r + SEG - 1: the
             // warp copies 32/SEG rows per instruction, SEG consecutive cells each
             constexpr int RPI = 32 / SEG;
@@ -322,6 +351,17 @@ sweep_kernel(const SweepArgs<T> a)
             constexpr int RPI = 32 / SEG;
             const int cc = lane % SEG, rr = lane / SEG;
             const int c = g * SEG + cc;
+            if (full_rows && (g + 1) * SEG <= nx) {
+                int cell = base0 + rr * dr + c * dc;
+                const T* src = stage + rr * RING + (c & (RING - 1));
+#pragma unroll
+                for (int r0 = 0; r0 < 32; r0 += RPI) {
+                    Is[cell] = *src;
+                    cell += RPI * dr;
+                    src += RPI * RING;
+                }
+                return;
+            }
 #pragma unroll
             for (int r0 = 0; r0 < 32; r0 += RPI) {
                 const int r = r0 + rr;
@@ -368,6 +408,41 @@ sweep_kernel(const SweepArgs<T> a)
             const T* wb = win + b * NW * SM::WIN + lane * RS;
             const T* ab = win_a + b * AW + 31 - lane;
             const double* rb = win_r + b * SEG * 32 + lane;
+            if (full_rows && t0 >= 31 && t0 + SEG <= nx) {
+                // interior chunk: every lane updates a cell at every step
+                T* st = stage + lane * RING;
+                const int cbase = t0 - lane;
+                T* eo = edge_out + cbase;
+                const bool put_edge = lane == 31 && band < nb - 1;
+#pragma unroll
+                for (int tt = 0; tt < SEG; ++tt) {
+                    T Isouth = __shfl_up_sync(kFull, Iprev, 1);
+                    const T e = __shfl_sync(kFull, edge_reg, tt);
+                    if (lane == 0) Isouth = e;
+                    T sv = wb[SM::W_SRC * SM::WIN + tt];
+                    const T ai = ab[tt];
+                    T rinv;
+                    if (PRE) {
+                        if (PT) sv = fma(wb[SM::W_SHIFT * SM::WIN + tt], wb[SM::W_IOLD * SM::WIN + tt], sv);
+                        rinv = (T)rb[tt * 32];
+                    } else {
+                        T d = wb[SM::W_SIGT * SM::WIN + tt] + ai + bj;
+                        if (PT) {
+                            const T sh = wb[SM::W_SHIFT * SM::WIN + tt];
+                            sv = fma(sh, wb[SM::W_IOLD * SM::WIN + tt], sv);
+                            d += sh;
+                        }
+                        rinv = rcp_t(d);
+                    }
+                    T acc = fma(ai, IW, sv);
+                    acc = fma(bj, Isouth, acc);
+                    const T Inew = acc * rinv;
+                    IW = Inew;
+                    Iprev = Inew;
+                    st[(cbase + tt) & (RING - 1)] = Inew;
+                    if (put_edge) eo[tt] = Inew;
+                }
+            } else
 #pragma unroll 4
             for (int tt = 0; tt < SEG; ++tt) {
                 const int t = t0 + tt;
@@ -404,10 +479,9 @@ sweep_kernel(const SweepArgs<T> a)
             }
             if (band < nb - 1 && lane == 31) {
                 const int cols = min(nx, t0 + SEG - 31);
-                if (cols > 0) {
-                    __threadfence();
-                    st_release_u64(flag_out, a.epoch_hi | (unsigned long long)cols);
-                }
+                // edge_out is written by this lane only: the release store
+                // orders those writes before the flag.
+                if (cols > 0) st_release_u64(flag_out, a.epoch_hi | (unsigned long long)cols);
             }
             __syncwarp();
             const int last_complete = m - LAG;
