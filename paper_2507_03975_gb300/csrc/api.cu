@@ -143,7 +143,6 @@ size_t layout(const Sizes& z, char* base, Plan* P)
     p.rsw = z.fp32 ? nullptr : reinterpret_cast<double*>(take(K * nb * (z.nx + 31) * 32 * sizeof(double)));
     p.I = take(K * N * Ts);
     p.edge = take(K * nb * z.nx * Ts);
-    p.flags = reinterpret_cast<unsigned long long*>(take(K * nb * sizeof(unsigned long long)));
     p.sigt = reinterpret_cast<double*>(take(N * sizeof(double)));
     p.shift = reinterpret_cast<double*>(take(N * sizeof(double)));
     p.src = reinterpret_cast<double*>(take(N * sizeof(double)));
@@ -196,6 +195,8 @@ int check_mesh(const gsis_mesh* m)
     if (!m) return fail(GSIS_ERR_ARG, "mesh is NULL");
     if (m->nx < 1 || m->ny < 1 || m->nx > kMaxSide || m->ny > kMaxSide)
         return fail(GSIS_ERR_ARG, "mesh size %d x %d out of range [1, %d]", m->nx, m->ny, kMaxSide);
+    if ((long long)m->nx * m->ny > (1LL << 30))
+        return fail(GSIS_ERR_ARG, "mesh of %d x %d cells exceeds 2^30 cells", m->nx, m->ny);
     if ((long long)m->nx * m->ny > (1LL << 30)) return fail(GSIS_ERR_ARG, "too many cells");
     if (!m->dx || !m->dy) return fail(GSIS_ERR_ARG, "mesh spacing arrays are NULL");
     for (int i = 0; i < m->nx; ++i)
@@ -268,7 +269,6 @@ int prepare(Plan& P, const gsis_mesh* mesh, const gsis_quadrature* quad, const g
     P.sigma_s = ss;
     P.q = q;
     P.inflow = inflow;
-    P.epoch = 0;
     int dev = 0, clk_khz = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, dev));
@@ -279,9 +279,8 @@ int prepare(Plan& P, const gsis_mesh* mesh, const gsis_quadrature* quad, const g
     CK(prepare_kernels(std::max(P.K, 1), P.fp32, P.pt));
     if (P.K > 0) {
         const int per_sm = std::max(1, sweep_max_active_blocks(P.fp32, P.pt));
-        const long long units = (long long)P.K * P.nb;
-        P.sweep_grid = (int)std::max(1LL, std::min<long long>((long long)per_sm * P.num_sms,
-                                                            (units + kSweepWarps - 1) / kSweepWarps));
+        const long long units = (long long)P.K * P.nb;   // one unit per warp pair, all pairs resident
+        P.sweep_grid = (int)std::max(1LL, std::min<long long>((long long)per_sm * P.num_sms, units));
     }
     P.mg.cluster = mg_cluster_size();
     P.red_grid = std::max(1, std::min({P.num_sms * 8, kMaxCgBlocks, (P.N + kRedBlock - 1) / kRedBlock}));
@@ -316,7 +315,9 @@ int prepare(Plan& P, const gsis_mesh* mesh, const gsis_quadrature* quad, const g
                            cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(const_cast<int*>(P.perm), hi.data(), hi.size() * sizeof(int),
                            cudaMemcpyHostToDevice, st));
-        CK(cudaMemsetAsync(P.flags, 0, (size_t)K * P.nb * sizeof(unsigned long long), st));
+        // band hand-off rows start "unwritten" (all-ones bytes); each sweep
+        // restores that state after consuming them
+        CK(cudaMemsetAsync(P.edge, 0xff, (size_t)K * P.nb * P.nx * (P.fp32 ? sizeof(float) : sizeof(double)), st));
         CK(cudaStreamSynchronize(st));   // host staging vectors go out of scope
         TIMED(GSIS_KCLASS_SETUP, 1, launch_setup(P, st));
     }
@@ -332,7 +333,7 @@ int read_status(Status& S, const Plan& P, cudaStream_t st)
     CK(cudaStreamSynchronize(st));
     prof_harvest();
     if (S.error & kErrBadInput)
-        return fail(GSIS_ERR_ARG, "sigma_a, sigma_s must be >= 0 with sigma_t > 0, q finite");
+        return fail(GSIS_ERR_ARG, "sigma_a, sigma_s must be >= 0 with sigma_t > 0; q and inflow finite");
     if (S.error & kErrTimeout)
         return fail(GSIS_ERR_DEVICE_TIMEOUT, "a device-side wait exceeded its bound");
     return GSIS_OK;

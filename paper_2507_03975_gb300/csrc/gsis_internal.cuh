@@ -12,8 +12,8 @@ namespace gsis {
 constexpr int kWarp = 32;
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxK = 4096;            // directions per quadrature (host-side check)
-constexpr int kMaxSide = (1 << 20) - 1; // cells per mesh side (edge-flag encoding)
-constexpr int kSweepWarps = 4;          // warps per sweep CTA
+constexpr int kMaxSide = (1 << 20) - 1; // cells per mesh side
+constexpr int kSweepPairs = 8;          // (compute, copy) warp pairs per sweep CTA
 constexpr int kRedBlock = 256;          // threads per reduction / stencil block
 constexpr int kMaxCgBlocks = 1024;      // partials capacity of the fixed-order grid reductions
 constexpr int kMaxLevels = 24;          // multigrid levels (2x2 aggregation down to one cell)
@@ -32,7 +32,6 @@ constexpr int kDiverged = 4;
 
 // Device-resident control block.
 struct Status {
-    unsigned long long sweep_tasks;   // dynamic task counter of the sweep (zeroed after each sweep)
     unsigned int ticket;              // last-block ticket of the Err reduction
     int error;                        // kErr* bits
     int done;                         // != 0: iteration finished, later kernels return at once
@@ -71,7 +70,6 @@ struct Plan {
     int sweep_grid;                 // persistent sweep CTAs
     int cg_grid;                    // cooperative synthetic CTAs
     int red_grid;                   // per-cell kernels' CTAs (Err reduction partial count)
-    unsigned long long epoch;       // sweep launch counter (edge flags)
 
     // mesh
     const double* dx; const double* dy;
@@ -85,8 +83,7 @@ struct Plan {
     const float* acoef_f; const float* bcoef_f;
     const double* rsw;              // FP64: 1/d in sweep order [K][nb][nx+31][32]
     void* I;                        // [K][N] T, intensities of the last sweep (sorted s)
-    void* edge;                     // [K][nb][nx] T, top row of each band
-    unsigned long long* flags;      // [K][nb] published edge columns
+    void* edge;                     // [K][nb][nx] T, last row of each band (all-ones bytes = not yet written)
     // cell data
     const double* sigma_a; const double* sigma_s; const double* q; const double* inflow;
     double* sigt; float* sigt_f;
@@ -129,38 +126,55 @@ void set_last_error(int code, const char* msg);   // message returned by gsis_la
 
 // ------------------------------------------------------------ device helpers
 #ifdef __CUDACC__
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p)
-{
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v)
-{
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" :: "l"(p), "l"(v) : "memory");
-}
-
 __device__ __forceinline__ int ld_volatile_int(const int* p)
 {
     return *reinterpret_cast<const volatile int*>(p);
 }
 
-// Waits (bounded by `limit` clock cycles) until *p >= target.  Returns false
-// and raises kErrTimeout if the bound is hit, false if another CTA has
-// already raised an error.
-__device__ __forceinline__ bool wait_at_least(const unsigned long long* p, unsigned long long target,
-                                              long long limit, int* err)
+__device__ __forceinline__ unsigned smem_addr(const void* p)
 {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// mbarrier in shared memory (arrive: release, wait: acquire, CTA scope)
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long* b)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(b))
+                 : "memory");
+}
+
+// Arrival on b once every cp.async this thread issued so far has landed
+// (the arrival is counted in the barrier's expected count).
+__device__ __forceinline__ void cp_async_mbar_arrive(unsigned long long* b)
+{
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(b)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* b, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_addr(b)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// Waits (bounded by `limit` clock cycles) for the phase of parity `parity`
+// to complete; false when the bound is hit.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity, long long limit)
+{
+    if (mbar_try_wait(b, parity)) return true;
     const long long t0 = clock64();
     for (;;) {
-        if (ld_acquire_u64(p) >= target) return true;
-        if (ld_volatile_int(err)) return false;
-        if (clock64() - t0 > limit) {
-            atomicOr(err, kErrTimeout);
-            return false;
-        }
-        __nanosleep(32);
+        if (mbar_try_wait(b, parity)) return true;
+        if (clock64() - t0 > limit) return false;
     }
 }
 

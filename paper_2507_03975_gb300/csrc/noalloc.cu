@@ -17,9 +17,9 @@
 //    cudaGetSymbolAddress (once per device, that device current); make that
 //    first call before any stream capture;
 //  * every call shares the one array and it keeps the last call's contents;
-//    the status block and the band hand-off flags that must start at zero are
-//    cleared by every call; calls that overlap on the GPU (other streams, other
-//    host threads) race on the array.
+//    the status block and the band hand-off rows that must start "unwritten"
+//    are reset by every call; calls that overlap on the GPU (other streams,
+//    other host threads) race on the array.
 #include <cuda_runtime.h>
 
 #include <cstdio>

@@ -9,16 +9,16 @@
 // one step, so the upwind south value is the value lane l-1 produced one step
 // earlier (one warp shuffle) and the upwind west value is the lane's own
 // previous result (a register).  Lane 0 takes its south value from the band
-// below, published through a global edge row and a release/acquire counter,
-// or from the inflow on the first band.  Units are handed out in band-major
-// order by an atomic counter to persistent CTAs, so a unit only ever waits on
-// a unit that a running warp already owns (no deadlock); every wait is
-// bounded and reports kErrTimeout instead of hanging.
+// below (its last-row results, handed over value by value through a global
+// row whose slots read "unwritten" until stored) or from the inflow on the
+// first band.  Each compute warp is paired with a copy warp that stages the
+// cell data of the coming steps in shared memory and fetches the south
+// values, so the compute warp touches global memory only to store results.
+// Every wait is bounded and reports kErrTimeout instead of hanging.
 //
-// Results are staged in shared memory and written as full 128-byte row
-// segments; all intensities of the last sweep stay in HBM as I[s][cell]
-// (needed by the moment reduction, the pseudo-time delta form of Sec. 4.3
-// and the final second moment).
+// All intensities of the last sweep stay in HBM as I[s][cell] (needed by the
+// moment reduction, the pseudo-time delta form of Sec. 4.3 and the final
+// second moment).
 #include <cuda_runtime.h>
 
 #include "gsis_internal.cuh"
@@ -57,15 +57,20 @@ __global__ void coef_kernel(int nx, int ny, int K, const double* __restrict__ dx
 // dx_ref = min(dx_i, dy_j)), the finite-volume synthetic operator
 // (Eqs. (elem_mtx_M), (Gamma_ij_com2) on the Cartesian mesh:
 // Gamma = 2 / (3 (sigma_i h_i + sigma_j h_j)); boundary
-// beta = 2/(3 sigma_i h_i) + 1/4 from Eq. (macro_bc_delta_flux)), input checks.
+// beta = 2/(3 sigma_i h_i) + 1/4 from Eq. (macro_bc_delta_flux)), input checks
+// (opacities, sources and inflow finite; opacities non-negative).
 __global__ void cell_setup_kernel(int nx, int ny, const double* __restrict__ dx,
                                   const double* __restrict__ dy, const double* __restrict__ sa,
                                   const double* __restrict__ ss, const double* __restrict__ q,
+                                  const double* __restrict__ inflow, int n_inflow,
                                   double cfl_p, double beta, double* sigt, float* sigt_f,
                                   double* shift, float* shift_f, double* diag, double* cx,
                                   double* cy, int* err)
 {
     const int N = nx * ny;
+    if (inflow)
+        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_inflow; t += gridDim.x * blockDim.x)
+            if (!isfinite(inflow[t])) atomicOr(err, kErrBadInput);
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
         const int j = c / nx, i = c - j * nx;
         const double a = sa[c], s = ss[c], st = a + s;
@@ -178,11 +183,8 @@ struct SweepArgs {
     const double* rsw;
     const T* sigt; const T* shift; const T* src;
     T* I; T* edge;
-    unsigned long long* flags;
-    unsigned long long epoch_hi;
     const double* inflow;
     const int* perm; const double* qmu; const double* qeta;
-    unsigned long long* tasks;
     int* err; const int* done;
     long long wait_cycles;
 };
@@ -193,22 +195,57 @@ __device__ __forceinline__ float rcp_t(float d) { return __frcp_rn(d); }
 template <int BYTES>
 __device__ __forceinline__ void cp_async(void* smem, const void* gmem)
 {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(smem)), "l"(gmem), "n"(BYTES)
+                 : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// Shared-memory plan of one sweep warp (all sizes in elements of T unless
-// noted).  Per-lane windows hold, for the SEG steps of a chunk, the cell data
-// of the lane's own row (padded rows: conflict-free column access); the
-// column-coefficient window covers the SEG + 31 columns the skewed lanes
-// touch in a chunk; the 1/d table chunk is SEG x 32 doubles in step order.
+// Band hand-off slots hold the bit pattern "all ones" (a NaN that no
+// arithmetic produces) until the upstream band writes the value.
+template <typename T> struct Bits;
+template <> struct Bits<double> {
+    using U = unsigned long long;
+    static constexpr U empty = ~0ull;
+    static __device__ __forceinline__ U load(const double* p)
+    {
+        U v;
+        asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p));
+        return v;
+    }
+    static __device__ __forceinline__ void store(double* p, double v)
+    {
+        asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v));
+    }
+    static __device__ __forceinline__ double value(U u) { return __longlong_as_double((long long)u); }
+    static __device__ __forceinline__ void clear(double* p) { *reinterpret_cast<U*>(p) = empty; }
+};
+template <> struct Bits<float> {
+    using U = unsigned int;
+    static constexpr U empty = ~0u;
+    static __device__ __forceinline__ U load(const float* p)
+    {
+        U v;
+        asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p));
+        return v;
+    }
+    static __device__ __forceinline__ void store(float* p, float v)
+    {
+        asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v));
+    }
+    static __device__ __forceinline__ float value(U u) { return __uint_as_float(u); }
+    static __device__ __forceinline__ void clear(float* p) { *reinterpret_cast<U*>(p) = empty; }
+};
+
+// Shared-memory plan of one (compute, copy) warp pair.  A chunk is SEG
+// consecutive steps (64-byte row segments).  Each of the NBUF chunk buffers
+// holds, for the lane's own row, the cell data of the SEG cells the lane
+// updates in the chunk (padded rows: conflict-free column access), the
+// column coefficients of the SEG + 31 columns the skewed lanes touch, the
+// 1/d table rows of the chunk (FP64) and the SEG south values of lane 0.
 template <typename T, bool PT, bool PRE>
 struct SweepSmem {
-    static constexpr int SEG = 128 / (int)sizeof(T);
-    static constexpr int RING = 4 * SEG;
+    static constexpr int SEG = 64 / (int)sizeof(T);
+    static constexpr int NBUF = 3;
     static constexpr int RS = SEG + 1;
     static constexpr int AW = SEG + 32;
     static constexpr int NW = (PRE ? 1 : 2) + (PT ? 2 : 0);   // src, [sigt], [shift, I^m]
@@ -216,288 +253,281 @@ struct SweepSmem {
     static constexpr int W_SIGT = 1;                          // FP32 only (no 1/d table)
     static constexpr int W_SHIFT = PRE ? 1 : 2;               // pseudo-time only
     static constexpr int W_IOLD = PRE ? 2 : 3;                // pseudo-time only
-    static constexpr int STAGE = 32 * RING;
     static constexpr int WIN = 32 * RS;
-    static constexpr size_t warp_bytes =
-        sizeof(T) * (size_t)(STAGE + 2 * NW * WIN + 2 * AW) + (PRE ? 2 * (size_t)SEG * 32 * sizeof(double) : 0);
-    static constexpr size_t bytes = kSweepWarps * ((warp_bytes + 15) / 16 * 16);
+    static constexpr size_t r16(size_t b) { return (b + 15) / 16 * 16; }
+    static constexpr size_t off_r = r16(sizeof(T) * (size_t)NW * WIN);
+    static constexpr size_t off_a = off_r + (PRE ? (size_t)SEG * 32 * sizeof(double) : 0);
+    static constexpr size_t off_e = off_a + r16(sizeof(T) * (size_t)AW);
+    static constexpr size_t buf_bytes = off_e + r16(sizeof(T) * (size_t)SEG);
+    static constexpr size_t bar_bytes = 64;                   // full[NBUF], empty[NBUF]
+    static constexpr size_t pair_bytes = bar_bytes + NBUF * buf_bytes;
+    static constexpr size_t bytes = kSweepPairs * pair_bytes;
+    static_assert(2 * NBUF * 8 <= bar_bytes, "barrier space");
 };
 
+// One persistent CTA per SM runs kSweepPairs warp pairs.  Pair p of CTA c
+// owns the units (direction s, band) with index u = band * K + s equal to
+// p * G + c + i * kSweepPairs * G (G = grid size), in increasing u.  All
+// pairs are resident, a unit waits only on unit u - K, and every pair takes
+// its units in increasing order, so the waits cannot form a cycle.
+//
+// Copy warp: for each chunk, cp.async of the window data into a free buffer
+// (arrival on the buffer's "full" barrier when the copies land), then the
+// south values of lane 0: the inflow on band 0, else the upstream band's
+// last-row results, polled until written (bounded).  Compute warp: waits on
+// "full", runs the SEG steps from shared memory, writes each result straight
+// to I, and the last lane also to this band's hand-off row, then arrives on
+// "empty".  Every wait is bounded; on time-out kErrTimeout is raised and the
+// warp leaves after its copies in flight have landed.
 template <typename T, bool PT, bool PRE>
-__global__ void __launch_bounds__(kSweepWarps * 32, 1)
+__global__ void __launch_bounds__(kSweepPairs * 64, 1)
 sweep_kernel(const SweepArgs<T> a)
 {
     using SM = SweepSmem<T, PT, PRE>;
-    constexpr int SEG = SM::SEG, RING = SM::RING, RS = SM::RS, AW = SM::AW, NW = SM::NW;
-    constexpr int LAG = (31 + SEG - 1) / SEG;   // segments a row band lags behind lane 0
+    using B = Bits<T>;
+    constexpr int SEG = SM::SEG, NBUF = SM::NBUF, RS = SM::RS, NW = SM::NW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    unsigned char* wbase = smem_raw + (threadIdx.x >> 5) * ((SM::warp_bytes + 15) / 16 * 16);
-    double* win_r = reinterpret_cast<double*>(wbase);                       // [2][SEG*32] (PRE)
-    T* stage = reinterpret_cast<T*>(wbase + (PRE ? 2 * SEG * 32 * sizeof(double) : 0));
-    T* win = stage + SM::STAGE;                                             // [2][NW][32*RS]
-    T* win_a = win + 2 * NW * SM::WIN;                                      // [2][AW]
-    const int lane = threadIdx.x & 31;
-    const int nx = a.nx, ny = a.ny, K = a.K, nb = a.nb;
-    const unsigned ntasks = (unsigned)(K * nb);
-    const int nchunks = (a.nsteps + SEG - 1) / SEG;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool copier = warp >= kSweepPairs;
+    const int pair = copier ? warp - kSweepPairs : warp;
+    unsigned char* pbase = smem_raw + (size_t)pair * SM::pair_bytes;
+    unsigned long long* full = reinterpret_cast<unsigned long long*>(pbase);
+    unsigned long long* empty = full + NBUF;
+    auto buf = [&](int b) { return pbase + SM::bar_bytes + (size_t)b * SM::buf_bytes; };
 
-    int stop = 0;
-    if (lane == 0) stop = ld_volatile_int(a.done);
-    if (__shfl_sync(kFull, stop, 0)) return;
-
-    for (;;) {
-        unsigned task = 0;
-        int bad = 0;
-        if (lane == 0) {
-            task = (unsigned)atomicAdd(a.tasks, 1ull);
-            bad = ld_volatile_int(a.err);
+    if (threadIdx.x < kSweepPairs) {
+        unsigned long long* f = reinterpret_cast<unsigned long long*>(smem_raw + (size_t)threadIdx.x * SM::pair_bytes);
+        for (int b = 0; b < NBUF; ++b) {
+            mbar_init(f + b, 64);            // 32 cp.async arrivals + 32 lane arrivals
+            mbar_init(f + NBUF + b, 32);     // 32 compute lanes
         }
-        task = __shfl_sync(kFull, task, 0);
-        bad = __shfl_sync(kFull, bad, 0);
-        if (task >= ntasks || bad) return;
-        const int band = (int)(task / (unsigned)K);
-        const int s = (int)(task - (unsigned)band * (unsigned)K);
+    }
+    __syncthreads();
+
+    const int nx = a.nx, ny = a.ny, K = a.K, nb = a.nb;
+    const int G = gridDim.x;
+    const int ntasks = K * nb;
+    const int nchunks = (a.nsteps + SEG - 1) / SEG;
+    const long long budget = a.wait_cycles;
+    {
+        int stop = 0;
+        if (lane == 0) stop = ld_volatile_int(a.done) | ld_volatile_int(a.err);
+        if (__shfl_sync(kFull, stop, 0)) return;
+    }
+
+    unsigned g = 0;   // chunks this pair has handled (buffer = g % NBUF)
+    for (int task = pair * G + blockIdx.x; task < ntasks; task += kSweepPairs * G) {
+        const int band = task / K;
+        const int s = task - band * K;
         const bool xpos = a.qmu[s] >= 0.0, ypos = a.qeta[s] >= 0.0;
         const int k = a.perm[s];
         const int jl = band * 32 + lane;
         const bool row_ok = jl < ny;
         const int j = ypos ? jl : ny - 1 - jl;
-        const T bj = row_ok ? a.bcoef[(size_t)s * ny + j] : T(0);
-        const T* arow = a.acoef + (size_t)s * nx;
         T* Is = a.I + (size_t)s * a.N;
-        const double* rrow = PRE ? a.rsw + ((size_t)s * nb + band) * (size_t)a.nsteps * 32 : nullptr;
-        T* edge_out = a.edge + ((size_t)s * nb + band) * nx;
-        const T* edge_in = a.edge + ((size_t)s * nb + band - 1) * nx;
-        unsigned long long* flag_out = a.flags + (size_t)s * nb + band;
-        const unsigned long long* flag_in = a.flags + (size_t)s * nb + band - 1;
-        const T* wsrc[NW];
-        wsrc[SM::W_SRC] = a.src;
-        if (!PRE) wsrc[SM::W_SIGT] = a.sigt;
-        if (PT) {
-            wsrc[SM::W_SHIFT] = a.shift;
-            wsrc[SM::W_IOLD] = Is;
-        }
-
-        // Cell index of (band row r, sweep column c) is affine in r and c:
-        // cell = base0 + r * dr + c * dc.
+        // cell of (band row r, sweep column c) = base0 + r * dr + c * dc
         const bool full_rows = band * 32 + 32 <= ny;
         const int dr = ypos ? nx : -nx, dc = xpos ? 1 : -1;
         const int base0 = (ypos ? band * 32 : ny - 1 - band * 32) * nx + (xpos ? 0 : nx - 1);
 
-        // Issue the asynchronous copies of chunk m into buffer b.
-        auto prefetch = [&](int m, int b) {
-            const int t0 = m * SEG;
-            T* wb = win + b * NW * SM::WIN;
-            if (full_rows && t0 >= 31 && t0 + SEG <= nx) {
-                // interior chunk: every row window lies inside the mesh
-                constexpr int RPI = 32 / SEG;
-                const int kk = lane % SEG, r = lane / SEG;
-                int cell = base0 + r * dr + (t0 + kk - r) * dc;
-                const int dcell = RPI * (dr - dc);
-                T* dst = wb + r * RS + kk;
-#pragma unroll 4
-                for (int r0 = 0; r0 < 32; r0 += RPI) {
-#pragma unroll
-                    for (int w = 0; w < NW; ++w) cp_async<sizeof(T)>(dst + w * SM::WIN, wsrc[w] + cell);
-                    cell += dcell;
-                    dst += RPI * RS;
+        if (copier) {
+            // ---------------------------------------------------- copy warp
+            const T* wsrc[NW];
+            wsrc[SM::W_SRC] = a.src;
+            if (!PRE) wsrc[SM::W_SIGT] = a.sigt;
+            if (PT) {
+                wsrc[SM::W_SHIFT] = a.shift;
+                wsrc[SM::W_IOLD] = Is;
+            }
+            const T* arow = a.acoef + (size_t)s * nx;
+            const double* rrow = PRE ? a.rsw + ((size_t)s * nb + band) * (size_t)a.nsteps * 32 : nullptr;
+            T* edge_in = band > 0 ? a.edge + ((size_t)s * nb + band - 1) * nx : nullptr;
+            for (int m = 0; m < nchunks; ++m, ++g) {
+                const int b = (int)(g % NBUF);
+                if (g >= NBUF) {
+                    const bool ok = __all_sync(kFull, mbar_wait(empty + b, ((g / NBUF) - 1) & 1, budget));
+                    if (!ok) {
+                        if (lane == 0) atomicOr(a.err, kErrTimeout);
+                        cp_async_wait_all();
+                        return;
+                    }
                 }
-                T* ab = win_a + b * AW;
-                for (int u = lane; u < SEG + 31; u += 32) cp_async<sizeof(T)>(ab + u, arow + (xpos ? t0 - 31 + u : nx - 1 - (t0 - 31 + u)));
+                unsigned char* bp = buf(b);
+                T* wb = reinterpret_cast<T*>(bp);
+                const int t0 = m * SEG;
+                constexpr int RPI = 32 / SEG;   // rows per copy instruction
+                const int kk = lane % SEG;
+                if (full_rows && t0 >= 31 && t0 + SEG <= nx) {
+                    // interior chunk: every row window lies inside the mesh
+                    const int r = lane / SEG;
+                    int cell = base0 + r * dr + (t0 + kk - r) * dc;
+                    const int dcell = RPI * (dr - dc);
+                    T* dst = wb + r * RS + kk;
+#pragma unroll
+                    for (int r0 = 0; r0 < 32; r0 += RPI) {
+#pragma unroll
+                        for (int w = 0; w < NW; ++w) cp_async<sizeof(T)>(dst + w * SM::WIN, wsrc[w] + cell);
+                        cell += dcell;
+                        dst += RPI * RS;
+                    }
+                    T* ab = reinterpret_cast<T*>(bp + SM::off_a);
+                    for (int u = lane; u < SEG + 31; u += 32)
+                        cp_async<sizeof(T)>(ab + u, arow + (xpos ? t0 - 31 + u : nx - 1 - (t0 - 31 + u)));
+                } else {
+                    // row r of the band needs columns t0 - r .. t0 - r + SEG - 1
+#pragma unroll 4
+                    for (int r0 = 0; r0 < 32; r0 += RPI) {
+                        const int r = r0 + lane / SEG;
+                        const int jr = band * 32 + r;
+                        const int c = t0 + kk - r;
+                        if (jr < ny && c >= 0 && c < nx) {
+                            const size_t cell = (size_t)(ypos ? jr : ny - 1 - jr) * nx + (xpos ? c : nx - 1 - c);
+#pragma unroll
+                            for (int w = 0; w < NW; ++w) cp_async<sizeof(T)>(wb + w * SM::WIN + r * RS + kk, wsrc[w] + cell);
+                        }
+                    }
+                    T* ab = reinterpret_cast<T*>(bp + SM::off_a);
+                    for (int u = lane; u < SEG + 31; u += 32) {
+                        const int c = t0 - 31 + u;
+                        if (c >= 0 && c < nx) cp_async<sizeof(T)>(ab + u, arow + (xpos ? c : nx - 1 - c));
+                    }
+                }
                 if (PRE) {
-                    double* rb = win_r + b * SEG * 32;
-                    for (int v = 2 * lane; v < SEG * 32; v += 64) cp_async<16>(rb + v, rrow + (size_t)t0 * 32 + v);
+                    const int nv = min(SEG, a.nsteps - t0) * 32;   // doubles, multiple of 32
+                    double* rb = reinterpret_cast<double*>(bp + SM::off_r);
+                    for (int v = 2 * lane; v < nv; v += 64) cp_async<16>(rb + v, rrow + (size_t)t0 * 32 + v);
                 }
-                cp_async_commit();
-                return;
-            }
-            // row r of the band needs columns t0 - r .. t0 - r + SEG - 1: the
-            // warp copies 32/SEG rows per instruction, SEG consecutive cells each
-            constexpr int RPI = 32 / SEG;
-            const int kk = lane % SEG;
-#pragma unroll 4
-            for (int r0 = 0; r0 < 32; r0 += RPI) {
-                const int r = r0 + lane / SEG;
-                const int jr = band * 32 + r;
-                const int c = t0 + kk - r;
-                if (jr < ny && c >= 0 && c < nx) {
-                    const size_t cell = (size_t)(ypos ? jr : ny - 1 - jr) * nx + (xpos ? c : nx - 1 - c);
-#pragma unroll
-                    for (int w = 0; w < NW; ++w) cp_async<sizeof(T)>(wb + w * SM::WIN + r * RS + kk, wsrc[w] + cell);
-                }
-            }
-            T* ab = win_a + b * AW;
-            for (int u = lane; u < SEG + 31; u += 32) {
-                const int c = t0 - 31 + u;
-                if (c >= 0 && c < nx) cp_async<sizeof(T)>(ab + u, arow + (xpos ? c : nx - 1 - c));
-            }
-            if (PRE) {
-                const int nv = min(SEG, a.nsteps - t0) * 32;   // doubles, multiple of 32
-                double* rb = win_r + b * SEG * 32;
-                for (int v = 2 * lane; v < nv; v += 64) cp_async<16>(rb + v, rrow + (size_t)t0 * 32 + v);
-            }
-            cp_async_commit();
-        };
-
-        T IW = T(0);
-        if (row_ok && a.inflow) {
-            const int f = xpos ? j : ny + j;
-            IW = (T)a.inflow[(size_t)f * K + k];
-        }
-        T Iprev = T(0), edge_reg = T(0);
-        int flushed = 0;
-
-        auto flush = [&](int g) {
-            constexpr int RPI = 32 / SEG;
-            const int cc = lane % SEG, rr = lane / SEG;
-            const int c = g * SEG + cc;
-            if (full_rows && (g + 1) * SEG <= nx) {
-                int cell = base0 + rr * dr + c * dc;
-                const T* src = stage + rr * RING + (c & (RING - 1));
-#pragma unroll
-                for (int r0 = 0; r0 < 32; r0 += RPI) {
-                    Is[cell] = *src;
-                    cell += RPI * dr;
-                    src += RPI * RING;
-                }
-                return;
-            }
-#pragma unroll
-            for (int r0 = 0; r0 < 32; r0 += RPI) {
-                const int r = r0 + rr;
-                const int jr = band * 32 + r;
-                if (c < nx && jr < ny) {
-                    const int jj = ypos ? jr : ny - 1 - jr;
-                    const int ii = xpos ? c : nx - 1 - c;
-                    Is[(size_t)jj * nx + ii] = stage[r * RING + (c & (RING - 1))];
-                }
-            }
-        };
-
-        prefetch(0, 0);
-        for (int m = 0; m < nchunks; ++m) {
-            const int t0 = m * SEG, b = m & 1;
-            if (m + 1 < nchunks) prefetch(m + 1, b ^ 1);
-            else cp_async_commit();   // empty group keeps the wait count uniform
-            // south values of lane 0 for columns t0 .. t0+SEG-1, one per lane
-            if (t0 < nx) {
-                edge_reg = T(0);
+                cp_async_mbar_arrive(full + b);
+                // south values of lane 0 for columns t0 .. t0 + SEG - 1
+                T ev = T(0);
+                const bool need = lane < SEG && t0 + lane < nx;
                 if (band == 0) {
-                    if (a.inflow && lane < SEG && t0 + lane < nx) {
+                    if (need && a.inflow) {
                         const int c = t0 + lane;
                         const int i = xpos ? c : nx - 1 - c;
                         const int f = ypos ? 2 * ny + i : 2 * ny + nx + i;
-                        edge_reg = (T)a.inflow[(size_t)f * K + k];
+                        ev = (T)a.inflow[(size_t)f * K + k];
                     }
                 } else {
-                    int ok = 1;
-                    if (lane == 0) {
-                        const unsigned long long need = a.epoch_hi | (unsigned long long)min(nx, t0 + SEG);
-                        ok = wait_at_least(flag_in, need, a.wait_cycles, a.err) ? 1 : 0;
+                    bool have = !need;
+                    const long long start = clock64();
+                    for (;;) {
+                        if (!have) {
+                            const typename B::U u = B::load(edge_in + t0 + lane);
+                            if (u != B::empty) {
+                                have = true;
+                                ev = B::value(u);
+                            }
+                        }
+                        if (__all_sync(kFull, have)) break;
+                        if (__any_sync(kFull, clock64() - start > budget)) {   // warp-uniform exit
+                            if (lane == 0) atomicOr(a.err, kErrTimeout);
+                            cp_async_wait_all();
+                            return;
+                        }
+                        __nanosleep(20);
                     }
-                    ok = __shfl_sync(kFull, ok, 0);
-                    if (!ok) {
-                        cp_async_wait<0>();   // no copy of ours stays in flight
-                        return;
-                    }
-                    if (lane < SEG && t0 + lane < nx) edge_reg = __ldcg(edge_in + t0 + lane);
                 }
+                if (lane < SEG) reinterpret_cast<T*>(bp + SM::off_e)[lane] = ev;
+                mbar_arrive(full + b);
             }
-            cp_async_wait<1>();   // chunk m has landed
-            __syncwarp();
-            const T* wb = win + b * NW * SM::WIN + lane * RS;
-            const T* ab = win_a + b * AW + 31 - lane;
-            const double* rb = win_r + b * SEG * 32 + lane;
-            if (full_rows && t0 >= 31 && t0 + SEG <= nx) {
-                // interior chunk: every lane updates a cell at every step
-                T* st = stage + lane * RING;
-                const int cbase = t0 - lane;
-                T* eo = edge_out + cbase;
-                const bool put_edge = lane == 31 && band < nb - 1;
+            // every value of the upstream hand-off row has been taken:
+            // mark it unwritten for the next sweep
+            if (band > 0)
+                for (int c = lane; c < nx; c += 32) B::clear(edge_in + c);
+        } else {
+            // ------------------------------------------------- compute warp
+            const T bj = row_ok ? a.bcoef[(size_t)s * ny + j] : T(0);
+            T IW = T(0);
+            if (row_ok && a.inflow) IW = (T)a.inflow[(size_t)(xpos ? j : ny + j) * K + k];
+            T Iprev = T(0);
+            T* eo = a.edge + ((size_t)s * nb + band) * nx;   // this band's last row, by column
+            const bool put_edge = lane == 31 && band < nb - 1;
+            for (int m = 0; m < nchunks; ++m, ++g) {
+                const int b = (int)(g % NBUF);
+                const bool ok = __all_sync(kFull, mbar_wait(full + b, (g / NBUF) & 1, budget));
+                if (!ok) {
+                    if (lane == 0) atomicOr(a.err, kErrTimeout);
+                    return;
+                }
+                const unsigned char* bp = buf(b);
+                const T* wb = reinterpret_cast<const T*>(bp) + lane * RS;
+                const T* ab = reinterpret_cast<const T*>(bp + SM::off_a) + 31 - lane;
+                const double* rb = reinterpret_cast<const double*>(bp + SM::off_r) + lane;
+                const T* ein = reinterpret_cast<const T*>(bp + SM::off_e);
+                const int t0 = m * SEG;
+                if (full_rows && t0 >= 31 && t0 + SEG <= nx) {
+                    // interior chunk: every lane updates a cell at every step
+                    T* Ic = Is + base0 + lane * dr + (t0 - lane) * dc;
+                    T* ec = eo + (t0 - 31);
 #pragma unroll
-                for (int tt = 0; tt < SEG; ++tt) {
-                    T Isouth = __shfl_up_sync(kFull, Iprev, 1);
-                    const T e = __shfl_sync(kFull, edge_reg, tt);
-                    if (lane == 0) Isouth = e;
-                    T sv = wb[SM::W_SRC * SM::WIN + tt];
-                    const T ai = ab[tt];
-                    T rinv;
-                    if (PRE) {
-                        if (PT) sv = fma(wb[SM::W_SHIFT * SM::WIN + tt], wb[SM::W_IOLD * SM::WIN + tt], sv);
-                        rinv = (T)rb[tt * 32];
-                    } else {
-                        T d = wb[SM::W_SIGT * SM::WIN + tt] + ai + bj;
-                        if (PT) {
-                            const T sh = wb[SM::W_SHIFT * SM::WIN + tt];
-                            sv = fma(sh, wb[SM::W_IOLD * SM::WIN + tt], sv);
-                            d += sh;
+                    for (int tt = 0; tt < SEG; ++tt) {
+                        // lane l gets lane l-1's previous result; lane 0 the south value
+                        const T e = ein[tt];
+                        const T Isouth = __shfl_sync(kFull, lane == 31 ? e : Iprev, (lane + 31) & 31);
+                        T sv = wb[SM::W_SRC * SM::WIN + tt];
+                        const T ai = ab[tt];
+                        T rinv;
+                        if (PRE) {
+                            if (PT) sv = fma(wb[SM::W_SHIFT * SM::WIN + tt], wb[SM::W_IOLD * SM::WIN + tt], sv);
+                            rinv = (T)rb[tt * 32];
+                        } else {
+                            T d = wb[SM::W_SIGT * SM::WIN + tt] + ai + bj;
+                            if (PT) {
+                                const T sh = wb[SM::W_SHIFT * SM::WIN + tt];
+                                sv = fma(sh, wb[SM::W_IOLD * SM::WIN + tt], sv);
+                                d += sh;
+                            }
+                            rinv = rcp_t(d);
                         }
-                        rinv = rcp_t(d);
+                        T acc = fma(ai, IW, sv);
+                        acc = fma(bj, Isouth, acc);
+                        const T Inew = acc * rinv;
+                        IW = Inew;
+                        Iprev = Inew;
+                        Ic[tt * dc] = Inew;
+                        if (put_edge) B::store(ec + tt, Inew);
                     }
-                    T acc = fma(ai, IW, sv);
-                    acc = fma(bj, Isouth, acc);
-                    const T Inew = acc * rinv;
-                    IW = Inew;
-                    Iprev = Inew;
-                    st[(cbase + tt) & (RING - 1)] = Inew;
-                    if (put_edge) eo[tt] = Inew;
-                }
-            } else
+                } else {
 #pragma unroll 4
-            for (int tt = 0; tt < SEG; ++tt) {
-                const int t = t0 + tt;
-                if (t >= a.nsteps) break;
-                T Isouth = __shfl_up_sync(kFull, Iprev, 1);
-                const T e = __shfl_sync(kFull, edge_reg, tt);
-                if (lane == 0) Isouth = e;
-                const int c = t - lane;
-                T Inew = T(0);
-                if (row_ok && c >= 0 && c < nx) {
-                    T sv = wb[SM::W_SRC * SM::WIN + tt];
-                    const T ai = ab[tt];
-                    T rinv;
-                    if (PRE) {
-                        if (PT) sv = fma(wb[SM::W_SHIFT * SM::WIN + tt], wb[SM::W_IOLD * SM::WIN + tt], sv);
-                        rinv = (T)rb[tt * 32];
-                    } else {
-                        T d = wb[SM::W_SIGT * SM::WIN + tt] + ai + bj;
-                        if (PT) {
-                            const T sh = wb[SM::W_SHIFT * SM::WIN + tt];
-                            sv = fma(sh, wb[SM::W_IOLD * SM::WIN + tt], sv);
-                            d += sh;
+                    for (int tt = 0; tt < SEG; ++tt) {
+                        const int t = t0 + tt;
+                        if (t >= a.nsteps) break;
+                        const T e = ein[tt];
+                        const T Isouth = __shfl_sync(kFull, lane == 31 ? e : Iprev, (lane + 31) & 31);
+                        const int c = t - lane;
+                        T Inew = T(0);
+                        if (row_ok && c >= 0 && c < nx) {
+                            T sv = wb[SM::W_SRC * SM::WIN + tt];
+                            const T ai = ab[tt];
+                            T rinv;
+                            if (PRE) {
+                                if (PT) sv = fma(wb[SM::W_SHIFT * SM::WIN + tt], wb[SM::W_IOLD * SM::WIN + tt], sv);
+                                rinv = (T)rb[tt * 32];
+                            } else {
+                                T d = wb[SM::W_SIGT * SM::WIN + tt] + ai + bj;
+                                if (PT) {
+                                    const T sh = wb[SM::W_SHIFT * SM::WIN + tt];
+                                    sv = fma(sh, wb[SM::W_IOLD * SM::WIN + tt], sv);
+                                    d += sh;
+                                }
+                                rinv = rcp_t(d);
+                            }
+                            T acc = fma(ai, IW, sv);
+                            acc = fma(bj, Isouth, acc);
+                            Inew = acc * rinv;
+                            IW = Inew;
+                            Is[base0 + lane * dr + c * dc] = Inew;
+                            if (put_edge) B::store(eo + c, Inew);
                         }
-                        rinv = rcp_t(d);
+                        Iprev = Inew;
                     }
-                    T acc = fma(ai, IW, sv);
-                    acc = fma(bj, Isouth, acc);
-                    Inew = acc * rinv;
-                    IW = Inew;
-                    stage[lane * RING + (c & (RING - 1))] = Inew;
-                    if (lane == 31 && band < nb - 1) edge_out[c] = Inew;
                 }
-                Iprev = Inew;
+                mbar_arrive(empty + b);
             }
-            if (band < nb - 1 && lane == 31) {
-                const int cols = min(nx, t0 + SEG - 31);
-                // edge_out is written by this lane only: the release store
-                // orders those writes before the flag.
-                if (cols > 0) st_release_u64(flag_out, a.epoch_hi | (unsigned long long)cols);
-            }
-            __syncwarp();
-            const int last_complete = m - LAG;
-            while (flushed <= last_complete && flushed * SEG < nx) {
-                flush(flushed);
-                ++flushed;
-            }
-            __syncwarp();
         }
-        cp_async_wait<0>();
-        while (flushed * SEG < nx) {
-            flush(flushed);
-            ++flushed;
-        }
-        __syncwarp();
     }
+    if (copier) cp_async_wait_all();
 }
 
 // --------------------------------------------------------------- moments
@@ -510,7 +540,6 @@ struct MomArgs {
     double* rho; double* Fx; double* Fy;                    // may be null (F)
     double* Pxx; double* Pxy; double* Pyy;                  // may be null
     const double* rho_new;                                  // GSIS correction of P (or null)
-    unsigned long long* tasks;                              // sweep counter to re-arm
     const int* done;
 };
 
@@ -522,7 +551,6 @@ __global__ void __launch_bounds__(kRedBlock) moments_kernel(const MomArgs<T> a)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* cf = reinterpret_cast<T*>(smem_raw);                     // [K][6]
     int* sk = reinterpret_cast<int*>(cf + 6 * a.K);             // [K]
-    if (blockIdx.x == 0 && threadIdx.x == 0) *a.tasks = 0ull;    // re-arm the sweep task counter
     if (a.done && ld_volatile_int(a.done)) return;
     for (int k = threadIdx.x; k < a.K; k += blockDim.x) {
         const double w = a.w[k], m = a.mu[k], e = a.eta[k];
@@ -627,16 +655,12 @@ cudaError_t launch_sweep_t(Plan& P, cudaStream_t st)
     a.rsw = P.rsw;
     a.I = static_cast<T*>(P.I);
     a.edge = static_cast<T*>(P.edge);
-    a.flags = P.flags;
-    P.epoch += 1;
-    a.epoch_hi = P.epoch << 20;
     a.inflow = P.inflow;
     a.perm = P.perm; a.qmu = P.qmu; a.qeta = P.qeta;
-    a.tasks = &P.status->sweep_tasks;
     a.err = &P.status->error;
     a.done = &P.status->done;
     a.wait_cycles = P.wait_cycles;
-    sweep_kernel<T, PT, PRE><<<P.sweep_grid, kSweepWarps * 32, sweep_smem<T, PT>(), st>>>(a);
+    sweep_kernel<T, PT, PRE><<<P.sweep_grid, kSweepPairs * 64, sweep_smem<T, PT>(), st>>>(a);
     return cudaGetLastError();
 }
 
@@ -662,7 +686,6 @@ cudaError_t launch_moments_t(const Plan& P, bool with_F, bool with_P, double* rh
     a.Fy = Fout ? Fout + P.N : P.Fy;
     if (with_P) { a.Pxx = Pout; a.Pxy = Pout + P.N; a.Pyy = Pout + 2 * (size_t)P.N; }
     a.rho_new = gsis_correct ? P.rho_m : nullptr;
-    a.tasks = &P.status->sweep_tasks;
     a.done = force ? nullptr : &P.status->done;
     const size_t smem = moments_smem<T>(P.K);
     const int grid = grid_for(P.N, kRedBlock, P.num_sms * 8);
@@ -702,7 +725,7 @@ template <typename T, bool PT>
 int sweep_occupancy()
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<T, PT, sizeof(T) == 8>, kSweepWarps * 32,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<T, PT, sizeof(T) == 8>, kSweepPairs * 64,
                                                       sweep_smem<T, PT>()) != cudaSuccess)
         return 0;
     return n;
@@ -732,7 +755,7 @@ cudaError_t launch_setup(const Plan& P, cudaStream_t st)
 cudaError_t launch_cell_setup(const Plan& P, double cfl_p, double beta, cudaStream_t st)
 {
     cell_setup_kernel<<<grid_for(P.N, 256, P.num_sms * 8), 256, 0, st>>>(
-        P.nx, P.ny, P.dx, P.dy, P.sigma_a, P.sigma_s, P.q, cfl_p, beta, P.sigt,
+        P.nx, P.ny, P.dx, P.dy, P.sigma_a, P.sigma_s, P.q, P.inflow, P.nbf * P.K, cfl_p, beta, P.sigt,
         P.fp32 ? P.sigt_f : nullptr, P.shift, P.fp32 ? P.shift_f : nullptr, P.diag, P.cx, P.cy,
         &P.status->error);
     cudaError_t e = cudaGetLastError();
