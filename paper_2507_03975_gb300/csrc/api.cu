@@ -156,6 +156,8 @@ size_t layout(const Sizes& z, char* base, Plan* P)
     p.fb = reinterpret_cast<double*>(take(nbf * sizeof(double)));
     double** syn[] = {&p.diag, &p.cx, &p.cy, &p.hotx, &p.hoty, &p.b, &p.x, &p.r, &p.z, &p.p, &p.qv};
     for (double** d : syn) *d = reinterpret_cast<double*>(take(N * sizeof(double)));
+    p.hw = reinterpret_cast<double*>(take(4 * N * sizeof(double)));
+    p.bface = reinterpret_cast<double*>(take(nbf * sizeof(double)));
     p.partials = reinterpret_cast<double*>(take(11 * (size_t)kMaxCgBlocks * sizeof(double)));
     // multigrid hierarchy: 2x2 aggregation down to a single cell
     {
@@ -195,8 +197,6 @@ int check_mesh(const gsis_mesh* m)
     if (!m) return fail(GSIS_ERR_ARG, "mesh is NULL");
     if (m->nx < 1 || m->ny < 1 || m->nx > kMaxSide || m->ny > kMaxSide)
         return fail(GSIS_ERR_ARG, "mesh size %d x %d out of range [1, %d]", m->nx, m->ny, kMaxSide);
-    if ((long long)m->nx * m->ny > (1LL << 30))
-        return fail(GSIS_ERR_ARG, "mesh of %d x %d cells exceeds 2^30 cells", m->nx, m->ny);
     if ((long long)m->nx * m->ny > (1LL << 30)) return fail(GSIS_ERR_ARG, "too many cells");
     if (!m->dx || !m->dy) return fail(GSIS_ERR_ARG, "mesh spacing arrays are NULL");
     for (int i = 0; i < m->nx; ++i)
@@ -462,7 +462,7 @@ int gsis_solve(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis_op
             TIMED(GSIS_KCLASS_MOMENTS, 2,
                   launch_moments_to(P, gsis, false, P.rho_h, nullptr, nullptr, false, P.fb, false, st));
             if (gsis) {
-                TIMED(GSIS_KCLASS_HOT_RHS, 2, launch_hot_rhs(P, P.rho_h, P.Fx, P.Fy, P.fb, st));
+                TIMED(GSIS_KCLASS_HOT_RHS, 2, launch_hot_rhs(P, P.rho_h, P.Fx, P.Fy, P.fb, P.rho_m, st));
                 TIMED(GSIS_KCLASS_SYNTH, 1, launch_synthetic_solve(P, P.rho_m, P.x, st));
                 TIMED(GSIS_KCLASS_UPDATE, 1, launch_update(P, P.x, st));
             } else {
@@ -545,8 +545,9 @@ int gsis_synthetic_step(const gsis_mesh* mesh, const gsis_options* opt, const do
     Plan P{};
     layout(z, static_cast<char*>(workspace), &P);
     if ((rc = prepare(P, mesh, nullptr, &o, sigma_a, sigma_s, q, nullptr, st))) return rc;
-    TIMED(GSIS_KCLASS_HOT_RHS, 2, launch_hot_rhs(P, rho_half, F_half, F_half + P.N, bflux, st));
-    TIMED(GSIS_KCLASS_SYNTH, 1, launch_synthetic_solve(P, rho_guess ? rho_guess : rho_half, rho_out, st));
+    const double* guess = rho_guess ? rho_guess : rho_half;
+    TIMED(GSIS_KCLASS_HOT_RHS, 2, launch_hot_rhs(P, rho_half, F_half, F_half + P.N, bflux, guess, st));
+    TIMED(GSIS_KCLASS_SYNTH, 1, launch_synthetic_solve(P, guess, rho_out, st));
     if (hot) {
         CK(cudaMemcpyAsync(hot, P.hotx, (size_t)P.N * sizeof(double), cudaMemcpyDeviceToDevice, st));
         CK(cudaMemcpyAsync(hot + P.N, P.hoty, (size_t)P.N * sizeof(double), cudaMemcpyDeviceToDevice, st));

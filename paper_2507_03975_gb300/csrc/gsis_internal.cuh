@@ -94,6 +94,8 @@ struct Plan {
     double* Fx; double* Fy; double* fb;
     // synthetic
     double* diag; double* cx; double* cy;
+    double* hw;                     // [4][N] HoT gradient weights E, W, N, S (with 1/(3 sigma_t))
+    double* bface;                  // [nbf] boundary face area * beta
     double* hotx; double* hoty; double* b;
     double* x; double* r; double* z; double* p; double* qv;
     double* partials;               // reductions scratch
@@ -114,8 +116,10 @@ cudaError_t launch_moments_to(const Plan& P, bool with_F, bool with_P, double* r
 cudaError_t prepare_kernels(int K, int fp32, int pt);
 int sweep_max_active_blocks(int fp32, int pt);
 cudaError_t launch_source_from(const Plan& P, const double* rho_in, cudaStream_t st);
+// HoT, right-hand side b and the first residual b - D guess of the synthetic
+// solve (FP32 copy in mg.r0, norms at partials + 4 * kMaxCgBlocks).
 cudaError_t launch_hot_rhs(const Plan& P, const double* rho_h, const double* Fx, const double* Fy,
-                           const double* fb, cudaStream_t st);
+                           const double* fb, const double* guess, cudaStream_t st);
 cudaError_t launch_mg_setup(const Plan& P, cudaStream_t st);
 cudaError_t launch_synthetic_solve(const Plan& P, const double* guess, double* out, cudaStream_t st);
 int mg_cluster_size();

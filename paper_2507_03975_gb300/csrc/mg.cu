@@ -18,6 +18,7 @@
 // Warm start x0 = previous rho: the correction vanishes with the residual,
 // so a capped number of inner iterations (the paper's capped LU-SGS/SOR
 // sub-iterations of Sec. 4.2) leaves the GSIS fixed point unchanged.
+#include <algorithm>
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -556,6 +557,536 @@ __global__ void __launch_bounds__(kMgBlock) mg_solve_kernel(const MgArgs a)
     cx.sync();
 }
 
+// ------------------------------------------------------------ strip solver
+// The same iteration (FP64 refinement around FP32 MG-PCG, identical cycle)
+// with every level resident in the cluster's shared memory.  Levels 0..ld
+// are cut into row strips, one per CTA; the cut is made on level P = ld + 1
+// and doubled downwards, so a coarse cell and its children always live in
+// the same CTA and the grid transfers stay local.  Each strip array carries
+// one halo row above and below; a phase that writes a boundary row also
+// stores it into the neighbour's halo row (distributed shared memory) before
+// the cluster barrier, so every read after the barrier is local.  Levels P..
+// live whole in CTA 0: the other CTAs store their restricted rows of level P
+// into CTA 0, and CTA 0 stores level P's correction back into every CTA.
+// Reductions store each CTA's partial into every CTA's slot table and sum
+// the table in a fixed order: all CTAs get the same bits.
+constexpr int kSA_D = 0, kSA_ID = 1, kSA_CX = 2, kSA_CY = 3, kSA_X = 4, kSA_T = 5, kSA_R = 6;
+constexpr int kSA_P = 7, kSA_DL = 8;   // level 0 only
+constexpr int kMaxCl = 16;
+
+struct SLevel {
+    int nx, ny;
+    int cap;       // floats per array: (largest strip or whole level + 2 halo rows) * nx, 16-byte multiple
+    int off;       // float offset of the level's arrays in dynamic shared memory
+    const float* gd; const float* gcx; const float* gcy;
+};
+
+struct SArgs {
+    int nl, ld, cl;
+    SLevel lv[kMaxLevels];
+    int nx, ny, N;
+    const double* diag; const double* cx; const double* cy;
+    const double* b; const double* guess; double* x;
+    const float* r0;       // b - D guess (FP32), computed with b
+    const double* norms;   // [0] = |b - D guess|^2, [1] = |b|^2 (FP64)
+    double rtol;
+    int max_iter, nu;
+    float inner_rtol, omega, alpha;
+    Status* status;
+};
+
+// This CTA's part of one level: rows [rs, rs + rows); array k at float
+// offset off + k * cap, cell (jj, i) at (jj + 1) * nx + i.
+struct Strip {
+    int nx, ny, rs, rows, cap, off, prev_rows;
+    bool prev, next;   // neighbouring strips exist (strip levels only)
+};
+
+extern __shared__ __align__(16) float sm_f[];
+
+__device__ __forceinline__ float* sarr(const Strip S, int k) { return sm_f + S.off + k * S.cap; }
+
+__device__ __forceinline__ void strip_rows(const SArgs& a, int l, int r, int& rs, int& re)
+{
+    const int P = a.ld + 1, nyP = a.lv[P].ny;
+    const int s0 = (int)((long long)r * nyP / a.cl), s1 = (int)((long long)(r + 1) * nyP / a.cl);
+    const int sh = P - l;
+    rs = s0 << sh;
+    re = min(s1 << sh, a.lv[l].ny);
+}
+
+// Visit this thread's cells of a strip: f(padded index, column, local row);
+// thread tid of nt threads takes cells tid, tid + nt, ...
+template <class F>
+__device__ __forceinline__ void each_cell(const Strip S, F f, int tid, int nt)
+{
+    const int nx = S.nx, n = S.rows * nx;
+    int lc = tid;
+    if (lc >= n) return;
+    int jj = lc / nx, i = lc - jj * nx;
+    const int sj = nt / nx, si = nt - sj * nx;
+    for (; lc < n; lc += nt) {
+        f(lc + nx, i, jj);
+        i += si;
+        jj += sj;
+        if (i >= nx) {
+            i -= nx;
+            ++jj;
+        }
+    }
+}
+
+template <class F>
+__device__ __forceinline__ void each_cell(const Strip S, F f)
+{
+    each_cell(S, f, (int)threadIdx.x, (int)blockDim.x);
+}
+
+// (A v)(cell) with v = array k; rows outside the strip come from the halos.
+__device__ __forceinline__ float strip_Av(const Strip S, int k, int c, int i, int jj)
+{
+    const float* base = sm_f + S.off;
+    const float* v = base + k * S.cap;
+    const float* cxa = base + kSA_CX * S.cap;
+    const float* cya = base + kSA_CY * S.cap;
+    const int nx = S.nx, j = S.rs + jj;
+    float y = base[kSA_D * S.cap + c] * v[c];
+    if (i + 1 < nx) y -= cxa[c] * v[c + 1];
+    if (i > 0) y -= cxa[c - 1] * v[c - 1];
+    if (j + 1 < S.ny) y -= cya[c] * v[c + nx];
+    if (j > 0) y -= cya[c - nx] * v[c - nx];
+    return y;
+}
+
+class SCluster {
+  public:
+    __device__ SCluster() : cl_(cg::this_cluster())
+    {
+        rank_ = (int)cl_.block_rank();
+        n_ = (int)cl_.num_blocks();
+    }
+    __device__ void sync() { cl_.sync(); }
+    __device__ int rank() const { return rank_; }
+    __device__ int size() const { return n_; }
+    template <typename V>
+    __device__ V* remote(V* p, int r) { return cl_.map_shared_rank(p, r); }
+    // Fixed-order sums over the cluster, identical bits in every thread of
+    // every CTA.  slots: [3][kMaxCl][2] rotating tables (a table is written
+    // again only after two more barriers, so one barrier per sum suffices).
+    template <typename V>
+    __device__ void sum2(V a, V b, V out[2], V* slots, int& rot, V* wsm)
+    {
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(kFull, a, o);
+            b += __shfl_xor_sync(kFull, b, o);
+        }
+        __syncthreads();   // wsm free (previous use complete)
+        if (lane == 0) {
+            wsm[wid] = a;
+            wsm[32 + wid] = b;
+        }
+        __syncthreads();
+        V* table = slots + rot * (2 * kMaxCl);
+        if (threadIdx.x < n_) {   // thread q stores this CTA's partial into CTA q's table
+            V ta = V(0), tb = V(0);
+            for (int w = 0; w < nw; ++w) {
+                ta += wsm[w];
+                tb += wsm[32 + w];
+            }
+            V* dst = cl_.map_shared_rank(table, (int)threadIdx.x);
+            dst[2 * rank_] = ta;
+            dst[2 * rank_ + 1] = tb;
+        }
+        cl_.sync();
+        V s0 = lane < n_ ? table[2 * lane] : V(0), s1 = lane < n_ ? table[2 * lane + 1] : V(0);
+        for (int o = 16; o > 0; o >>= 1) {
+            s0 += __shfl_xor_sync(kFull, s0, o);
+            s1 += __shfl_xor_sync(kFull, s1, o);
+        }
+        out[0] = s0;
+        out[1] = s1;
+        rot = (rot + 1) % 3;
+    }
+
+  private:
+    cg::cluster_group cl_;
+    int rank_, n_;
+};
+
+__device__ __forceinline__ int other_buf(int k) { return k == kSA_X ? kSA_T : kSA_X; }
+
+__global__ void __launch_bounds__(kMgBlock) mg_strip_kernel(const SArgs a)
+{
+    __shared__ float slots_f[3 * 2 * kMaxCl];
+    __shared__ double slots_d[3 * 2 * kMaxCl];
+    __shared__ float wsm_f[64];
+    __shared__ double wsm_d[64];
+    __shared__ Strip St[kMaxLevels];
+    SCluster cx;
+    if (ld_volatile_int(&a.status->done)) return;   // same value in every CTA
+    const int r = cx.rank(), ld = a.ld, P = ld + 1, nl = a.nl, nu = a.nu;
+    const float om = a.omega, alpha = a.alpha;
+    const int down_buf = (nu % 2) ? kSA_X : kSA_T;   // pre-smoothed iterate; post-smoothed: kSA_T
+    float* prev_sm = r > 0 ? cx.remote(sm_f, r - 1) : nullptr;
+    float* next_sm = r + 1 < cx.size() ? cx.remote(sm_f, r + 1) : nullptr;
+
+    if (threadIdx.x < nl) {
+        const int l = threadIdx.x;
+        Strip S;
+        S.nx = a.lv[l].nx;
+        S.ny = a.lv[l].ny;
+        S.cap = a.lv[l].cap;
+        S.off = a.lv[l].off;
+        S.rs = 0;
+        S.rows = S.ny;
+        S.prev_rows = 0;
+        S.prev = false;
+        S.next = false;
+        if (l <= ld) {
+            int rs, re;
+            strip_rows(a, l, r, rs, re);
+            S.rs = rs;
+            S.rows = re - rs;
+            if (r > 0) {
+                int ps, pe;
+                strip_rows(a, l, r - 1, ps, pe);
+                S.prev_rows = pe - ps;
+                S.prev = true;
+            }
+            S.next = r + 1 < cx.size();
+        }
+        St[l] = S;
+    }
+    // zero every array (halo rows on the domain boundary stay zero)
+    {
+        const int tot = a.lv[nl - 1].off + 7 * a.lv[nl - 1].cap;
+        for (int c = threadIdx.x; c < tot; c += blockDim.x) sm_f[c] = 0.f;
+    }
+    __syncthreads();
+    // coefficients of the levels this CTA holds (and the south coupling of
+    // row 0): one flat index over all of them, 4 items' loads in flight per thread
+    __shared__ int first[kMaxLevels + 1];
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int l = 0; l < nl; ++l) {
+            first[l] = acc;
+            if (l <= ld || r == 0) acc += St[l].rows * St[l].nx + (St[l].rs > 0 ? St[l].nx : 0);
+        }
+        first[nl] = acc;
+    }
+    __syncthreads();
+    {
+        const int tot = first[nl];
+        constexpr int U = 4;
+        for (int e0 = threadIdx.x; e0 < tot; e0 += U * blockDim.x) {
+            float dv[U], xv[U], yv[U];
+            int lv[U], cc[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + u * blockDim.x;
+                lv[u] = -1;
+                if (e < tot) {
+                    int l = 0;
+                    while (first[l + 1] <= e) ++l;
+                    const Strip S = St[l];
+                    const SLevel& L = a.lv[l];
+                    const int c = e - first[l] - (S.rs > 0 ? S.nx : 0);   // c < 0: south halo row
+                    const int g = S.rs * S.nx + c;
+                    lv[u] = l;
+                    cc[u] = c;
+                    yv[u] = L.gcy[g];
+                    if (c >= 0) {
+                        dv[u] = L.gd[g];
+                        xv[u] = L.gcx[g];
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (lv[u] < 0) continue;
+                const Strip S = St[lv[u]];
+                const int c = cc[u] + S.nx;   // padded index
+                sarr(S, kSA_CY)[c] = yv[u];
+                if (cc[u] >= 0) {
+                    sarr(S, kSA_D)[c] = dv[u];
+                    sarr(S, kSA_ID)[c] = 1.f / dv[u];
+                    sarr(S, kSA_CX)[c] = xv[u];
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    // store v into array k of strip S at (c, i, jj), and into the neighbours' halo rows
+    auto put = [&](const Strip S, int k, int c, int i, int jj, float v) {
+        sarr(S, k)[c] = v;
+        if (jj == 0 && S.prev) prev_sm[S.off + k * S.cap + (S.prev_rows + 1) * S.nx + i] = v;
+        if (jj == S.rows - 1 && S.next) next_sm[S.off + k * S.cap + i] = v;
+    };
+    // `steps` damped-Jacobi steps from buffer cur; returns the buffer of the
+    // result.  mode 0: strip level, every thread, cluster barriers; 1: level
+    // held whole by CTA 0, every thread, block barriers; 2: the same with the
+    // lanes of warp 0 alone and warp barriers (small levels).
+    auto jacobi = [&](const Strip S, int cur, int steps, int mode) {
+        const float* rr = sarr(S, kSA_R);
+        const float* id = sarr(S, kSA_ID);
+        const int tid = mode == 2 ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
+        const int nt = mode == 2 ? 32 : (int)blockDim.x;
+        for (int k = 0; k < steps; ++k) {
+            if (mode == 0) cx.sync();
+            else if (mode == 1) __syncthreads();
+            else __syncwarp();
+            const int oth = other_buf(cur), c0 = cur;
+            const float* src = sarr(S, cur);
+            each_cell(S, [&](int c, int i, int jj) {
+                put(S, oth, c, i, jj, src[c] + om * (rr[c] - strip_Av(S, c0, c, i, jj)) * id[c]);
+            }, tid, nt);
+            cur = oth;
+        }
+        return cur;
+    };
+    // residual of buffer cur summed over 2x2 children into coarse rows
+    // row0.. of the padded coarse array cr (coarse width cnx), thread tid of nt
+    auto restrict_to = [&](const Strip S, int cur, float* cr, int cnx, int row0, int tid, int nt) {
+        const float* rr = sarr(S, kSA_R);
+        const int crows = (S.rows + 1) / 2, nx = S.nx;
+        for (int cc = tid; cc < crows * cnx; cc += nt) {
+            const int JJ = cc / cnx, I = cc - JJ * cnx;
+            float sum = 0.f;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int i = 2 * I + (q & 1), jj = 2 * JJ + (q >> 1);
+                if (i < nx && jj < S.rows) {
+                    const int c = (jj + 1) * nx + i;
+                    sum += rr[c] - strip_Av(S, cur, c, i, jj);
+                }
+            }
+            cr[(row0 + JJ + 1) * cnx + I] = sum;
+        }
+    };
+
+    // z = M^{-1} s: one V-cycle, input level-0 R, output level-0 T
+    auto vcycle = [&]() {
+        for (int l = 0; l <= ld; ++l) {   // down over the strips
+            const Strip S = St[l];
+            {
+                const float* rr = sarr(S, kSA_R);
+                const float* id = sarr(S, kSA_ID);
+                each_cell(S, [&](int c, int i, int jj) { put(S, kSA_X, c, i, jj, om * rr[c] * id[c]); });
+            }
+            const int cur = jacobi(S, kSA_X, nu - 1, 0);
+            cx.sync();
+            const Strip C = St[l + 1];
+            if (l < ld) {
+                restrict_to(S, cur, sarr(C, kSA_R), C.nx, 0, threadIdx.x, blockDim.x);
+                __syncthreads();
+            } else {   // level P rows go to CTA 0
+                restrict_to(S, cur, cx.remote(sarr(C, kSA_R), 0), C.nx, S.rs / 2, threadIdx.x, blockDim.x);
+            }
+        }
+        cx.sync();
+        if (r == 0) {   // levels P.. whole in CTA 0: every thread on levels of more
+                        // than 64 cells, warp 0 alone below (cheaper barriers)
+            int wl = P;
+            while (wl < nl - 1 && St[wl].rows * St[wl].nx > 64) ++wl;
+            auto down = [&](int l, int mode) {
+                const Strip L = St[l];
+                const int tid = mode == 2 ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
+                const int nt = mode == 2 ? 32 : (int)blockDim.x;
+                const float* rr = sarr(L, kSA_R);
+                const float* id = sarr(L, kSA_ID);
+                float* xv = sarr(L, kSA_X);
+                each_cell(L, [&](int c, int, int) { xv[c] = om * rr[c] * id[c]; }, tid, nt);
+                const int cur = jacobi(L, kSA_X, nu - 1, mode);
+                if (mode == 2) __syncwarp();
+                else __syncthreads();
+                const Strip C = St[l + 1];
+                restrict_to(L, cur, sarr(C, kSA_R), C.nx, 0, tid, nt);
+                if (mode == 2) __syncwarp();
+                else __syncthreads();
+            };
+            auto up = [&](int l, int mode) {
+                const Strip L = St[l];
+                const Strip C = St[l + 1];
+                const int tid = mode == 2 ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
+                const int nt = mode == 2 ? 32 : (int)blockDim.x;
+                float* xv = sarr(L, down_buf);
+                const float* ct = sarr(C, kSA_T);
+                each_cell(L, [&](int c, int i, int j) { xv[c] += alpha * ct[(j / 2 + 1) * C.nx + i / 2]; }, tid, nt);
+                jacobi(L, down_buf, nu, mode);
+                if (mode == 2) __syncwarp();
+                else __syncthreads();
+            };
+            for (int l = P; l < wl; ++l) down(l, 1);
+            if (threadIdx.x < 32) {
+                for (int l = wl; l < nl - 1; ++l) down(l, 2);
+                const Strip L = St[nl - 1];
+                const float* rr = sarr(L, kSA_R);
+                const float* id = sarr(L, kSA_ID);
+                float* tv = sarr(L, kSA_T);
+                each_cell(L, [&](int c, int, int) { tv[c] = rr[c] * id[c]; }, (int)threadIdx.x, 32);
+                __syncwarp();
+                for (int l = nl - 2; l >= wl; --l) up(l, 2);
+            }
+            __syncthreads();
+            for (int l = wl - 1; l >= P; --l) up(l, 1);
+            __syncthreads();
+            // level P's correction into every other CTA
+            const Strip C = St[P];
+            const float* ct = sarr(C, kSA_T) + C.nx;
+            const int n = C.rows * C.nx;
+            for (int q = 1; q < cx.size(); ++q) {
+                float* dst = cx.remote(sarr(C, kSA_T), q) + C.nx;
+                for (int c = threadIdx.x; c < n; c += blockDim.x) dst[c] = ct[c];
+            }
+        }
+        cx.sync();
+        for (int l = ld; l >= 0; --l) {   // up over the strips
+            const Strip S = St[l];
+            const Strip C = St[l + 1];
+            const float* ct = sarr(C, kSA_T);
+            const float* xo = sarr(S, down_buf);
+            const int crow0 = l == ld ? S.rs / 2 : 0;   // level P is held whole
+            each_cell(S, [&](int c, int i, int jj) {
+                put(S, down_buf, c, i, jj, xo[c] + alpha * ct[(crow0 + jj / 2 + 1) * C.nx + i / 2]);
+            });
+            jacobi(S, down_buf, nu, 0);
+            __syncthreads();
+        }
+    };
+
+    const Strip S0 = St[0];
+    const int nx = a.nx, ny = a.ny;
+    const int n0 = S0.rows * nx, g00 = S0.rs * nx;
+    float* s_ = sarr(S0, kSA_R) + nx;
+    float* dl_ = sarr(S0, kSA_DL) + nx;
+    const float* z_ = sarr(S0, kSA_T) + nx;
+    const float* p_ = sarr(S0, kSA_P) + nx;
+    int rotf = 0, rotd = 0;
+    int total = 0;
+    double relres = 0.0;
+    const double bb = a.norms[1];
+    __shared__ int stop_now;
+    for (int outer = 0;; ++outer) {
+        // residual s = b - D x: from the right-hand-side pass on the first
+        // pass (x = guess), else in FP64 here
+        double rr;
+        if (outer == 0) {
+            for (int c = threadIdx.x; c < n0; c += blockDim.x) {
+                s_[c] = a.r0[g00 + c];
+                dl_[c] = 0.f;
+            }
+            rr = a.norms[0];
+        } else {
+            cx.sync();   // every CTA's x update visible
+            double lrr = 0.0;
+            for (int c0 = threadIdx.x; c0 < n0; c0 += 2 * blockDim.x) {
+                double xc[2], xe[2], xw[2], xn[2], xs[2], dg[2], ce[2], cw[2], cn[2], cs[2], bv[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {   // loads only (indices clamped into the strip's rows)
+                    const int c = min(c0 + u * blockDim.x, n0 - 1);
+                    const int g = g00 + c, jj = c / nx, i = c - jj * nx, j = S0.rs + jj;
+                    const int ge = i + 1 < nx ? g + 1 : g, gw = i > 0 ? g - 1 : g;
+                    const int gn = j + 1 < ny ? g + nx : g, gs = j > 0 ? g - nx : g;
+                    xc[u] = __ldcg(a.x + g);
+                    xe[u] = __ldcg(a.x + ge);
+                    xw[u] = __ldcg(a.x + gw);
+                    xn[u] = __ldcg(a.x + gn);
+                    xs[u] = __ldcg(a.x + gs);
+                    dg[u] = a.diag[g];
+                    ce[u] = i + 1 < nx ? a.cx[g] : 0.0;
+                    cw[u] = i > 0 ? a.cx[gw] : 0.0;
+                    cn[u] = j + 1 < ny ? a.cy[g] : 0.0;
+                    cs[u] = j > 0 ? a.cy[gs] : 0.0;
+                    bv[u] = a.b[g];
+                }
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int c = c0 + u * blockDim.x;
+                    if (c < n0) {
+                        const double v = dg[u] * xc[u] - ce[u] * xe[u] - cw[u] * xw[u] - cn[u] * xn[u] - cs[u] * xs[u];
+                        const double rv = bv[u] - v;
+                        s_[c] = (float)rv;
+                        dl_[c] = 0.f;
+                        lrr += rv * rv;
+                    }
+                }
+            }
+            double v2[2];
+            cx.sum2<double>(lrr, 0.0, v2, slots_d, rotd, wsm_d);
+            rr = v2[0];
+        }
+        // stop test in one thread (FP64 is slow here; every thread reads the verdict)
+        if (threadIdx.x == 0) {
+            relres = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+            stop_now = (rr <= a.rtol * a.rtol * bb || total >= a.max_iter) ? 1 : 0;
+        }
+        __syncthreads();
+        if (stop_now) {
+            if (outer == 0)
+                for (int c = threadIdx.x; c < n0; c += blockDim.x) a.x[g00 + c] = a.guess[g00 + c];
+            break;
+        }
+        // FP32 MG-PCG for D d = s, d = 0 to start
+        vcycle();
+        float f2[2];
+        {
+            float l0 = 0.f, l1 = 0.f;
+            each_cell(S0, [&](int c, int i, int jj) {
+                const float z = z_[c - nx], sv = s_[c - nx];
+                put(S0, kSA_P, c, i, jj, z);
+                l0 += sv * z;
+                l1 += sv * sv;
+            });
+            cx.sum2<float>(l0, l1, f2, slots_f, rotf, wsm_f);
+        }
+        float rz = f2[0];
+        const float istop = a.inner_rtol * a.inner_rtol * f2[1];
+        while (total < a.max_iter && rz > 0.f) {
+            // the previous barrier published p and its halo rows
+            float lpq = 0.f;
+            each_cell(S0, [&](int c, int i, int jj) { lpq += p_[c - nx] * strip_Av(S0, kSA_P, c, i, jj); });
+            cx.sum2<float>(lpq, 0.f, f2, slots_f, rotf, wsm_f);
+            const float al = rz / f2[0];
+            float lss = 0.f;
+            each_cell(S0, [&](int c, int i, int jj) {   // q = A p again (same bits) instead of storing it
+                dl_[c - nx] += al * p_[c - nx];
+                const float sc = s_[c - nx] - al * strip_Av(S0, kSA_P, c, i, jj);
+                s_[c - nx] = sc;
+                lss += sc * sc;
+            });
+            ++total;
+            cx.sum2<float>(lss, 0.f, f2, slots_f, rotf, wsm_f);
+            if (f2[0] <= istop || total >= a.max_iter) break;
+            vcycle();
+            float lrz = 0.f;
+            for (int c = threadIdx.x; c < n0; c += blockDim.x) lrz += s_[c] * z_[c];
+            cx.sum2<float>(lrz, 0.f, f2, slots_f, rotf, wsm_f);
+            const float be = f2[0] / rz;
+            rz = f2[0];
+            each_cell(S0, [&](int c, int i, int jj) { put(S0, kSA_P, c, i, jj, z_[c - nx] + be * p_[c - nx]); });
+            cx.sync();   // p and its halo rows visible before the product
+        }
+        {
+            const double* xo = outer == 0 ? a.guess : a.x;
+            for (int c = threadIdx.x; c < n0; c += blockDim.x) a.x[g00 + c] = xo[g00 + c] + (double)dl_[c];
+        }
+        if (total >= a.max_iter) {   // budget spent: no further residual evaluation
+            relres = -1.0;
+            break;
+        }
+        __syncthreads();   // stop_now is rewritten by thread 0 on the next pass
+    }
+    if (r == 0 && threadIdx.x == 0) {
+        a.status->synth_iters = total;
+        a.status->synth_iters_total += total;
+        a.status->synth_relres = relres;
+    }
+    // no CTA may leave while another can still store into its shared memory
+    cx.sync();
+}
+
 }  // namespace
 
 // Builds the level hierarchy (once per call; D does not change).
@@ -576,8 +1107,121 @@ cudaError_t launch_mg_setup(const Plan& P, cudaStream_t st)
     return cudaSuccess;
 }
 
+namespace {
+
+// Strip plan for cluster size cl: false if level 1 has fewer rows than CTAs
+// or the levels do not fit the shared memory of one CTA.
+bool strip_plan(const Plan& P, int cl, size_t smem_cap, SArgs& sa, size_t& bytes)
+{
+    const MgPlan& g = P.mg;
+    if (cl < 2 || cl > kMaxCl || g.nl < 2) return false;
+    int ld = -1;
+    for (int l = 0; l + 1 < g.nl; ++l)
+        if (g.ny[l + 1] >= cl) ld = l;
+    if (ld < 0) return false;
+    const int Pl = ld + 1, nyP = g.ny[Pl];
+    size_t off = 0;
+    for (int l = 0; l < g.nl; ++l) {
+        int rows = g.ny[l];
+        if (l <= ld) {
+            rows = 0;
+            for (int r = 0; r < cl; ++r) {
+                const int s0 = (int)((long long)r * nyP / cl), s1 = (int)((long long)(r + 1) * nyP / cl);
+                const int rs = s0 << (Pl - l), re = std::min(s1 << (Pl - l), g.ny[l]);
+                rows = std::max(rows, re - rs);
+            }
+        }
+        long long cap = (long long)(rows + 2) * g.nx[l];
+        cap = (cap + 3) / 4 * 4;   // 16-byte aligned arrays
+        const int narr = l == 0 ? 9 : 7;
+        sa.lv[l] = SLevel{g.nx[l], g.ny[l], (int)cap, (int)off, g.d[l], g.cx[l], g.cy[l]};
+        off += (size_t)narr * (size_t)cap;
+        if (off * sizeof(float) > smem_cap) return false;
+    }
+    sa.nl = g.nl;
+    sa.ld = ld;
+    sa.cl = cl;
+    bytes = off * sizeof(float);
+    return true;
+}
+
+cudaError_t launch_cluster(const void* fn, void** args, int cl, size_t smem, cudaStream_t st)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(cl);
+    cfg.blockDim = dim3(kMgBlock);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+int clusters_fit(const void* fn, int cl, size_t smem)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(cl);
+    cfg.blockDim = dim3(kMgBlock);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+}  // namespace
+
+// The strip solver when its plan fits a schedulable cluster (16 or 8 CTAs),
+// else the solver with the fine levels in global memory.
 cudaError_t launch_synthetic_solve(const Plan& P, const double* guess, double* out, cudaStream_t st)
 {
+    {
+        int dev = 0, cap = 0;
+        cudaFuncAttributes fa{};
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&cap, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+            cudaFuncGetAttributes(&fa, mg_strip_kernel) == cudaSuccess) {
+            const size_t smem_cap = (size_t)cap > fa.sharedSizeBytes ? (size_t)cap - fa.sharedSizeBytes : 0;
+            for (int cl = std::min(P.mg.cluster, 16); cl >= 8; cl /= 2) {
+                SArgs sa{};
+                size_t bytes = 0;
+                if (!strip_plan(P, cl, smem_cap, sa, bytes)) continue;
+                cudaError_t e = cudaFuncSetAttribute(mg_strip_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)bytes);
+                if (e != cudaSuccess) return e;
+                if (clusters_fit((const void*)mg_strip_kernel, cl, bytes) < 1) continue;
+                sa.nx = P.nx; sa.ny = P.ny; sa.N = P.N;
+                sa.diag = P.diag; sa.cx = P.cx; sa.cy = P.cy; sa.b = P.b; sa.guess = guess; sa.x = out;
+                sa.r0 = P.mg.r0;
+                sa.norms = P.partials + (size_t)4 * kMaxCgBlocks;
+                sa.rtol = P.synth_rtol;
+                sa.max_iter = P.synth_max_iter;
+                sa.nu = 2;
+                sa.inner_rtol = 1e-4f;
+                sa.omega = 0.8f;
+                sa.alpha = 1.8f;
+                sa.status = P.status;
+                void* args[] = {&sa};
+                return launch_cluster((const void*)mg_strip_kernel, args, cl, bytes, st);
+            }
+        } else {
+            cudaGetLastError();
+        }
+    }
     MgArgs a{};
     a.nl = P.mg.nl;
     a.local_from = P.mg.local_from;
@@ -623,6 +1267,9 @@ cudaError_t launch_synthetic_solve(const Plan& P, const double* guess, double* o
 int mg_cluster_size()
 {
     if (cudaFuncSetAttribute(mg_solve_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+    }
+    if (cudaFuncSetAttribute(mg_strip_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
         cudaGetLastError();
     }
     for (int c = 16; c >= 1; c /= 2) {

@@ -27,7 +27,7 @@ namespace gsis {
 
 namespace {
 
-constexpr double kFourPi = 12.566370614359172953850573533118;
+constexpr double kInvFourPi = 0.079577471545947667884441881686257;   // 1 / (4 pi)
 
 // --------------------------------------------------------------- set-up
 // |mu_s|/dx_i and |eta_s|/dy_j per sorted direction (both precisions).
@@ -65,7 +65,7 @@ __global__ void cell_setup_kernel(int nx, int ny, const double* __restrict__ dx,
                                   const double* __restrict__ inflow, int n_inflow,
                                   double cfl_p, double beta, double* sigt, float* sigt_f,
                                   double* shift, float* shift_f, double* diag, double* cx,
-                                  double* cy, int* err)
+                                  double* cy, double* hw, double* bface, int* err)
 {
     const int N = nx * ny;
     if (inflow)
@@ -118,6 +118,29 @@ __global__ void cell_setup_kernel(int nx, int ny, const double* __restrict__ dx,
         diag[c] = d;
         cx[c] = hy * gE;
         cy[c] = hx * gN;
+        // adaptive least-squares gradient on the Cartesian mesh (Eqs. (shifted_j),
+        // (new_vector), (LSF_mdf)): G_x = sum_{E,W} d_j (rho_j - rho_i) / sum d_j^2
+        // with d_E = +(hx/2 + (sigma_E/sigma_i) dx_E/2), d_W = -(...); the weights
+        // d_j / sum d^2 carry the 1/(3 sigma_t) of the high-order terms (Eq. (GSIS_HoT))
+        {
+            double dE = 0.0, dW = 0.0, dN = 0.0, dS = 0.0;
+            if (i + 1 < nx) dE = 0.5 * hx + ((sa[c + 1] + ss[c + 1]) / st) * 0.5 * dx[i + 1];
+            if (i > 0) dW = -(0.5 * hx + ((sa[c - 1] + ss[c - 1]) / st) * 0.5 * dx[i - 1]);
+            if (j + 1 < ny) dN = 0.5 * hy + ((sa[c + nx] + ss[c + nx]) / st) * 0.5 * dy[j + 1];
+            if (j > 0) dS = -(0.5 * hy + ((sa[c - nx] + ss[c - nx]) / st) * 0.5 * dy[j - 1]);
+            const double inv3s = 1.0 / (3.0 * st);
+            const double sx = dE * dE + dW * dW, sy = dN * dN + dS * dS;
+            const double fx = sx > 0.0 ? inv3s / sx : 0.0, fy = sy > 0.0 ? inv3s / sy : 0.0;
+            hw[c] = dE * fx;
+            hw[N + c] = dW * fx;
+            hw[2 * N + c] = dN * fy;
+            hw[3 * N + c] = dS * fy;
+        }
+        // boundary faces: area * beta (Eq. (macro_bc_delta_flux)), faces W, E, S, N
+        if (i == 0) bface[j] = hy * bx;
+        if (i == nx - 1) bface[ny + j] = hy * bx;
+        if (j == 0) bface[2 * ny + i] = hx * by;
+        if (j == ny - 1) bface[2 * ny + nx + i] = hx * by;
     }
 }
 
@@ -169,7 +192,7 @@ __global__ void source_kernel(int N, const double* __restrict__ ss, const double
                               const double* __restrict__ rho, double* src, float* src_f)
 {
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
-        const double v = (ss[c] * rho[c] + q[c]) / kFourPi;
+        const double v = (ss[c] * rho[c] + q[c]) * kInvFourPi;
         src[c] = v;
         if (src_f) src_f[c] = (float)v;
     }
@@ -218,6 +241,12 @@ template <> struct Bits<double> {
     }
     static __device__ __forceinline__ double value(U u) { return __longlong_as_double((long long)u); }
     static __device__ __forceinline__ void clear(double* p) { *reinterpret_cast<U*>(p) = empty; }
+    // plain store of a result; no compiler memory clobber, so the shared-memory
+    // loads of the next steps may be issued ahead of it
+    static __device__ __forceinline__ void put(double* p, double v)
+    {
+        asm volatile("st.global.f64 [%0], %1;" ::"l"(p), "d"(v));
+    }
 };
 template <> struct Bits<float> {
     using U = unsigned int;
@@ -234,6 +263,10 @@ template <> struct Bits<float> {
     }
     static __device__ __forceinline__ float value(U u) { return __uint_as_float(u); }
     static __device__ __forceinline__ void clear(float* p) { *reinterpret_cast<U*>(p) = empty; }
+    static __device__ __forceinline__ void put(float* p, float v)
+    {
+        asm volatile("st.global.f32 [%0], %1;" ::"l"(p), "f"(v));
+    }
 };
 
 // Shared-memory plan of one (compute, copy) warp pair.  A chunk is SEG
@@ -485,7 +518,7 @@ sweep_kernel(const SweepArgs<T> a)
                         const T Inew = acc * rinv;
                         IW = Inew;
                         Iprev = Inew;
-                        Ic[tt * dc] = Inew;
+                        B::put(Ic + tt * dc, Inew);
                         if (put_edge) B::store(ec + tt, Inew);
                     }
                 } else {
@@ -517,7 +550,7 @@ sweep_kernel(const SweepArgs<T> a)
                             acc = fma(bj, Isouth, acc);
                             Inew = acc * rinv;
                             IW = Inew;
-                            Is[base0 + lane * dr + c * dc] = Inew;
+                            B::put(Is + base0 + lane * dr + c * dc, Inew);
                             if (put_edge) B::store(eo + c, Inew);
                         }
                         Iprev = Inew;
@@ -756,8 +789,8 @@ cudaError_t launch_cell_setup(const Plan& P, double cfl_p, double beta, cudaStre
 {
     cell_setup_kernel<<<grid_for(P.N, 256, P.num_sms * 8), 256, 0, st>>>(
         P.nx, P.ny, P.dx, P.dy, P.sigma_a, P.sigma_s, P.q, P.inflow, P.nbf * P.K, cfl_p, beta, P.sigt,
-        P.fp32 ? P.sigt_f : nullptr, P.shift, P.fp32 ? P.shift_f : nullptr, P.diag, P.cx, P.cy,
-        &P.status->error);
+        P.fp32 ? P.sigt_f : nullptr, P.shift, P.fp32 ? P.shift_f : nullptr, P.diag, P.cx, P.cy, P.hw,
+        P.bface, &P.status->error);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (!P.fp32) {

@@ -21,7 +21,7 @@ namespace gsis {
 
 namespace {
 
-constexpr double kFourPi = 12.566370614359172953850573533118;
+constexpr double kInvFourPi = 0.079577471545947667884441881686257;   // 1 / (4 pi)
 
 int grid_for(long long n, int block, int cap)
 {
@@ -31,69 +31,97 @@ int grid_for(long long n, int block, int cap)
     return (int)g;
 }
 
-__global__ void hot_kernel(int nx, int ny, const double* __restrict__ dx, const double* __restrict__ dy,
-                           const double* __restrict__ sigt, const double* __restrict__ rho,
-                           const double* __restrict__ Fx, const double* __restrict__ Fy,
-                           double* hotx, double* hoty, const int* done)
+// HoT = F + G / (3 sigma_t) with the gradient weights of the cell set-up.
+__global__ void hot_kernel(int nx, int ny, const double* __restrict__ hw, const double* __restrict__ rho,
+                           const double* __restrict__ Fx, const double* __restrict__ Fy, double* hotx,
+                           double* hoty, const int* done)
 {
     if (ld_volatile_int(done)) return;
     const int N = nx * ny;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
         const int j = c / nx, i = c - j * nx;
-        const double si = sigt[c], ri = rho[c];
-        double num = 0.0, den = 0.0;
-        if (i + 1 < nx) {
-            const double d = 0.5 * dx[i] + (sigt[c + 1] / si) * 0.5 * dx[i + 1];
-            num += d * (rho[c + 1] - ri);
-            den += d * d;
-        }
-        if (i > 0) {
-            const double d = -(0.5 * dx[i] + (sigt[c - 1] / si) * 0.5 * dx[i - 1]);
-            num += d * (rho[c - 1] - ri);
-            den += d * d;
-        }
-        const double gx = den > 0.0 ? num / den : 0.0;
-        num = 0.0;
-        den = 0.0;
-        if (j + 1 < ny) {
-            const double d = 0.5 * dy[j] + (sigt[c + nx] / si) * 0.5 * dy[j + 1];
-            num += d * (rho[c + nx] - ri);
-            den += d * d;
-        }
-        if (j > 0) {
-            const double d = -(0.5 * dy[j] + (sigt[c - nx] / si) * 0.5 * dy[j - 1]);
-            num += d * (rho[c - nx] - ri);
-            den += d * d;
-        }
-        const double gy = den > 0.0 ? num / den : 0.0;
-        hotx[c] = Fx[c] + gx / (3.0 * si);
-        hoty[c] = Fy[c] + gy / (3.0 * si);
+        const double ri = rho[c];
+        double gx = 0.0, gy = 0.0;
+        if (i + 1 < nx) gx = fma(hw[c], rho[c + 1] - ri, gx);
+        if (i > 0) gx = fma(hw[N + c], rho[c - 1] - ri, gx);
+        if (j + 1 < ny) gy = fma(hw[2 * N + c], rho[c + nx] - ri, gy);
+        if (j > 0) gy = fma(hw[3 * N + c], rho[c - nx] - ri, gy);
+        hotx[c] = Fx[c] + gx;
+        hoty[c] = Fy[c] + gy;
     }
 }
 
-__global__ void rhs_kernel(int nx, int ny, const double* __restrict__ dx, const double* __restrict__ dy,
-                           const double* __restrict__ sigt, const double* __restrict__ q,
-                           const double* __restrict__ rho_h, const double* __restrict__ hotx,
-                           const double* __restrict__ hoty, const double* __restrict__ fb, double* b,
-                           const int* done)
+struct RhsArgs {
+    int nx, ny;
+    const double* dx; const double* dy;
+    const double* sigt; const double* q; const double* rho_h;
+    const double* hotx; const double* hoty; const double* fb; const double* bface;
+    double* b;
+    // first residual of the synthetic solve, r0 = b - D guess
+    const double* diag; const double* cx; const double* cy; const double* guess;
+    float* r0;          // FP32 copy for the inner iteration
+    double* partials;   // [2][gridDim]
+    double* norms;      // out: [0] = r0.r0, [1] = b.b
+    Status* status;
+};
+
+// b, then r0 = b - D guess (five-point D) and the fixed-order sums r0.r0, b.b
+// (last-block ticket).
+__global__ void __launch_bounds__(kRedBlock) rhs_kernel(const RhsArgs a)
 {
-    if (ld_volatile_int(done)) return;
-    const int N = nx * ny;
+    __shared__ double sm[33];
+    __shared__ int am_last;
+    if (ld_volatile_int(&a.status->done)) return;
+    const int nx = a.nx, ny = a.ny, N = nx * ny;
+    const double* dx = a.dx; const double* dy = a.dy;
+    const double* hotx = a.hotx; const double* hoty = a.hoty; const double* fb = a.fb;
+    double lrr = 0.0, lbb = 0.0;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
         const int j = c / nx, i = c - j * nx;
         const double hx = dx[i], hy = dy[j];
-        double v = hx * hy * q[c];
+        double v = hx * hy * a.q[c];
         if (i + 1 < nx) v -= hy * 0.5 * (hotx[c] + hotx[c + 1]);
         if (i > 0) v += hy * 0.5 * (hotx[c] + hotx[c - 1]);
         if (j + 1 < ny) v -= hx * 0.5 * (hoty[c] + hoty[c + nx]);
         if (j > 0) v += hx * 0.5 * (hoty[c] + hoty[c - nx]);
-        const double st = sigt[c], rh = rho_h[c];
-        const double bx = 2.0 / (3.0 * st * hx) + 0.25, by = 2.0 / (3.0 * st * hy) + 0.25;
-        if (i == 0) v -= hy * (fb[j] - bx * rh);
-        if (i == nx - 1) v -= hy * (fb[ny + j] - bx * rh);
-        if (j == 0) v -= hx * (fb[2 * ny + i] - by * rh);
-        if (j == ny - 1) v -= hx * (fb[2 * ny + nx + i] - by * rh);
-        b[c] = v;
+        const double rh = a.rho_h[c];
+        const double* bf = a.bface;
+        if (i == 0) v -= hy * fb[j] - bf[j] * rh;
+        if (i == nx - 1) v -= hy * fb[ny + j] - bf[ny + j] * rh;
+        if (j == 0) v -= hx * fb[2 * ny + i] - bf[2 * ny + i] * rh;
+        if (j == ny - 1) v -= hx * fb[2 * ny + nx + i] - bf[2 * ny + nx + i] * rh;
+        a.b[c] = v;
+        const double* g = a.guess;
+        double dg = a.diag[c] * g[c];
+        if (i + 1 < nx) dg -= a.cx[c] * g[c + 1];
+        if (i > 0) dg -= a.cx[c - 1] * g[c - 1];
+        if (j + 1 < ny) dg -= a.cy[c] * g[c + nx];
+        if (j > 0) dg -= a.cy[c - nx] * g[c - nx];
+        const double rv = v - dg;
+        a.r0[c] = (float)rv;
+        lrr += rv * rv;
+        lbb += v * v;
+    }
+    lrr = block_sum(lrr, sm);
+    lbb = block_sum(lbb, sm);
+    if (threadIdx.x == 0) {
+        a.partials[blockIdx.x] = lrr;
+        a.partials[gridDim.x + blockIdx.x] = lbb;
+        __threadfence();
+        const unsigned t = atomicAdd(&a.status->ticket, 1u);
+        am_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!am_last) return;
+    if (threadIdx.x < 32) {
+        __threadfence();
+        const double srr = warp_sum_array(a.partials, gridDim.x);
+        const double sbb = warp_sum_array(a.partials + gridDim.x, gridDim.x);
+        if (threadIdx.x == 0) {
+            a.norms[0] = srr;
+            a.norms[1] = sbb;
+            a.status->ticket = 0u;
+        }
     }
 }
 
@@ -129,8 +157,8 @@ __global__ void __launch_bounds__(kRedBlock) update_kernel(const UpdArgs a)
         num += (nw - od) * (nw - od) * V;
         den += nw * nw * V;
         a.rho_m[c] = nw;
-        double s = (a.sigma_s[c] * nw + a.q[c]) / kFourPi;
-        if (a.pt) s += a.shift[c] * (nw - a.rho_h[c]) / kFourPi;
+        double s = (a.sigma_s[c] * nw + a.q[c]) * kInvFourPi;
+        if (a.pt) s += a.shift[c] * (nw - a.rho_h[c]) * kInvFourPi;
         a.src[c] = s;
         if (a.src_f) a.src_f[c] = (float)s;
     }
@@ -175,15 +203,22 @@ __global__ void __launch_bounds__(kRedBlock) update_kernel(const UpdArgs a)
 }  // namespace
 
 cudaError_t launch_hot_rhs(const Plan& P, const double* rho_h, const double* Fx, const double* Fy,
-                           const double* fb, cudaStream_t st)
+                           const double* fb, const double* guess, cudaStream_t st)
 {
     const int g = grid_for(P.N, 256, P.num_sms * 8);
-    hot_kernel<<<g, 256, 0, st>>>(P.nx, P.ny, P.dx, P.dy, P.sigt, rho_h, Fx, Fy, P.hotx, P.hoty,
-                                  &P.status->done);
+    hot_kernel<<<g, 256, 0, st>>>(P.nx, P.ny, P.hw, rho_h, Fx, Fy, P.hotx, P.hoty, &P.status->done);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    rhs_kernel<<<g, 256, 0, st>>>(P.nx, P.ny, P.dx, P.dy, P.sigt, P.q, rho_h, P.hotx, P.hoty, fb, P.b,
-                                  &P.status->done);
+    RhsArgs a{};
+    a.nx = P.nx; a.ny = P.ny; a.dx = P.dx; a.dy = P.dy;
+    a.sigt = P.sigt; a.q = P.q; a.rho_h = rho_h; a.hotx = P.hotx; a.hoty = P.hoty; a.fb = fb; a.b = P.b;
+    a.bface = P.bface;
+    a.diag = P.diag; a.cx = P.cx; a.cy = P.cy; a.guess = guess;
+    a.r0 = P.mg.r0;
+    a.partials = P.partials;
+    a.norms = P.partials + (size_t)4 * kMaxCgBlocks;
+    a.status = P.status;
+    rhs_kernel<<<P.red_grid, kRedBlock, 0, st>>>(a);
     return cudaGetLastError();
 }
 
