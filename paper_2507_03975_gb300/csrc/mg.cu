@@ -642,19 +642,31 @@ __device__ __forceinline__ void each_cell(const Strip S, F f)
     each_cell(S, f, (int)threadIdx.x, (int)blockDim.x);
 }
 
-// (A v)(cell) with v = array k; rows outside the strip come from the halos.
-__device__ __forceinline__ float strip_Av(const Strip S, int k, int c, int i, int jj)
+// Visit this thread's cells by padded index only.
+template <class F>
+__device__ __forceinline__ void each_c(const Strip S, F f, int tid, int nt)
+{
+    const int end = (S.rows + 1) * S.nx;
+    for (int c = S.nx + tid; c < end; c += nt) f(c);
+}
+
+// (A v)(cell) with v = array k at padded index c; rows outside the strip come
+// from the halos.  No branches: a coupling to a missing neighbour is zero (the
+// operator and its Galerkin coarsenings have zero face coefficients on the
+// domain boundary, halo rows there stay zero), and every neighbour index stays
+// inside the padded array.
+__device__ __forceinline__ float strip_Av(const Strip S, int k, int c)
 {
     const float* base = sm_f + S.off;
     const float* v = base + k * S.cap;
     const float* cxa = base + kSA_CX * S.cap;
     const float* cya = base + kSA_CY * S.cap;
-    const int nx = S.nx, j = S.rs + jj;
+    const int nx = S.nx;
     float y = base[kSA_D * S.cap + c] * v[c];
-    if (i + 1 < nx) y -= cxa[c] * v[c + 1];
-    if (i > 0) y -= cxa[c - 1] * v[c - 1];
-    if (j + 1 < S.ny) y -= cya[c] * v[c + nx];
-    if (j > 0) y -= cya[c - nx] * v[c - nx];
+    y -= cxa[c] * v[c + 1];
+    y -= cxa[c - 1] * v[c - 1];
+    y -= cya[c] * v[c + nx];
+    y -= cya[c - nx] * v[c - nx];
     return y;
 }
 
@@ -818,11 +830,12 @@ __global__ void __launch_bounds__(kMgBlock) mg_strip_kernel(const SArgs a)
     }
     __syncthreads();
 
-    // store v into array k of strip S at (c, i, jj), and into the neighbours' halo rows
-    auto put = [&](const Strip S, int k, int c, int i, int jj, float v) {
+    // store v into array k of strip S at padded index c, and into the
+    // neighbours' halo rows when c lies in the first or last row
+    auto put = [&](const Strip S, int k, int c, float v) {
         sarr(S, k)[c] = v;
-        if (jj == 0 && S.prev) prev_sm[S.off + k * S.cap + (S.prev_rows + 1) * S.nx + i] = v;
-        if (jj == S.rows - 1 && S.next) next_sm[S.off + k * S.cap + i] = v;
+        if (S.prev && c < 2 * S.nx) prev_sm[S.off + k * S.cap + S.prev_rows * S.nx + c] = v;
+        if (S.next && c >= S.rows * S.nx) next_sm[S.off + k * S.cap + c - S.rows * S.nx] = v;
     };
     // `steps` damped-Jacobi steps from buffer cur; returns the buffer of the
     // result.  mode 0: strip level, every thread, cluster barriers; 1: level
@@ -839,9 +852,7 @@ __global__ void __launch_bounds__(kMgBlock) mg_strip_kernel(const SArgs a)
             else __syncwarp();
             const int oth = other_buf(cur), c0 = cur;
             const float* src = sarr(S, cur);
-            each_cell(S, [&](int c, int i, int jj) {
-                put(S, oth, c, i, jj, src[c] + om * (rr[c] - strip_Av(S, c0, c, i, jj)) * id[c]);
-            }, tid, nt);
+            each_c(S, [&](int c) { put(S, oth, c, src[c] + om * (rr[c] - strip_Av(S, c0, c)) * id[c]); }, tid, nt);
             cur = oth;
         }
         return cur;
@@ -859,7 +870,7 @@ __global__ void __launch_bounds__(kMgBlock) mg_strip_kernel(const SArgs a)
                 const int i = 2 * I + (q & 1), jj = 2 * JJ + (q >> 1);
                 if (i < nx && jj < S.rows) {
                     const int c = (jj + 1) * nx + i;
-                    sum += rr[c] - strip_Av(S, cur, c, i, jj);
+                    sum += rr[c] - strip_Av(S, cur, c);
                 }
             }
             cr[(row0 + JJ + 1) * cnx + I] = sum;
@@ -873,7 +884,7 @@ __global__ void __launch_bounds__(kMgBlock) mg_strip_kernel(const SArgs a)
             {
                 const float* rr = sarr(S, kSA_R);
                 const float* id = sarr(S, kSA_ID);
-                each_cell(S, [&](int c, int i, int jj) { put(S, kSA_X, c, i, jj, om * rr[c] * id[c]); });
+                each_c(S, [&](int c) { put(S, kSA_X, c, om * rr[c] * id[c]); }, threadIdx.x, blockDim.x);
             }
             const int cur = jacobi(S, kSA_X, nu - 1, 0);
             cx.sync();
@@ -897,7 +908,7 @@ __global__ void __launch_bounds__(kMgBlock) mg_strip_kernel(const SArgs a)
                 const float* rr = sarr(L, kSA_R);
                 const float* id = sarr(L, kSA_ID);
                 float* xv = sarr(L, kSA_X);
-                each_cell(L, [&](int c, int, int) { xv[c] = om * rr[c] * id[c]; }, tid, nt);
+                each_c(L, [&](int c) { xv[c] = om * rr[c] * id[c]; }, tid, nt);
                 const int cur = jacobi(L, kSA_X, nu - 1, mode);
                 if (mode == 2) __syncwarp();
                 else __syncthreads();
@@ -925,7 +936,7 @@ __global__ void __launch_bounds__(kMgBlock) mg_strip_kernel(const SArgs a)
                 const float* rr = sarr(L, kSA_R);
                 const float* id = sarr(L, kSA_ID);
                 float* tv = sarr(L, kSA_T);
-                each_cell(L, [&](int c, int, int) { tv[c] = rr[c] * id[c]; }, (int)threadIdx.x, 32);
+                each_c(L, [&](int c) { tv[c] = rr[c] * id[c]; }, (int)threadIdx.x, 32);
                 __syncwarp();
                 for (int l = nl - 2; l >= wl; --l) up(l, 2);
             }
@@ -949,7 +960,7 @@ __global__ void __launch_bounds__(kMgBlock) mg_strip_kernel(const SArgs a)
             const float* xo = sarr(S, down_buf);
             const int crow0 = l == ld ? S.rs / 2 : 0;   // level P is held whole
             each_cell(S, [&](int c, int i, int jj) {
-                put(S, down_buf, c, i, jj, xo[c] + alpha * ct[(crow0 + jj / 2 + 1) * C.nx + i / 2]);
+                put(S, down_buf, c, xo[c] + alpha * ct[(crow0 + jj / 2 + 1) * C.nx + i / 2]);
             });
             jacobi(S, down_buf, nu, 0);
             __syncthreads();
@@ -1033,12 +1044,12 @@ __global__ void __launch_bounds__(kMgBlock) mg_strip_kernel(const SArgs a)
         float f2[2];
         {
             float l0 = 0.f, l1 = 0.f;
-            each_cell(S0, [&](int c, int i, int jj) {
+            each_c(S0, [&](int c) {
                 const float z = z_[c - nx], sv = s_[c - nx];
-                put(S0, kSA_P, c, i, jj, z);
+                put(S0, kSA_P, c, z);
                 l0 += sv * z;
                 l1 += sv * sv;
-            });
+            }, threadIdx.x, blockDim.x);
             cx.sum2<float>(l0, l1, f2, slots_f, rotf, wsm_f);
         }
         float rz = f2[0];
@@ -1046,16 +1057,16 @@ __global__ void __launch_bounds__(kMgBlock) mg_strip_kernel(const SArgs a)
         while (total < a.max_iter && rz > 0.f) {
             // the previous barrier published p and its halo rows
             float lpq = 0.f;
-            each_cell(S0, [&](int c, int i, int jj) { lpq += p_[c - nx] * strip_Av(S0, kSA_P, c, i, jj); });
+            each_c(S0, [&](int c) { lpq += p_[c - nx] * strip_Av(S0, kSA_P, c); }, threadIdx.x, blockDim.x);
             cx.sum2<float>(lpq, 0.f, f2, slots_f, rotf, wsm_f);
             const float al = rz / f2[0];
             float lss = 0.f;
-            each_cell(S0, [&](int c, int i, int jj) {   // q = A p again (same bits) instead of storing it
+            each_c(S0, [&](int c) {   // q = A p again (same bits) instead of storing it
                 dl_[c - nx] += al * p_[c - nx];
-                const float sc = s_[c - nx] - al * strip_Av(S0, kSA_P, c, i, jj);
+                const float sc = s_[c - nx] - al * strip_Av(S0, kSA_P, c);
                 s_[c - nx] = sc;
                 lss += sc * sc;
-            });
+            }, threadIdx.x, blockDim.x);
             ++total;
             cx.sum2<float>(lss, 0.f, f2, slots_f, rotf, wsm_f);
             if (f2[0] <= istop || total >= a.max_iter) break;
@@ -1065,7 +1076,7 @@ __global__ void __launch_bounds__(kMgBlock) mg_strip_kernel(const SArgs a)
             cx.sum2<float>(lrz, 0.f, f2, slots_f, rotf, wsm_f);
             const float be = f2[0] / rz;
             rz = f2[0];
-            each_cell(S0, [&](int c, int i, int jj) { put(S0, kSA_P, c, i, jj, z_[c - nx] + be * p_[c - nx]); });
+            each_c(S0, [&](int c) { put(S0, kSA_P, c, z_[c - nx] + be * p_[c - nx]); }, threadIdx.x, blockDim.x);
             cx.sync();   // p and its halo rows visible before the product
         }
         {
