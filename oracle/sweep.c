@@ -156,3 +156,55 @@ int oracle_sweep(int nx, int ny, const double* dx, const double* dy, int K,
     free(dI);
     return 0;
 }
+
+/*
+ * Transposed kinetic operator (adjoint of the kinetic step).  The sweep above
+ * solves, for each ordinate k, the lower-triangular system A_k I_k = S with
+ *   (A_k)_cc = sigma_t,c + sum_{faces f of c, Omega.n >= 0} (Omega.n A_f)/V_c,
+ *   (A_k)_cn = (Omega.n_f A_f)/V_c  for the inflow faces f (Omega.n < 0) of c,
+ *   n the neighbour across f.
+ * This routine solves A_k^T phi_k = psi_k: row n of A_k^T couples n to the
+ * cells c that take n as an upwind neighbour, i.e. the neighbours across the
+ * faces of n with Omega.n_f > 0, with the coefficient -(Omega.n_f A_f)/V_c
+ * seen from n.  Those cells come after n in upwind order, so the system is
+ * solved by visiting the cells in reverse upwind order.  psi and phi are
+ * [K][N]; there is no boundary term (inflow enters the forward problem as a
+ * source, not through A_k).
+ */
+int oracle_sweep_transposed(int nx, int ny, const double* dx, const double* dy, int K,
+                            const double* mu, const double* eta, const double* sigma_t,
+                            const double* psi, double* phi)
+{
+    const int N = nx * ny;
+    for (int k = 0; k < K; ++k) {
+        const double m = mu[k], e = eta[k];
+        const double* pk = psi + (size_t)k * N;
+        double* fk = phi + (size_t)k * N;
+        const int i0 = (m >= 0.0) ? 0 : nx - 1, di = (m >= 0.0) ? 1 : -1;
+        const int j0 = (e >= 0.0) ? 0 : ny - 1, dj = (e >= 0.0) ? 1 : -1;
+        for (int jj = ny - 1; jj >= 0; --jj) {
+            const int j = j0 + dj * jj;
+            for (int ii = nx - 1; ii >= 0; --ii) {
+                const int i = i0 + di * ii;
+                const int n = i + nx * j;
+                const double V = dx[i] * dy[j];
+                const double An[4] = {dy[j], dy[j], dx[i], dx[i]};   /* W E S N */
+                const double on[4] = {-m, m, -e, e};                 /* Omega . n */
+                double diag = sigma_t[n];
+                double rhs = pk[n];
+                for (int f = 0; f < 4; ++f) {
+                    if (on[f] >= 0.0) diag += on[f] * An[f] / V;
+                    if (on[f] > 0.0) {
+                        const int c = neighbour(nx, ny, i, j, f);
+                        if (c >= 0) {
+                            const int ic = c % nx, jc = c / nx;
+                            rhs += on[f] * An[f] / (dx[ic] * dy[jc]) * fk[c];
+                        }
+                    }
+                }
+                fk[n] = rhs / diag;
+            }
+        }
+    }
+    return 0;
+}
