@@ -183,6 +183,49 @@ int gsis_synthetic_step(const gsis_mesh* mesh, const gsis_options* opt,
                         void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * Bytes of device workspace needed by gsis_adjoint (the gsis_solve layout
+ * plus the adjoint intensities and vectors).
+ */
+int gsis_adjoint_workspace_bytes(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis_options* opt,
+                                 size_t* bytes);
+
+/*
+ * Gradient of a functional J(rho*) of the converged GSIS solution rho*
+ * (Sec. 3.1, steady, no pseudo-time) with respect to the per-cell opacities,
+ * by the adjoint of the GSIS fixed point.  The paper has no counterpart of
+ * this call: it differentiates the discrete equations this library solves.
+ *   The kinetic step at rho* (I_k = A_k^{-1} s, s = (sigma_s rho* + q)/4pi,
+ *   Eqs. (RTE_d), (RTE_SI)) and the synthetic equation D rho* = b (Eqs.
+ *   (MSE_d1), (Fij_d), (macro_bc_delta_flux), with the adaptive least-squares
+ *   HoT, Eqs. (GSIS_HoT), (shifted_j), (new_vector), (LSF_mdf)) are held as
+ *   constraints; the adjoint lam = D nu solves the transposed GSIS iteration
+ *   lam = M^T lam + dJ/drho (one synthetic solve, the transposed right-hand
+ *   side and one transposed sweep of every ordinate per iteration, iterated
+ *   to opt->tol on Err(lam), Eq. (Err_W)); the gradient is the explicit
+ *   derivative of the Lagrangian (kinetic source and diagonal, Gamma_f,
+ *   boundary beta, HoT weights, V sigma_a).
+ * rho_star: device [N], the converged solution of gsis_solve with the same
+ *   mesh, quadrature, options and inputs (the kinetic step is retaken at it).
+ * dJ_drho: device [N].  grad_sigma_a, grad_sigma_s: device [N] out.
+ * iters_out, err_out: host, may be NULL (adjoint iterations, final Err(lam)).
+ * Requirements (else GSIS_ERR_ARG): opt->scheme == GSIS_SCHEME_GSIS, no
+ *   pseudo-time (opt->cfl_p, opt->beta <= 0), uniform dx and dy (the
+ *   transposed upwind sweep is then the sweep of the reflected direction),
+ *   a quadrature closed under Omega -> -Omega with equal weights.
+ * opt->precision selects FP64 or FP32 transposed sweeps, as in gsis_solve.
+ * opt->stall_window ends the iteration as in gsis_solve (the FP32 form has a
+ *   floor of Err(lam) near 1e-7).
+ * Workspace: gsis_adjoint_workspace_bytes.  Returns GSIS_OK, or
+ *   GSIS_ERR_MAXITER / GSIS_ERR_STALLED / GSIS_ERR_DIVERGED for the adjoint
+ *   iteration (the gradient is written in every case), or an
+ *   argument, CUDA, timeout or workspace error.  Synchronises the stream.
+ */
+int gsis_adjoint(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis_options* opt,
+                 const double* sigma_a, const double* sigma_s, const double* q, const double* inflow,
+                 const double* rho_star, const double* dJ_drho, double* grad_sigma_a, double* grad_sigma_s,
+                 int* iters_out, double* err_out, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
  * gsis_transport_sweep() for callers that cannot allocate device memory.
  * The paper has no counterpart: this is an interface convenience.
  *

@@ -110,7 +110,7 @@ constexpr size_t kAlign = 256;
 constexpr double kPi = 3.14159265358979323846;
 
 struct Sizes {
-    int nx, ny, K, fp32, hist;
+    int nx, ny, K, fp32, hist, adjoint;
 };
 
 // Carves the workspace (base may be null: size query only).
@@ -189,6 +189,17 @@ size_t layout(const Sizes& z, char* base, Plan* P)
         for (float** f : v) *f = reinterpret_cast<float*>(take(N * sizeof(float)));
     }
     p.hist = reinterpret_cast<double*>(take((size_t)std::max(1, z.hist) * sizeof(double)));
+    if (z.adjoint) {
+        p.Iadj = take(K * N * Ts);
+        double** adj[] = {&p.adj_a, &p.adj_x, &p.adj_y, &p.lam, &p.nu};
+        for (double** d : adj) *d = reinterpret_cast<double*>(take(N * sizeof(double)));
+        if (z.fp32) {
+            float** af[] = {&p.adj_a_f, &p.adj_x_f, &p.adj_y_f};
+            for (float** f : af) *f = reinterpret_cast<float*>(take(N * sizeof(float)));
+        }
+        p.adj_inflow = reinterpret_cast<double*>(take(nbf * K * sizeof(double)));
+        p.refl = reinterpret_cast<int*>(take(K * sizeof(int)));
+    }
     return off;
 }
 
@@ -357,6 +368,46 @@ void gsis::set_last_error(int code, const char* msg)
     (void)code;
     g_last_error = msg ? msg : "";
 }
+
+namespace {
+
+bool uniform_spacing(const double* h, int n)
+{
+    for (int i = 1; i < n; ++i)
+        if (!(std::fabs(h[i] - h[0]) <= 1e-12 * std::fabs(h[0]))) return false;
+    return true;
+}
+
+// Sorted index (quadrant-major, as in prepare) of the reflected direction
+// -Omega of every sorted direction; false if the set is not closed under
+// the reflection with equal weights.
+bool reflection_table(const gsis_quadrature* quad, std::vector<int>& refl)
+{
+    const int K = quad->K;
+    std::vector<int> perm;
+    perm.reserve(K);
+    for (int qd = 0; qd < 4; ++qd)
+        for (int k = 0; k < K; ++k) {
+            const int kq = (quad->mu[k] < 0.0 ? 1 : 0) + (quad->eta[k] < 0.0 ? 2 : 0);
+            if (kq == qd) perm.push_back(k);
+        }
+    refl.assign(K, -1);
+    for (int s = 0; s < K; ++s) {
+        const int k = perm[s];
+        for (int t = 0; t < K; ++t) {
+            const int m = perm[t];
+            if (std::fabs(quad->mu[m] + quad->mu[k]) <= 1e-12 && std::fabs(quad->eta[m] + quad->eta[k]) <= 1e-12 &&
+                std::fabs(quad->w[m] - quad->w[k]) <= 1e-12 * std::fabs(quad->w[k])) {
+                refl[s] = t;
+                break;
+            }
+        }
+        if (refl[s] < 0) return false;
+    }
+    return true;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -557,6 +608,109 @@ int gsis_synthetic_step(const gsis_mesh* mesh, const gsis_options* opt, const do
     if ((rc = read_status(S, P, st))) return rc;
     if (synth_iters_out) *synth_iters_out = S.synth_iters;
     return GSIS_OK;
+}
+
+int gsis_adjoint_workspace_bytes(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis_options* opt,
+                                 size_t* bytes)
+{
+    g_last_error.clear();
+    int rc;
+    if ((rc = check_mesh(mesh)) || (rc = check_quad(quad)) || (rc = check_opt(opt))) return rc;
+    if (!bytes) return fail(GSIS_ERR_ARG, "bytes is NULL");
+    Sizes z = sizes_of(mesh, quad, opt);
+    z.adjoint = 1;
+    *bytes = layout(z, nullptr, nullptr);
+    return GSIS_OK;
+}
+
+int gsis_adjoint(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis_options* opt,
+                 const double* sigma_a, const double* sigma_s, const double* q, const double* inflow,
+                 const double* rho_star, const double* dJ_drho, double* grad_sigma_a, double* grad_sigma_s,
+                 int* iters_out, double* err_out, void* workspace, size_t workspace_bytes, void* stream)
+{
+    g_last_error.clear();
+    int rc;
+    if ((rc = check_mesh(mesh)) || (rc = check_quad(quad)) || (rc = check_opt(opt))) return rc;
+    if (!sigma_a || !sigma_s || !q || !rho_star || !dJ_drho || !grad_sigma_a || !grad_sigma_s)
+        return fail(GSIS_ERR_ARG, "a required device pointer is NULL");
+    if (opt->scheme != GSIS_SCHEME_GSIS) return fail(GSIS_ERR_ARG, "the adjoint is that of the GSIS solution");
+    if (opt->cfl_p > 0.0 || opt->beta > 0.0)
+        return fail(GSIS_ERR_ARG, "the adjoint is that of the steady GSIS map without pseudo-time");
+    if (!uniform_spacing(mesh->dx, mesh->nx) || !uniform_spacing(mesh->dy, mesh->ny))
+        return fail(GSIS_ERR_ARG, "the adjoint needs a uniform mesh (transposed sweep = reflected sweep)");
+    std::vector<int> refl;
+    if (!reflection_table(quad, refl))
+        return fail(GSIS_ERR_ARG, "the adjoint needs a quadrature closed under Omega -> -Omega with equal weights");
+    Sizes z = sizes_of(mesh, quad, opt);
+    z.adjoint = 1;
+    if ((rc = check_ws(workspace, workspace_bytes, layout(z, nullptr, nullptr)))) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Plan P{};
+    layout(z, static_cast<char*>(workspace), &P);
+    if ((rc = prepare(P, mesh, quad, opt, sigma_a, sigma_s, q, inflow, st))) return rc;
+    P.g = dJ_drho;
+    CK(cudaMemcpyAsync(P.refl, refl.data(), refl.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    // kinetic step at rho*: I_k, rho_1/2, F, F_b
+    CK(cudaMemcpyAsync(P.rho_m, rho_star, (size_t)P.N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    TIMED(GSIS_KCLASS_SETUP, 1, launch_source_from(P, P.rho_m, st));
+    TIMED(GSIS_KCLASS_SWEEP, 1, launch_sweep(P, st));
+    TIMED(GSIS_KCLASS_MOMENTS, 2, launch_moments_to(P, true, false, P.rho_h, nullptr, nullptr, false, P.fb, false, st));
+    // lam = g (also the first right-hand side), nu = 0
+    CK(cudaMemcpyAsync(P.lam, dJ_drho, (size_t)P.N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(P.b, dJ_drho, (size_t)P.N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemsetAsync(P.nu, 0, (size_t)P.N * sizeof(double), st));
+    CK(cudaStreamSynchronize(st));   // the host table goes out of scope
+    Status S{};
+    if ((rc = read_status(S, P, st))) return rc;
+
+    // transposed GSIS iteration lam = M^T lam + g
+    auto pass = [&](bool update) -> int {
+        TIMED(GSIS_KCLASS_HOT_RHS, 1, launch_synth_resid(P, P.b, P.nu, st));
+        TIMED(GSIS_KCLASS_SYNTH, 1, launch_synthetic_solve(P, P.nu, P.x, st));
+        TIMED(GSIS_KCLASS_HOT_RHS, 2, launch_adjoint_rhs(P, P.x, st));
+        TIMED(GSIS_KCLASS_SWEEP, 1, launch_adjoint_sweep(P, st));
+        if (update) TIMED(GSIS_KCLASS_UPDATE, 1, launch_adjoint_update(P, st));
+        return GSIS_OK;
+    };
+    const int nmax = opt->fixed_iters > 0 ? opt->fixed_iters : opt->max_iter;
+    int launched = 0;
+    double best = INFINITY;
+    int since_best = 0;
+    bool stalled = false;
+    while (launched < nmax) {
+        const int batch = std::min(opt->check_every, nmax - launched);
+        for (int b = 0; b < batch; ++b)
+            if ((rc = pass(true))) return rc;
+        launched += batch;
+        if ((rc = read_status(S, P, st))) return rc;
+        if (S.done) break;
+        if (opt->stall_window > 0) {
+            if (S.err < best) {
+                best = S.err;
+                since_best = 0;
+            } else if (++since_best >= opt->stall_window) {
+                stalled = true;
+                break;
+            }
+        }
+    }
+    // nu and phi at the final lam, then the explicit derivative
+    CK(cudaMemsetAsync(&P.status->done, 0, sizeof(int), st));
+    if ((rc = pass(false))) return rc;
+    TIMED(GSIS_KCLASS_UPDATE, 1, launch_adjoint_gradient(P, grad_sigma_a, grad_sigma_s, st));
+    Status S2{};
+    if ((rc = read_status(S2, P, st))) return rc;
+    g_last_info.iters = S.iter;
+    g_last_info.synth_inner_iters = S2.synth_iters_total;
+    g_last_info.err = S.err;
+    g_last_info.synth_relres = S2.synth_relres;
+    if (iters_out) *iters_out = S.iter;
+    if (err_out) *err_out = S.err;
+    if (S.reason == kDiverged) return fail(GSIS_ERR_DIVERGED, "adjoint Err = %g after %d iterations", S.err, S.iter);
+    if (S.reason == kConverged || S.reason == kFixedDone) return GSIS_OK;
+    if (stalled) return fail(GSIS_ERR_STALLED, "adjoint Err = %g did not decrease for %d checks", S.err,
+                             opt->stall_window);
+    return fail(GSIS_ERR_MAXITER, "adjoint Err = %g after %d iterations", S.err, S.iter);
 }
 
 }  // extern "C"

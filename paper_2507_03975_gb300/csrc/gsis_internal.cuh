@@ -102,6 +102,15 @@ struct Plan {
     double* hist;                   // [max_iter]
     Status* status;
     MgPlan mg;
+    // adjoint (allocated by the adjoint layout only)
+    void* Iadj;                     // [K][N] T, transposed-sweep solutions (index: the swept, reflected direction)
+    double* adj_a; double* adj_x; double* adj_y;      // adjoint moments: rho_bar_1/2, F_bar_x, F_bar_y
+    float* adj_a_f; float* adj_x_f; float* adj_y_f;   // FP32 copies (FP32 sweep)
+    double* adj_inflow;             // [nbf][K] adjoint of the boundary flux, as an inflow of the transposed sweep
+    double* lam;                    // lam = D nu (adjoint of rho)
+    double* nu;                     // nu (adjoint of the synthetic equation)
+    const double* g;                // dJ/drho (caller's device array)
+    int* refl;                      // [K] sorted index of the reflected direction
 };
 
 // ------------------------------------------------------------ launchers
@@ -124,6 +133,12 @@ cudaError_t launch_mg_setup(const Plan& P, cudaStream_t st);
 cudaError_t launch_synthetic_solve(const Plan& P, const double* guess, double* out, cudaStream_t st);
 int mg_cluster_size();
 cudaError_t launch_update(const Plan& P, const double* rho_new, cudaStream_t st);
+// adjoint (csrc/adjoint.cu, sweep in csrc/sweep.cu)
+cudaError_t launch_adjoint_sweep(Plan& P, cudaStream_t st);
+cudaError_t launch_synth_resid(const Plan& P, const double* b, const double* guess, cudaStream_t st);
+cudaError_t launch_adjoint_rhs(const Plan& P, const double* nu_new, cudaStream_t st);   // nu, h_bar, rho_bar, inflow
+cudaError_t launch_adjoint_update(const Plan& P, cudaStream_t st);
+cudaError_t launch_adjoint_gradient(const Plan& P, double* grad_sa, double* grad_ss, cudaStream_t st);
 
 int device_sm_count();
 void set_last_error(int code, const char* msg);   // message returned by gsis_last_error()

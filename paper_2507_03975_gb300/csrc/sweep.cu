@@ -21,6 +21,8 @@
 // second moment).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "gsis_internal.cuh"
 
 namespace gsis {
@@ -199,12 +201,19 @@ __global__ void source_kernel(int N, const double* __restrict__ ss, const double
 }
 
 // --------------------------------------------------------------- sweep
+// Source of the sweep: isotropic (plain), isotropic plus the pseudo-time
+// term shift * I^m (delta form), or the adjoint source
+// w_s (a - mu_s bx - eta_s by) of the transposed kinetic step.
+constexpr int kSrcPlain = 0, kSrcPseudoTime = 1, kSrcAdjoint = 2;
+
 template <typename T>
 struct SweepArgs {
     int nx, ny, N, K, nb, nsteps;
     const T* acoef; const T* bcoef;
     const double* rsw;
     const T* sigt; const T* shift; const T* src;
+    const T* ax; const T* ay;   // adjoint source: bx, by (src holds a)
+    const double* qw;           // sorted weights (adjoint source)
     T* I; T* edge;
     const double* inflow;
     const int* perm; const double* qmu; const double* qeta;
@@ -312,11 +321,12 @@ struct SweepSmem {
 // to I, and the last lane also to this band's hand-off row, then arrives on
 // "empty".  Every wait is bounded; on time-out kErrTimeout is raised and the
 // warp leaves after its copies in flight have landed.
-template <typename T, bool PT, bool PRE>
+template <typename T, int MODE, bool PRE>
 __global__ void __launch_bounds__(kSweepPairs * 64, 1)
 sweep_kernel(const SweepArgs<T> a)
 {
-    using SM = SweepSmem<T, PT, PRE>;
+    constexpr bool PT = MODE == kSrcPseudoTime, ADJ = MODE == kSrcAdjoint;
+    using SM = SweepSmem<T, MODE != kSrcPlain, PRE>;
     using B = Bits<T>;
     constexpr int SEG = SM::SEG, NBUF = SM::NBUF, RS = SM::RS, NW = SM::NW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -371,6 +381,10 @@ sweep_kernel(const SweepArgs<T> a)
             if (PT) {
                 wsrc[SM::W_SHIFT] = a.shift;
                 wsrc[SM::W_IOLD] = Is;
+            }
+            if (ADJ) {
+                wsrc[SM::W_SHIFT] = a.ax;
+                wsrc[SM::W_IOLD] = a.ay;
             }
             const T* arow = a.acoef + (size_t)s * nx;
             const double* rrow = PRE ? a.rsw + ((size_t)s * nb + band) * (size_t)a.nsteps * 32 : nullptr;
@@ -471,6 +485,13 @@ sweep_kernel(const SweepArgs<T> a)
         } else {
             // ------------------------------------------------- compute warp
             const T bj = row_ok ? a.bcoef[(size_t)s * ny + j] : T(0);
+            T cw = T(0), cm = T(0), ce = T(0);   // adjoint source w (a - mu bx - eta by)
+            if (ADJ) {
+                const double ws = a.qw[s];
+                cw = (T)ws;
+                cm = (T)(-ws * a.qmu[s]);
+                ce = (T)(-ws * a.qeta[s]);
+            }
             T IW = T(0);
             if (row_ok && a.inflow) IW = (T)a.inflow[(size_t)(xpos ? j : ny + j) * K + k];
             T Iprev = T(0);
@@ -499,6 +520,7 @@ sweep_kernel(const SweepArgs<T> a)
                         const T e = ein[tt];
                         const T Isouth = __shfl_sync(kFull, lane == 31 ? e : Iprev, (lane + 31) & 31);
                         T sv = wb[SM::W_SRC * SM::WIN + tt];
+                        if (ADJ) sv = fma(cm, wb[SM::W_SHIFT * SM::WIN + tt], fma(ce, wb[SM::W_IOLD * SM::WIN + tt], cw * sv));
                         const T ai = ab[tt];
                         T rinv;
                         if (PRE) {
@@ -532,6 +554,7 @@ sweep_kernel(const SweepArgs<T> a)
                         T Inew = T(0);
                         if (row_ok && c >= 0 && c < nx) {
                             T sv = wb[SM::W_SRC * SM::WIN + tt];
+                            if (ADJ) sv = fma(cm, wb[SM::W_SHIFT * SM::WIN + tt], fma(ce, wb[SM::W_IOLD * SM::WIN + tt], cw * sv));
                             const T ai = ab[tt];
                             T rinv;
                             if (PRE) {
@@ -672,10 +695,10 @@ int grid_for(long long n, int block, int cap)
     return (int)g;
 }
 
-template <typename T, bool PT>
+template <typename T, int MODE>
 size_t sweep_smem();
 
-template <typename T, bool PT, bool PRE>
+template <typename T, int MODE, bool PRE>
 cudaError_t launch_sweep_t(Plan& P, cudaStream_t st)
 {
     SweepArgs<T> a{};
@@ -689,11 +712,21 @@ cudaError_t launch_sweep_t(Plan& P, cudaStream_t st)
     a.I = static_cast<T*>(P.I);
     a.edge = static_cast<T*>(P.edge);
     a.inflow = P.inflow;
+    if (MODE == kSrcAdjoint) {   // transposed kinetic step: reflected direction, adjoint source
+        if constexpr (sizeof(T) == 8) {
+            a.src = P.adj_a; a.ax = P.adj_x; a.ay = P.adj_y;
+        } else {
+            a.src = P.adj_a_f; a.ax = P.adj_x_f; a.ay = P.adj_y_f;
+        }
+        a.I = static_cast<T*>(P.Iadj);
+        a.inflow = P.adj_inflow;
+    }
+    a.qw = P.qw;
     a.perm = P.perm; a.qmu = P.qmu; a.qeta = P.qeta;
     a.err = &P.status->error;
     a.done = &P.status->done;
     a.wait_cycles = P.wait_cycles;
-    sweep_kernel<T, PT, PRE><<<P.sweep_grid, kSweepPairs * 64, sweep_smem<T, PT>(), st>>>(a);
+    sweep_kernel<T, MODE, PRE><<<P.sweep_grid, kSweepPairs * 64, sweep_smem<T, MODE>(), st>>>(a);
     return cudaGetLastError();
 }
 
@@ -732,10 +765,10 @@ cudaError_t launch_moments_t(const Plan& P, bool with_F, bool with_P, double* rh
     return cudaGetLastError();
 }
 
-template <typename T, bool PT>
+template <typename T, int MODE>
 size_t sweep_smem()
 {
-    return SweepSmem<T, PT, sizeof(T) == 8>::bytes;
+    return SweepSmem<T, MODE != kSrcPlain, sizeof(T) == 8>::bytes;
 }
 
 template <typename T>
@@ -743,10 +776,15 @@ cudaError_t prepare_t(int K)
 {
     cudaError_t e;
     const int ms = (int)moments_smem<T>(K);
-    if ((e = cudaFuncSetAttribute(sweep_kernel<T, false, sizeof(T) == 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)sweep_smem<T, false>())) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(sweep_kernel<T, true, sizeof(T) == 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)sweep_smem<T, true>())) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(sweep_kernel<T, kSrcPlain, sizeof(T) == 8>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sweep_smem<T, kSrcPlain>())) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(sweep_kernel<T, kSrcPseudoTime, sizeof(T) == 8>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sweep_smem<T, kSrcPseudoTime>())) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(sweep_kernel<T, kSrcAdjoint, sizeof(T) == 8>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sweep_smem<T, kSrcAdjoint>())) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(moments_kernel<T, true, true>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, ms)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(moments_kernel<T, true, false>,
@@ -754,12 +792,12 @@ cudaError_t prepare_t(int K)
     return cudaFuncSetAttribute(moments_kernel<T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ms);
 }
 
-template <typename T, bool PT>
+template <typename T, int MODE>
 int sweep_occupancy()
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<T, PT, sizeof(T) == 8>, kSweepPairs * 64,
-                                                      sweep_smem<T, PT>()) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<T, MODE, sizeof(T) == 8>, kSweepPairs * 64,
+                                                      sweep_smem<T, MODE>()) != cudaSuccess)
         return 0;
     return n;
 }
@@ -830,9 +868,15 @@ cudaError_t launch_source_from(const Plan& P, const double* rho_in, cudaStream_t
 cudaError_t launch_sweep(Plan& P, cudaStream_t st)
 {
     if (P.fp32) {
-        return P.pt ? launch_sweep_t<float, true, false>(P, st) : launch_sweep_t<float, false, false>(P, st);
+        return P.pt ? launch_sweep_t<float, kSrcPseudoTime, false>(P, st)
+                    : launch_sweep_t<float, kSrcPlain, false>(P, st);
     }
-    return P.pt ? launch_sweep_t<double, true, true>(P, st) : launch_sweep_t<double, false, true>(P, st);
+    return P.pt ? launch_sweep_t<double, kSrcPseudoTime, true>(P, st) : launch_sweep_t<double, kSrcPlain, true>(P, st);
+}
+
+cudaError_t launch_adjoint_sweep(Plan& P, cudaStream_t st)
+{
+    return P.fp32 ? launch_sweep_t<float, kSrcAdjoint, false>(P, st) : launch_sweep_t<double, kSrcAdjoint, true>(P, st);
 }
 
 // Moments of the last sweep into the given outputs: rho always, F when
@@ -855,8 +899,14 @@ cudaError_t prepare_kernels(int K, int fp32, int pt)
 
 int sweep_max_active_blocks(int fp32, int pt)
 {
-    if (fp32) return pt ? sweep_occupancy<float, true>() : sweep_occupancy<float, false>();
-    return pt ? sweep_occupancy<double, true>() : sweep_occupancy<double, false>();
+    // one grid for every variant a plan may launch (forward, pseudo-time,
+    // adjoint): every warp pair must be resident, so take the smallest
+    (void)pt;
+    if (fp32)
+        return std::min({sweep_occupancy<float, kSrcPlain>(), sweep_occupancy<float, kSrcPseudoTime>(),
+                         sweep_occupancy<float, kSrcAdjoint>()});
+    return std::min({sweep_occupancy<double, kSrcPlain>(), sweep_occupancy<double, kSrcPseudoTime>(),
+                     sweep_occupancy<double, kSrcAdjoint>()});
 }
 
 }  // namespace gsis

@@ -96,6 +96,10 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.gsis_synthetic_step.argtypes = [Mp, Op, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, ip, vp, sz, vp]
     lib.gsis_transport_sweep_static.argtypes = [Mp, Qp, Op, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.gsis_transport_sweep_static.restype = ctypes.c_int
+    lib.gsis_adjoint_workspace_bytes.argtypes = [Mp, Qp, Op, ctypes.POINTER(sz)]
+    lib.gsis_adjoint_workspace_bytes.restype = ctypes.c_int
+    lib.gsis_adjoint.argtypes = [Mp, Qp, Op, vp, vp, vp, vp, vp, vp, vp, vp, ip, _P, vp, sz, vp]
+    lib.gsis_adjoint.restype = ctypes.c_int
     lib.gsis_last_solve_info.argtypes = [ctypes.POINTER(SolveInfo)]
     lib.gsis_last_solve_info.restype = ctypes.c_int
     lib.gsis_profile_enable.argtypes = [ctypes.c_int]
@@ -312,3 +316,78 @@ def synthetic_step(dx, dy, sigma_a, sigma_s, q, rho_half, F_half, bflux, rho_gue
         ctypes.c_size_t(workspace.numel()), _stream(stream))
     _raise(rc)
     return dict(rho=rho, hot=hot, rhs=rhs, synth_iters=it.value, workspace=workspace)
+
+
+def adjoint_workspace_bytes(dx, dy, mu, eta, w, options: Options | None = None) -> int:
+    a = _Args(dx, dy, mu, eta, w)
+    o = options or default_options()
+    n = ctypes.c_size_t(0)
+    _raise(load().gsis_adjoint_workspace_bytes(ctypes.byref(a.mesh), ctypes.byref(a.quad), ctypes.byref(o),
+                                               ctypes.byref(n)))
+    return int(n.value)
+
+
+def adjoint(dx, dy, mu, eta, w, sigma_a, sigma_s, q, rho_star, dJ_drho, inflow=None,
+            options: Options | None = None, workspace=None, stream=None):
+    """gsis_adjoint: gradient of J(rho*) with respect to sigma_a, sigma_s given
+    dJ/drho; returns dict(grad_sigma_a, grad_sigma_s, iters, err, status, workspace)."""
+    import torch
+    a = _Args(dx, dy, mu, eta, w)
+    o = options or default_options()
+    N, K = a.mesh.nx * a.mesh.ny, a.quad.K
+    dev = sigma_a.device
+    gsa = torch.empty(N, dtype=torch.float64, device=dev)
+    gss = torch.empty(N, dtype=torch.float64, device=dev)
+    iters, err = ctypes.c_int(0), ctypes.c_double(0.0)
+    nbytes = adjoint_workspace_bytes(a.dx, a.dy, a.mu, a.eta, a.w, o)
+    workspace = _workspace(nbytes, workspace, dev)
+    rc = load().gsis_adjoint(
+        ctypes.byref(a.mesh), ctypes.byref(a.quad), ctypes.byref(o),
+        _dev(sigma_a, N, "sigma_a"), _dev(sigma_s, N, "sigma_s"), _dev(q, N, "q"),
+        _dev(inflow, 2 * (a.mesh.nx + a.mesh.ny) * K, "inflow"), _dev(rho_star, N, "rho_star"),
+        _dev(dJ_drho, N, "dJ_drho"), _dev(gsa), _dev(gss), ctypes.byref(iters), ctypes.byref(err),
+        ctypes.c_void_p(workspace.data_ptr()), ctypes.c_size_t(workspace.numel()), _stream(stream))
+    _raise(rc)
+    return dict(grad_sigma_a=gsa, grad_sigma_s=gss, iters=iters.value, err=err.value, status=rc,
+                workspace=workspace)
+
+
+def _autograd_function():
+    import torch
+
+    class GsisSolve(torch.autograd.Function):
+        """rho* = GSIS solution as a differentiable function of (sigma_a, sigma_s):
+        forward = gsis_solve, backward = gsis_adjoint with dJ/drho = grad_output."""
+
+        @staticmethod
+        def forward(ctx, sigma_a, sigma_s, q, host, inflow, options):
+            dx, dy, mu, eta, w = host
+            r = solve(dx, dy, mu, eta, w, sigma_a.detach().contiguous(), sigma_s.detach().contiguous(),
+                      q.detach().contiguous(), inflow=inflow, options=options, want_P=False)
+            rho = r["rho"]
+            ctx.host, ctx.inflow, ctx.options = host, inflow, options
+            ctx.save_for_backward(sigma_a, sigma_s, q, rho)
+            return rho
+
+        @staticmethod
+        def backward(ctx, grad_rho):
+            sigma_a, sigma_s, q, rho = ctx.saved_tensors
+            dx, dy, mu, eta, w = ctx.host
+            out = adjoint(dx, dy, mu, eta, w, sigma_a.detach().contiguous(), sigma_s.detach().contiguous(),
+                          q.detach().contiguous(), rho, grad_rho.detach().to(torch.float64).contiguous(),
+                          inflow=ctx.inflow, options=ctx.options)
+            return out["grad_sigma_a"], out["grad_sigma_s"], None, None, None, None
+
+    return GsisSolve
+
+
+_GsisSolve = None
+
+
+def solve_differentiable(dx, dy, mu, eta, w, sigma_a, sigma_s, q, inflow=None, options: Options | None = None):
+    """rho* (device [N]) of gsis_solve, differentiable with respect to sigma_a and
+    sigma_s through torch.autograd (the backward pass is gsis_adjoint)."""
+    global _GsisSolve
+    if _GsisSolve is None:
+        _GsisSolve = _autograd_function()
+    return _GsisSolve.apply(sigma_a, sigma_s, q, (dx, dy, mu, eta, w), inflow, options)
