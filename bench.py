@@ -49,7 +49,9 @@ def _workload(args=None):
                    synthetic=f"FP64 iterative refinement, FP32 multigrid-CG inner iterations capped at {cap} "
                              "per GSIS iteration (warm-started; same fixed point)" if cap > 0 else
                              "solved to relative residual 1e-12",
-                   l2="flushed before each step (512 MiB write); per-solve working set ~105 MB")
+                   l2="flushed before each step (512 MiB write); per-solve working set ~105 MB",
+                   kernel_timing="a second pass of the same solves with CUDA events around every kernel "
+                                 "class (roofline, shares); value and ms_per_step from the uninstrumented pass")
 
 
 def _dist():
@@ -114,6 +116,36 @@ def _sweep_traffic():
     with open(src, "rb") as f:
         digest = hashlib.sha256(f.read()).hexdigest()
     return 100_548_864 if digest.startswith(SWEEP_CAPTURE_SHA256) else None
+
+
+def adjoint_measure(gsis, torch, stream):
+    """Forward solve and adjoint gradient of J = sum of rho over 16 seed-3
+    detector cells on the 64x64 S8 workload (sigma_t = 10, ratio 0.99, q = 1,
+    vacuum), FP32 sweeps with the FP64 synthetic solve (and the FP64 form for
+    reference); device time with CUDA events, inputs resident."""
+    p = W.config_small()
+    rng = np.random.Generator(np.random.PCG64(3))
+    g = np.zeros(p.N)
+    g[rng.choice(p.N, 16, replace=False)] = 1.0
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    sa, ss, q, gd = t(p.sigma_a), t(p.sigma_s), t(p.q), t(g)
+    out = {"workload": "uniform_64x64_S8, J = sum of rho over 16 detector cells (seed 3)"}
+    for name, prec, tol in (("fp32_sweeps", gsis.FP32_SWEEP, 1e-6), ("fp64", gsis.FP64, 1e-8)):
+        opt = gsis.default_options(precision=prec, tol=tol, stall_window=4, max_iter=2000)
+        ws = None
+        for _ in range(3):   # two warm-up rounds, the last one timed
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            r = gsis.solve(p.dx, p.dy, p.mu, p.eta, p.w, sa, ss, q, None, opt, want_P=False)
+            e1.record(stream)
+            a = gsis.adjoint(p.dx, p.dy, p.mu, p.eta, p.w, sa, ss, q, r["rho"], gd, options=opt, workspace=ws)
+            ws = a["workspace"]
+            e2.record(stream)
+            e2.synchronize()
+        out[name] = {"forward_ms": e0.elapsed_time(e1), "adjoint_ms": e1.elapsed_time(e2),
+                     "forward_iters": r["iters"], "adjoint_iters": a["iters"], "adjoint_err": a["err"],
+                     "tol": tol}
+    return out
 
 
 def _peaks():
@@ -189,8 +221,8 @@ def run_ours(args):
         gsis.solve(p.dx, p.dy, p.mu, p.eta, p.w, sa, ss, q, inflow, opt, workspace=workspace)
     torch.cuda.synchronize()
 
-    # ---- timed: K complete solves, inputs resident in HBM
-    gsis.profile_enable(True)
+    # ---- timed: K complete solves, inputs resident in HBM (no instrumentation)
+    gsis.profile_enable(False)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -210,9 +242,18 @@ def run_ours(args):
         if r["status"] != gsis.GSIS_OK:
             raise RuntimeError(f"solve did not converge: status {r['status']}, Err {r['err']}")
     torch.cuda.synchronize()
+    clocks = _clock_summary(proc, cf, torch.cuda.current_device()) if rank == 0 else None
+    if dist:
+        dist.barrier()
+    # ---- the same K solves again with CUDA events around every kernel class on
+    # the launching stream: per-launch durations and shares for the roofline
+    gsis.profile_enable(True)
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        gsis.solve(p.dx, p.dy, p.mu, p.eta, p.w, sa, ss, q, inflow, opt, workspace=workspace)
+    torch.cuda.synchronize()
     prof = gsis.profile_read()
     gsis.profile_enable(False)
-    clocks = _clock_summary(proc, cf, torch.cuda.current_device()) if rank == 0 else None
     total_ms = sum(step_ms)
     if dist:
         tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
@@ -263,6 +304,11 @@ def run_ours(args):
         e1.synchronize()
         si = {"s": e0.elapsed_time(e1) * 1e-3, "iters": rs["iters"], "status": rs["status"],
               "updates_per_s": rs["iters"] * p.N * p.K / (e0.elapsed_time(e1) * 1e-3)}
+
+    # ---- adjoint (gradient of a detector functional, 64x64 S8 workload), once
+    adj = None
+    if not args.no_adjoint:
+        adj = adjoint_measure(gsis, torch, stream)
 
     if rank != 0:
         if dist:
@@ -320,6 +366,7 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(sum(v["kernels"] for v in prof.values())),
             "kernel_ms": {k: v["total_ms"] for k, v in prof.items()},
+            "adjoint": adj,
             "clocks": clocks}
     print(json.dumps(line))
     if dist:
@@ -336,6 +383,7 @@ def main():
     ap.add_argument("--no-si", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-gradient measurement")
     ap.add_argument("--synth-cap", type=int, default=SYNTH_CAP,
                     help="inner iterations of the synthetic solve per GSIS iteration (0: solve to 1e-12)")
     args = ap.parse_args()

@@ -6,7 +6,9 @@ with the CUDA library and neither imports the other.
 
 Parity pins (see tests/test_oracle_pins.py): every function here is checked
 against closed forms, invariants or brute force on tiny inputs; none is
-"parity unpinned".
+"parity unpinned".  The adjoint (oracle/adjoint.py) is pinned by
+tests/test_oracle_adjoint.py: dot-product identities of each transposed step
+against the forward oracle and central differences of full forward solves.
 """
 from .gsis import (  # noqa: F401
     angular_source, transport_sweep, alsm_gradient, high_order_terms, geometry, pseudo_time_shift,
