@@ -32,6 +32,10 @@ constexpr int kDiverged = 4;
 
 // Device-resident control block.
 struct Status {
+    unsigned int sweep_tasks;         // sweep unit counter (re-armed by each launch's last warp)
+    unsigned int sweep_exits;         // sweep warps that have left (same)
+    unsigned int sweep_arrived;       // sweep CTAs that have started (same)
+    int sweep_mode;                   // sweep unit placement of the running launch (same)
     unsigned int ticket;              // last-block ticket of the Err reduction
     int error;                        // kErr* bits
     int done;                         // != 0: iteration finished, later kernels return at once

@@ -218,6 +218,10 @@ struct SweepArgs {
     const double* inflow;
     const int* perm; const double* qmu; const double* qeta;
     int* err; const int* done;
+    unsigned int* tasks;     // unit counter (band-major order)
+    unsigned int* exits;     // warps that have left
+    unsigned int* arrived;   // CTAs that have started
+    int* mode;               // 0 undecided, 1 static placement, 2 counter
     long long wait_cycles;
 };
 
@@ -300,18 +304,25 @@ struct SweepSmem {
     static constexpr size_t off_r = r16(sizeof(T) * (size_t)NW * WIN);
     static constexpr size_t off_a = off_r + (PRE ? (size_t)SEG * 32 * sizeof(double) : 0);
     static constexpr size_t off_e = off_a + r16(sizeof(T) * (size_t)AW);
-    static constexpr size_t buf_bytes = off_e + r16(sizeof(T) * (size_t)SEG);
+    static constexpr size_t off_h = off_e + r16(sizeof(T) * (size_t)SEG);   // unit index of the chunk
+    static constexpr size_t buf_bytes = off_h + 16;
     static constexpr size_t bar_bytes = 64;                   // full[NBUF], empty[NBUF]
     static constexpr size_t pair_bytes = bar_bytes + NBUF * buf_bytes;
     static constexpr size_t bytes = kSweepPairs * pair_bytes;
     static_assert(2 * NBUF * 8 <= bar_bytes, "barrier space");
 };
 
-// One persistent CTA per SM runs kSweepPairs warp pairs.  Pair p of CTA c
-// owns the units (direction s, band) with index u = band * K + s equal to
-// p * G + c + i * kSweepPairs * G (G = grid size), in increasing u.  All
-// pairs are resident, a unit waits only on unit u - K, and every pair takes
-// its units in increasing order, so the waits cannot form a cycle.
+// One persistent CTA per SM runs kSweepPairs warp pairs; a pair's copy warp
+// chooses the units (direction s, band), u = band * K + s, and hands each to
+// its compute warp in the header of the unit's first chunk buffer.  When the
+// whole grid is resident (every CTA checks in within a few microseconds) the
+// units are placed statically: pair p of CTA c takes u = p G + c + i 8G, so
+// each SM's first units come from different bands and run at different
+// times; every unit is owned by a running pair and waits only on u - K.
+// Otherwise (part of the grid held back by other work on the GPU) the pairs
+// take units from a counter in increasing order, so a unit only waits on one
+// that a running pair took earlier.  One atomic decision picks the mode for
+// every CTA; the launch's last warp to leave re-arms the counters.
 //
 // Copy warp: for each chunk, cp.async of the window data into a free buffer
 // (arrival on the buffer's "full" barrier when the copies land), then the
@@ -352,14 +363,78 @@ sweep_kernel(const SweepArgs<T> a)
     const int ntasks = K * nb;
     const int nchunks = (a.nsteps + SEG - 1) / SEG;
     const long long budget = a.wait_cycles;
+
+    __shared__ int cta_mode;
+    if (threadIdx.x == 0) {
+        atomicAdd(a.arrived, 1u);
+        const long long t0 = clock64();
+        int m = 0;
+        for (;;) {
+            m = *reinterpret_cast<volatile int*>(a.mode);
+            if (m != 0) break;
+            if (*reinterpret_cast<volatile unsigned*>(a.arrived) >= (unsigned)G) atomicCAS(a.mode, 0, 1);
+            else if (clock64() - t0 > 20000) atomicCAS(a.mode, 0, 2);
+        }
+        cta_mode = m;
+    }
+    __syncthreads();
+    const bool placed = cta_mode == 1;
+
+    unsigned g = 0;   // chunks this pair has handled (buffer = g % NBUF)
+    int next_static = pair * G + (int)blockIdx.x;
+    bool first = true;
+    auto body = [&]() {
     {
         int stop = 0;
         if (lane == 0) stop = ld_volatile_int(a.done) | ld_volatile_int(a.err);
         if (__shfl_sync(kFull, stop, 0)) return;
     }
-
-    unsigned g = 0;   // chunks this pair has handled (buffer = g % NBUF)
-    for (int task = pair * G + blockIdx.x; task < ntasks; task += kSweepPairs * G) {
+    for (;;) {
+        int task;
+        if (copier) {
+            // next unit; -1: none left, or an error was raised
+            int t = -1;
+            if (lane == 0) {
+                if (placed) {
+                    t = next_static;
+                    next_static += kSweepPairs * G;
+                } else {
+                    if (first && pair >= kSweepPairs / 2) {
+                        // the second half of the pairs shares sub-partitions with the
+                        // first half: let the first half take the first units, so that
+                        // concurrently running units start on distinct sub-partitions
+                        const unsigned want = min((unsigned)ntasks, (unsigned)(kSweepPairs / 2) * (unsigned)G);
+                        const long long t0 = clock64();
+                        while (*reinterpret_cast<volatile unsigned*>(a.tasks) < want && clock64() - t0 < 20000)
+                            __nanosleep(64);
+                    }
+                    t = (int)atomicAdd(a.tasks, 1u);
+                }
+                if (t >= ntasks || ld_volatile_int(a.err)) t = -1;
+            }
+            task = __shfl_sync(kFull, t, 0);
+            first = false;
+            if (task < 0) {   // end marker in the next buffer, then leave
+                const int b = (int)(g % NBUF);
+                if (g >= NBUF && !__all_sync(kFull, mbar_wait(empty + b, ((g / NBUF) - 1) & 1, budget))) {
+                    if (lane == 0) atomicOr(a.err, kErrTimeout);
+                    return;
+                }
+                if (lane == 0) *reinterpret_cast<volatile int*>(buf(b) + SM::off_h) = -1;
+                cp_async_mbar_arrive(full + b);
+                mbar_arrive(full + b);
+                return;
+            }
+        } else {
+            // the unit is in the header of its first chunk's buffer
+            const int b = (int)(g % NBUF);
+            if (!__all_sync(kFull, mbar_wait(full + b, (g / NBUF) & 1, budget))) {
+                if (lane == 0) atomicOr(a.err, kErrTimeout);
+                return;
+            }
+            task = *reinterpret_cast<volatile const int*>(buf(b) + SM::off_h);
+            if (task < 0) return;
+        }
         const int band = task / K;
         const int s = task - band * K;
         const bool xpos = a.qmu[s] >= 0.0, ypos = a.qeta[s] >= 0.0;
@@ -476,6 +551,7 @@ sweep_kernel(const SweepArgs<T> a)
                     }
                 }
                 if (lane < SEG) reinterpret_cast<T*>(bp + SM::off_e)[lane] = ev;
+                if (lane == 0) *reinterpret_cast<volatile int*>(bp + SM::off_h) = task;
                 mbar_arrive(full + b);
             }
             // every value of the upstream hand-off row has been taken:
@@ -583,7 +659,20 @@ sweep_kernel(const SweepArgs<T> a)
             }
         }
     }
+    };
+    body();
     if (copier) cp_async_wait_all();
+    // the launch's last warp to leave re-arms the counters for the next launch
+    __syncwarp();
+    if (lane == 0) {
+        __threadfence();
+        if (atomicAdd(a.exits, 1u) == (unsigned)G * (unsigned)(2 * kSweepPairs) - 1u) {
+            *a.tasks = 0u;
+            *a.arrived = 0u;
+            *a.mode = 0;
+            *a.exits = 0u;
+        }
+    }
 }
 
 // --------------------------------------------------------------- moments
@@ -725,6 +814,10 @@ cudaError_t launch_sweep_t(Plan& P, cudaStream_t st)
     a.perm = P.perm; a.qmu = P.qmu; a.qeta = P.qeta;
     a.err = &P.status->error;
     a.done = &P.status->done;
+    a.tasks = &P.status->sweep_tasks;
+    a.exits = &P.status->sweep_exits;
+    a.arrived = &P.status->sweep_arrived;
+    a.mode = &P.status->sweep_mode;
     a.wait_cycles = P.wait_cycles;
     sweep_kernel<T, MODE, PRE><<<P.sweep_grid, kSweepPairs * 64, sweep_smem<T, MODE>(), st>>>(a);
     return cudaGetLastError();
