@@ -226,6 +226,101 @@ int gsis_adjoint(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis_
                  int* iters_out, double* err_out, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * Batched solve: n independent steady problems, each with its own mesh,
+ * quadrature, opacities, sources and inflow, iterated together under one set
+ * of options.  The paper solves one problem at a time and has no counterpart
+ * of this call: it is a throughput form of gsis_solve.  Each problem goes
+ * through exactly the iteration of gsis_solve (Sec. 2.2 / Sec. 3.1, same
+ * kernels, same order of operations): rho, F, the iteration count and Err
+ * equal gsis_solve's bit for bit whenever the synthetic solver runs on the
+ * cluster size gsis_solve picks (tuning->synth_cells_per_cta = 0), and agree
+ * to the synthetic tolerance otherwise (its cluster-wide sums are then
+ * rounded in another order).
+ *
+ * Per iteration every step is one launch over all problems: one persistent
+ * sweep over the units (ordinate, 32-row band) of every problem, drawn in the
+ * order tuning->sweep_order gives, one launch each for the moments and
+ * boundary fluxes, the HoT and synthetic right-hand side, and the update, and
+ * one strip-solver launch per cluster size (one cluster per problem; the
+ * cluster sizes run concurrently).  opt->check_every iterations are captured
+ * once as a CUDA graph and replayed; the host reads every problem's status
+ * after each replay, and launches skip a problem once it has stopped
+ * (converged, diverged, iteration cap, stalled).
+ */
+typedef struct {
+    gsis_mesh mesh;             /* HOST spacing arrays, as in gsis_solve */
+    gsis_quadrature quad;       /* HOST arrays, as in gsis_solve */
+    const double* sigma_a;      /* device [N] */
+    const double* sigma_s;      /* device [N] */
+    const double* q;            /* device [N] */
+    const double* inflow;       /* device [n_bface*K] or NULL (vacuum) */
+    double* rho;                /* device [N] out */
+    double* F;                  /* device [2N] out, or NULL */
+    int iters;                  /* out: iterations done */
+    double err;                 /* out: final Err(rho) */
+    int status;                 /* out: the gsis_status gsis_solve would return for this problem */
+} gsis_problem;
+
+typedef enum {
+    GSIS_ORDER_PROBLEM = 0,      /* problem after problem, in the given order */
+    GSIS_ORDER_BAND = 1,         /* band 0 of every problem, then band 1, ... */
+    GSIS_ORDER_LONGEST = 2,      /* problem after problem, longest sweep chain (bands x width) first */
+    GSIS_ORDER_BAND_LONGEST = 3  /* band-major, longest chains first within a band */
+} gsis_sweep_order;
+
+typedef struct {
+    int sweep_order;            /* gsis_sweep_order; default GSIS_ORDER_LONGEST */
+    int sweep_dynamic;          /* 1: sweep units from a counter in order; 0: static placement
+                                   when the whole grid is resident (default 1) */
+    int synth_cells_per_cta;    /* strip solver of each problem on the smallest cluster of 2, 4, 8
+                                   or 16 CTAs with at most this many cells per CTA (larger where the
+                                   levels do not fit a CTA); 0 = the cluster gsis_solve uses
+                                   (default 0) */
+} gsis_batch_tuning;
+
+/* Fills *t with the defaults above. */
+void gsis_default_batch_tuning(gsis_batch_tuning* t);
+
+/* Bytes of device workspace for gsis_solve_batch / gsis_batch_autotune on
+ * these problems and options (every problem's gsis_solve workspace plus the
+ * batch tables).  Returns GSIS_OK or GSIS_ERR_ARG. */
+int gsis_batch_workspace_bytes(const gsis_problem* probs, int n, const gsis_options* opt, size_t* bytes);
+
+/*
+ * Solves probs[0..n-1] (1 <= n <= 4096) as described above and writes each
+ * problem's rho, F, iters, err and status.  opt is shared (scheme, precision,
+ * tolerances, pseudo-time, check_every, stall_window; stall detection is per
+ * problem).  tuning: NULL = the tuning gsis_batch_autotune last chose for a
+ * batch of the same shapes and options in this process, else the defaults.
+ * workspace: device, >= gsis_batch_workspace_bytes(), 256-byte aligned.
+ * SYNCHRONISES the stream.  Returns GSIS_OK when every problem returned
+ * GSIS_OK, GSIS_ERR_MAXITER / _DIVERGED / _STALLED when some problem did
+ * (see probs[p].status), or an argument, CUDA, timeout or workspace error
+ * (then no problem's outputs are valid).
+ */
+int gsis_solve_batch(gsis_problem* probs, int n, const gsis_options* opt, const gsis_batch_tuning* tuning,
+                     void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Autotuner of gsis_solve_batch: runs trial_iters iterations (after one
+ * untimed iteration) of every candidate tuning -- the four sweep orders,
+ * static or counter placement, and synth_cells_per_cta in {0, 4096, 16384}
+ * -- from rho^0 = 0, timed with CUDA events on the stream, and keeps the
+ * fastest per iteration (ties to the earlier candidate).  The choice is
+ * remembered for later gsis_solve_batch calls with tuning = NULL on batches
+ * of the same shapes and options.
+ * best: HOST out.  ms_per_iter: HOST out or NULL, the chosen candidate's time.
+ * class_ms: HOST [GSIS_KCLASS_COUNT] out or NULL: device time per iteration of
+ *   each kernel class (sweep, moments, HoT / right-hand side, synthetic,
+ *   update) of the chosen tuning, from events between the class launches.
+ * Problem outputs (rho, F, iters, err, status) are not written.
+ * SYNCHRONISES the stream.
+ */
+int gsis_batch_autotune(gsis_problem* probs, int n, const gsis_options* opt, int trial_iters,
+                        gsis_batch_tuning* best, double* ms_per_iter, double* class_ms,
+                        void* workspace, size_t workspace_bytes, void* stream);
+
+/*
  * gsis_transport_sweep() for callers that cannot allocate device memory.
  * The paper has no counterpart: this is an interface convenience.
  *

@@ -17,6 +17,7 @@
 
 #include "gsis.h"
 #include "gsis_internal.cuh"
+#include "host.h"
 
 using namespace gsis;
 
@@ -25,7 +26,9 @@ namespace {
 thread_local std::string g_last_error;
 thread_local gsis_solve_info g_last_info{};
 
-int fail(int code, const char* fmt, ...)
+}  // namespace
+
+int gsis::fail(int code, const char* fmt, ...)
 {
     char buf[512];
     va_list ap;
@@ -36,12 +39,7 @@ int fail(int code, const char* fmt, ...)
     return code;
 }
 
-#define CK(expr)                                                                                  \
-    do {                                                                                          \
-        cudaError_t e_ = (expr);                                                                  \
-        if (e_ != cudaSuccess)                                                                    \
-            return fail(GSIS_ERR_CUDA, "%s failed: %s", #expr, cudaGetErrorString(e_));          \
-    } while (0)
+namespace {
 
 // ------------------------------------------------------------ instrumentation
 struct Profiler {
@@ -106,12 +104,10 @@ void prof_harvest()
         CK(expr);                                   \
     } while (0)
 
-constexpr size_t kAlign = 256;
-constexpr double kPi = 3.14159265358979323846;
+}  // namespace
 
-struct Sizes {
-    int nx, ny, K, fp32, hist, adjoint;
-};
+namespace gsis {
+
 
 // Carves the workspace (base may be null: size query only).
 size_t layout(const Sizes& z, char* base, Plan* P)
@@ -333,8 +329,10 @@ int prepare(Plan& P, const gsis_mesh* mesh, const gsis_quadrature* quad, const g
         TIMED(GSIS_KCLASS_SETUP, 1, launch_setup(P, st));
     }
     TIMED(GSIS_KCLASS_SETUP, P.fp32 ? 1 : 2, launch_cell_setup(P, opt->cfl_p, opt->beta, st));
-    if (P.scheme == GSIS_SCHEME_GSIS || P.K == 0)
+    if (P.scheme == GSIS_SCHEME_GSIS || P.K == 0) {
         TIMED(GSIS_KCLASS_SETUP, P.mg.nl, launch_mg_setup(P, st));
+        CK(plan_synthetic(P));
+    }
     return GSIS_OK;
 }
 
@@ -361,7 +359,7 @@ Sizes sizes_of(const gsis_mesh* m, const gsis_quadrature* q, const gsis_options*
     return z;
 }
 
-}  // namespace
+}  // namespace gsis
 
 void gsis::set_last_error(int code, const char* msg)
 {

@@ -74,6 +74,8 @@ struct Plan {
     int sweep_grid;                 // persistent sweep CTAs
     int cg_grid;                    // cooperative synthetic CTAs
     int red_grid;                   // per-cell kernels' CTAs (Err reduction partial count)
+    int synth_cl;                   // synthetic solver: strip-solver cluster size, 0 = global-memory solver
+    size_t synth_bytes;             // its dynamic shared memory
 
     // mesh
     const double* dx; const double* dy;
@@ -134,6 +136,7 @@ cudaError_t launch_source_from(const Plan& P, const double* rho_in, cudaStream_t
 cudaError_t launch_hot_rhs(const Plan& P, const double* rho_h, const double* Fx, const double* Fy,
                            const double* fb, const double* guess, cudaStream_t st);
 cudaError_t launch_mg_setup(const Plan& P, cudaStream_t st);
+cudaError_t plan_synthetic(Plan& P);   // before the first solve launch (no runtime calls in the launch)
 cudaError_t launch_synthetic_solve(const Plan& P, const double* guess, double* out, cudaStream_t st);
 int mg_cluster_size();
 cudaError_t launch_update(const Plan& P, const double* rho_new, cudaStream_t st);
@@ -143,6 +146,45 @@ cudaError_t launch_synth_resid(const Plan& P, const double* b, const double* gue
 cudaError_t launch_adjoint_rhs(const Plan& P, const double* nu_new, cudaStream_t st);   // nu, h_bar, rho_bar, inflow
 cudaError_t launch_adjoint_update(const Plan& P, cudaStream_t st);
 cudaError_t launch_adjoint_gradient(const Plan& P, double* grad_sa, double* grad_ss, cudaStream_t st);
+
+// ------------------------------------------------------------ batches
+// Device tables of a batched solve (every problem's arguments of one
+// iteration, built once); problem p of a per-block table owns blocks
+// [bstart[p], bstart[p + 1]).
+struct BatchTables {
+    int B, fp32, pt, with_F, maxK;
+    Status* status;                 // the launch-level sweep counters and error bits
+    long long wait_cycles;
+    // sweep: SweepArgs<T>[B] and the unit segments (one band of one problem each)
+    const void* sweep;
+    const int* seg_start; const int* seg_prob; const int* seg_band;
+    int nseg, ntasks, sweep_grid;
+    int dynamic;                    // 1: units from the counter even when the grid is resident
+    // moments and boundary fluxes, HoT, right-hand side, update
+    const void* mom; const int* mom_bstart; int mom_blocks;
+    const void* hot; const int* hot_bstart; int hot_blocks;
+    const void* rhs; const int* rhs_bstart; int rhs_blocks;
+    const void* upd; const int* upd_bstart; int upd_blocks;
+};
+
+size_t sweep_batch_rec_bytes(int fp32);
+void sweep_batch_rec(const Plan& P, void* out);
+cudaError_t launch_sweep_batch(const BatchTables& bt, cudaStream_t st);
+size_t mom_batch_rec_bytes(int fp32);
+int mom_batch_rec(const Plan& P, bool with_F, void* out);
+cudaError_t launch_moments_batch(const BatchTables& bt, cudaStream_t st);
+size_t hot_batch_rec_bytes();
+size_t rhs_batch_rec_bytes();
+size_t upd_batch_rec_bytes();
+int hot_batch_rec(const Plan& P, void* out);
+int rhs_batch_rec(const Plan& P, void* out);
+int upd_batch_rec(const Plan& P, bool gsis, void* out);
+cudaError_t launch_hot_rhs_batch(const BatchTables& bt, cudaStream_t st);
+cudaError_t launch_update_batch(const BatchTables& bt, cudaStream_t st);
+size_t strip_batch_rec_bytes();
+bool strip_batch_rec(const Plan& P, int cl, void* out, size_t* bytes);
+bool prepare_strip_batch(int cl, size_t bytes);
+cudaError_t launch_strip_batch(const void* tab, int n, int cl, size_t bytes, cudaStream_t st);
 
 int device_sm_count();
 void set_last_error(int code, const char* msg);   // message returned by gsis_last_error()
@@ -217,6 +259,19 @@ __device__ __forceinline__ double block_sum(double v, double* sm)
     }
     __syncthreads();
     return sm[32];
+}
+
+// Largest i in [0, n) with start[i] <= x (start ascending, start[0] <= x):
+// the problem (or segment) of block / unit x in a batched launch.
+__device__ __forceinline__ int batch_find(const int* __restrict__ start, int n, int x)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(start + mid) <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
 }
 
 // Fixed-order sum of n doubles by one warp; identical result in all lanes.

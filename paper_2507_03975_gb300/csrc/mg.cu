@@ -20,6 +20,9 @@
 // sub-iterations of Sec. 4.2) leaves the GSIS fixed point unchanged.
 #include <algorithm>
 #include <cooperative_groups.h>
+#include <cstring>
+#include <map>
+#include <mutex>
 #include <cuda_runtime.h>
 
 #include "gsis_internal.cuh"
@@ -728,7 +731,7 @@ class SCluster {
 
 __device__ __forceinline__ int other_buf(int k) { return k == kSA_X ? kSA_T : kSA_X; }
 
-__global__ void __launch_bounds__(kMgBlock) mg_strip_kernel(const SArgs a)
+__device__ __forceinline__ void strip_body(const SArgs& a)
 {
     __shared__ float slots_f[3 * 2 * kMaxCl];
     __shared__ double slots_d[3 * 2 * kMaxCl];
@@ -1098,6 +1101,14 @@ __global__ void __launch_bounds__(kMgBlock) mg_strip_kernel(const SArgs a)
     cx.sync();
 }
 
+__global__ void __launch_bounds__(kMgBlock) mg_strip_kernel(const SArgs a) { strip_body(a); }
+
+// One cluster per problem: cluster c solves the problem of tab[c].
+__global__ void __launch_bounds__(kMgBlock) mg_strip_batch_kernel(const SArgs* __restrict__ tab)
+{
+    strip_body(tab[blockIdx.x / cg::this_cluster().num_blocks()]);
+}
+
 }  // namespace
 
 // Builds the level hierarchy (once per call; D does not change).
@@ -1196,43 +1207,58 @@ int clusters_fit(const void* fn, int cl, size_t smem)
 
 }  // namespace
 
-// The strip solver when its plan fits a schedulable cluster (16 or 8 CTAs),
-// else the solver with the fine levels in global memory.
-cudaError_t launch_synthetic_solve(const Plan& P, const double* guess, double* out, cudaStream_t st)
+namespace {
+
+// Shared memory one strip-solver CTA may use for its levels.
+size_t strip_smem_cap()
 {
-    {
-        int dev = 0, cap = 0;
-        cudaFuncAttributes fa{};
-        if (cudaGetDevice(&dev) == cudaSuccess &&
-            cudaDeviceGetAttribute(&cap, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
-            cudaFuncGetAttributes(&fa, mg_strip_kernel) == cudaSuccess) {
-            const size_t smem_cap = (size_t)cap > fa.sharedSizeBytes ? (size_t)cap - fa.sharedSizeBytes : 0;
-            for (int cl = std::min(P.mg.cluster, 16); cl >= 8; cl /= 2) {
-                SArgs sa{};
-                size_t bytes = 0;
-                if (!strip_plan(P, cl, smem_cap, sa, bytes)) continue;
-                cudaError_t e = cudaFuncSetAttribute(mg_strip_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                     (int)bytes);
-                if (e != cudaSuccess) return e;
-                if (clusters_fit((const void*)mg_strip_kernel, cl, bytes) < 1) continue;
-                sa.nx = P.nx; sa.ny = P.ny; sa.N = P.N;
-                sa.diag = P.diag; sa.cx = P.cx; sa.cy = P.cy; sa.b = P.b; sa.guess = guess; sa.x = out;
-                sa.r0 = P.mg.r0;
-                sa.norms = P.partials + (size_t)4 * kMaxCgBlocks;
-                sa.rtol = P.synth_rtol;
-                sa.max_iter = P.synth_max_iter;
-                sa.nu = 2;
-                sa.inner_rtol = 1e-4f;
-                sa.omega = 0.8f;
-                sa.alpha = 1.8f;
-                sa.status = P.status;
-                void* args[] = {&sa};
-                return launch_cluster((const void*)mg_strip_kernel, args, cl, bytes, st);
-            }
-        } else {
+    static size_t cap = [] {
+        int dev = 0, c = 0;
+        cudaFuncAttributes fa{}, fb{};
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&c, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+            cudaFuncGetAttributes(&fa, mg_strip_batch_kernel) != cudaSuccess ||
+            cudaFuncGetAttributes(&fb, mg_strip_kernel) != cudaSuccess) {
             cudaGetLastError();
+            return (size_t)0;
         }
-    }
+        const size_t stat = std::max(fa.sharedSizeBytes, fb.sharedSizeBytes);
+        return (size_t)c > stat ? (size_t)c - stat : (size_t)0;
+    }();
+    return cap;
+}
+
+// Raises a kernel's dynamic shared-memory limit (never lowers it: plans of
+// other sizes may launch concurrently).
+cudaError_t raise_limit(const void* fn, size_t bytes)
+{
+    static std::mutex mu;
+    static std::map<const void*, size_t> have;
+    std::lock_guard<std::mutex> g(mu);
+    size_t& h = have[fn];
+    if (bytes <= h) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) h = bytes;
+    return e;
+}
+
+void strip_fill(const Plan& P, const double* guess, double* out, SArgs& sa)
+{
+    sa.nx = P.nx; sa.ny = P.ny; sa.N = P.N;
+    sa.diag = P.diag; sa.cx = P.cx; sa.cy = P.cy; sa.b = P.b; sa.guess = guess; sa.x = out;
+    sa.r0 = P.mg.r0;
+    sa.norms = P.partials + (size_t)4 * kMaxCgBlocks;
+    sa.rtol = P.synth_rtol;
+    sa.max_iter = P.synth_max_iter;
+    sa.nu = 2;
+    sa.inner_rtol = 1e-4f;
+    sa.omega = 0.8f;
+    sa.alpha = 1.8f;
+    sa.status = P.status;
+}
+
+MgArgs fallback_args(const Plan& P, const double* guess, double* out, size_t& smem)
+{
     MgArgs a{};
     a.nl = P.mg.nl;
     a.local_from = P.mg.local_from;
@@ -1256,9 +1282,52 @@ cudaError_t launch_synthetic_solve(const Plan& P, const double* guess, double* o
         off += 6 * P.mg.nx[l] * P.mg.ny[l];
         off = (off + 3) / 4 * 4;
     }
-    const size_t smem = (size_t)off * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(mg_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    smem = (size_t)off * sizeof(float);
+    return a;
+}
+
+}  // namespace
+
+// Chooses the synthetic solver of P before any launch: the strip solver on
+// the largest schedulable cluster (16 or 8 CTAs) whose plan fits, else the
+// solver with the fine levels in global memory; sets the kernels' shared
+// memory limits, so the launches themselves make no other runtime call (a
+// stream capture can record them).
+cudaError_t plan_synthetic(Plan& P)
+{
+    P.synth_cl = 0;
+    P.synth_bytes = 0;
+    const size_t cap = strip_smem_cap();
+    for (int cl = std::min(P.mg.cluster, 16); cap > 0 && cl >= 8; cl /= 2) {
+        SArgs sa{};
+        size_t bytes = 0;
+        if (!strip_plan(P, cl, cap, sa, bytes)) continue;
+        const cudaError_t e = raise_limit((const void*)mg_strip_kernel, bytes);
+        if (e != cudaSuccess) return e;
+        if (clusters_fit((const void*)mg_strip_kernel, cl, bytes) < 1) continue;
+        P.synth_cl = cl;
+        P.synth_bytes = bytes;
+        return cudaSuccess;
+    }
+    size_t smem = 0;
+    (void)fallback_args(P, nullptr, nullptr, smem);
+    P.synth_bytes = smem;
+    return raise_limit((const void*)mg_solve_kernel, smem);
+}
+
+// The solver plan_synthetic chose.
+cudaError_t launch_synthetic_solve(const Plan& P, const double* guess, double* out, cudaStream_t st)
+{
+    if (P.synth_cl > 0) {
+        SArgs sa{};
+        size_t bytes = 0;
+        if (!strip_plan(P, P.synth_cl, (size_t)-1, sa, bytes)) return cudaErrorInvalidConfiguration;
+        strip_fill(P, guess, out, sa);
+        void* args[] = {&sa};
+        return launch_cluster((const void*)mg_strip_kernel, args, P.synth_cl, bytes, st);
+    }
+    size_t smem = 0;
+    const MgArgs a = fallback_args(P, guess, out, smem);
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(P.mg.cluster);
     cfg.blockDim = dim3(kMgBlock);
@@ -1274,13 +1343,68 @@ cudaError_t launch_synthetic_solve(const Plan& P, const double* guess, double* o
     return cudaLaunchKernelEx(&cfg, mg_solve_kernel, a);
 }
 
-// Largest cluster (16, else 8, 4, 2, 1) the device can schedule for the solver.
+size_t strip_batch_rec_bytes() { return sizeof(SArgs); }
+
+// Strip-solver record of P (guess rho^m, solution into x) on clusters of cl
+// CTAs; false when its levels do not fit one CTA's shared memory.
+bool strip_batch_rec(const Plan& P, int cl, void* out, size_t* bytes)
+{
+    SArgs sa{};
+    size_t b = 0;
+    if (!strip_plan(P, cl, strip_smem_cap(), sa, b)) return false;
+    strip_fill(P, P.rho_m, P.x, sa);
+    std::memcpy(out, &sa, sizeof(sa));
+    *bytes = b;
+    return true;
+}
+
+// Makes clusters of cl CTAs with `bytes` of shared memory launchable by the
+// batched strip solver; false if the device cannot schedule one.
+bool prepare_strip_batch(int cl, size_t bytes)
+{
+    if (raise_limit((const void*)mg_strip_batch_kernel, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return clusters_fit((const void*)mg_strip_batch_kernel, cl, bytes) >= 1;
+}
+
+cudaError_t launch_strip_batch(const void* tab, int n, int cl, size_t bytes, cudaStream_t st)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(n * cl);
+    cfg.blockDim = dim3(kMgBlock);
+    cfg.dynamicSmemBytes = bytes;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, mg_strip_batch_kernel, static_cast<const SArgs*>(tab));
+}
+
+// Largest cluster (16, else 8, 4, 2, 1) the device can schedule for the solver
+// (queried once per process).
+static int mg_cluster_size_query();
+
 int mg_cluster_size()
+{
+    static const int c = mg_cluster_size_query();
+    return c;
+}
+
+static int mg_cluster_size_query()
 {
     if (cudaFuncSetAttribute(mg_solve_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
         cudaGetLastError();
     }
     if (cudaFuncSetAttribute(mg_strip_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+    }
+    if (cudaFuncSetAttribute(mg_strip_batch_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
         cudaGetLastError();
     }
     for (int c = 16; c >= 1; c /= 2) {

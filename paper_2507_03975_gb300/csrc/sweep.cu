@@ -22,6 +22,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <vector>
 
 #include "gsis_internal.cuh"
 
@@ -225,6 +229,23 @@ struct SweepArgs {
     long long wait_cycles;
 };
 
+// Several independent problems in one launch: unit u of the launch lies in
+// segment g (seg_start[g] <= u < seg_start[g + 1]); a segment is one band of
+// one problem, all K_p of its directions.  Within a problem the bands appear
+// in increasing order, so a unit's upstream unit has the smaller index.
+template <typename T>
+struct SweepBatch {
+    const SweepArgs<T>* probs;   // [B]
+    const int* seg_start;        // [nseg + 1]
+    const int* seg_prob;         // [nseg]
+    const int* seg_band;         // [nseg]
+    int nseg, ntasks;
+    int dynamic;                 // 1: counter order even when the grid is resident
+    unsigned int* tasks; unsigned int* exits; unsigned int* arrived; int* mode;
+    int* err;                    // the launch's own error bits (a wait outside any unit)
+    long long wait_cycles;
+};
+
 __device__ __forceinline__ double rcp_t(double d) { return 1.0 / d; }
 __device__ __forceinline__ float rcp_t(float d) { return __frcp_rn(d); }
 
@@ -332,9 +353,9 @@ struct SweepSmem {
 // to I, and the last lane also to this band's hand-off row, then arrives on
 // "empty".  Every wait is bounded; on time-out kErrTimeout is raised and the
 // warp leaves after its copies in flight have landed.
-template <typename T, int MODE, bool PRE>
+template <typename T, int MODE, bool PRE, bool BATCH>
 __global__ void __launch_bounds__(kSweepPairs * 64, 1)
-sweep_kernel(const SweepArgs<T> a)
+sweep_kernel(const SweepArgs<T> a1, const SweepBatch<T> bt)
 {
     constexpr bool PT = MODE == kSrcPseudoTime, ADJ = MODE == kSrcAdjoint;
     using SM = SweepSmem<T, MODE != kSrcPlain, PRE>;
@@ -358,66 +379,85 @@ sweep_kernel(const SweepArgs<T> a)
     }
     __syncthreads();
 
-    const int nx = a.nx, ny = a.ny, K = a.K, nb = a.nb;
     const int G = gridDim.x;
-    const int ntasks = K * nb;
-    const int nchunks = (a.nsteps + SEG - 1) / SEG;
-    const long long budget = a.wait_cycles;
+    const int ntasks = BATCH ? bt.ntasks : a1.K * a1.nb;
+    const long long budget = BATCH ? bt.wait_cycles : a1.wait_cycles;
+    unsigned* const c_tasks = BATCH ? bt.tasks : a1.tasks;
+    unsigned* const c_exits = BATCH ? bt.exits : a1.exits;
+    unsigned* const c_arrived = BATCH ? bt.arrived : a1.arrived;
+    int* const c_mode = BATCH ? bt.mode : a1.mode;
 
     __shared__ int cta_mode;
     if (threadIdx.x == 0) {
-        atomicAdd(a.arrived, 1u);
+        atomicAdd(c_arrived, 1u);
         const long long t0 = clock64();
         int m = 0;
         for (;;) {
-            m = *reinterpret_cast<volatile int*>(a.mode);
+            m = *reinterpret_cast<volatile int*>(c_mode);
             if (m != 0) break;
-            if (*reinterpret_cast<volatile unsigned*>(a.arrived) >= (unsigned)G) atomicCAS(a.mode, 0, 1);
-            else if (clock64() - t0 > 20000) atomicCAS(a.mode, 0, 2);
+            if (*reinterpret_cast<volatile unsigned*>(c_arrived) >= (unsigned)G) atomicCAS(c_mode, 0, 1);
+            else if (clock64() - t0 > 20000) atomicCAS(c_mode, 0, 2);
         }
         cta_mode = m;
     }
     __syncthreads();
-    const bool placed = cta_mode == 1;
+    const bool placed = cta_mode == 1 && !(BATCH && bt.dynamic);
 
     unsigned g = 0;   // chunks this pair has handled (buffer = g % NBUF)
     int next_static = pair * G + (int)blockIdx.x;
     bool first = true;
     auto body = [&]() {
-    {
+    if (!BATCH) {
         int stop = 0;
-        if (lane == 0) stop = ld_volatile_int(a.done) | ld_volatile_int(a.err);
+        if (lane == 0) stop = ld_volatile_int(a1.done) | ld_volatile_int(a1.err);
         if (__shfl_sync(kFull, stop, 0)) return;
     }
     for (;;) {
-        int task;
+        int task, prob = 0, ltask;   // launch unit, its problem and the unit within the problem
         if (copier) {
-            // next unit; -1: none left, or an error was raised
-            int t = -1;
+            // next unit; -1: none left, or an error was raised.  In a batch the
+            // units of a problem that has stopped (converged or failed) are skipped.
+            int t = -1, pp = 0, lt = 0;
             if (lane == 0) {
-                if (placed) {
-                    t = next_static;
-                    next_static += kSweepPairs * G;
-                } else {
-                    if (first && pair >= kSweepPairs / 2) {
-                        // the second half of the pairs shares sub-partitions with the
-                        // first half: let the first half take the first units, so that
-                        // concurrently running units start on distinct sub-partitions
-                        const unsigned want = min((unsigned)ntasks, (unsigned)(kSweepPairs / 2) * (unsigned)G);
-                        const long long t0 = clock64();
-                        while (*reinterpret_cast<volatile unsigned*>(a.tasks) < want && clock64() - t0 < 20000)
-                            __nanosleep(64);
+                for (;;) {
+                    if (placed) {
+                        t = next_static;
+                        next_static += kSweepPairs * G;
+                    } else {
+                        if (first && pair >= kSweepPairs / 2) {
+                            // the second half of the pairs shares sub-partitions with the
+                            // first half: let the first half take the first units, so that
+                            // concurrently running units start on distinct sub-partitions
+                            const unsigned want = min((unsigned)ntasks, (unsigned)(kSweepPairs / 2) * (unsigned)G);
+                            const long long t0 = clock64();
+                            while (*reinterpret_cast<volatile unsigned*>(c_tasks) < want && clock64() - t0 < 20000)
+                                __nanosleep(64);
+                        }
+                        first = false;
+                        t = (int)atomicAdd(c_tasks, 1u);
                     }
-                    t = (int)atomicAdd(a.tasks, 1u);
+                    if (t >= ntasks) { t = -1; break; }
+                    if (!BATCH) {
+                        if (ld_volatile_int(a1.err)) t = -1;
+                        lt = t;
+                        break;
+                    }
+                    const int sg = batch_find(bt.seg_start, bt.nseg, t);
+                    pp = bt.seg_prob[sg];
+                    const SweepArgs<T>& q = bt.probs[pp];
+                    if (ld_volatile_int(q.done) | ld_volatile_int(q.err)) continue;
+                    lt = bt.seg_band[sg] * q.K + (t - bt.seg_start[sg]);
+                    break;
                 }
-                if (t >= ntasks || ld_volatile_int(a.err)) t = -1;
             }
             task = __shfl_sync(kFull, t, 0);
+            prob = __shfl_sync(kFull, pp, 0);
+            ltask = __shfl_sync(kFull, lt, 0);
             first = false;
             if (task < 0) {   // end marker in the next buffer, then leave
                 const int b = (int)(g % NBUF);
                 if (g >= NBUF && !__all_sync(kFull, mbar_wait(empty + b, ((g / NBUF) - 1) & 1, budget))) {
-                    if (lane == 0) atomicOr(a.err, kErrTimeout);
+                    if (lane == 0) atomicOr(BATCH ? bt.err : a1.err, kErrTimeout);
                     return;
                 }
                 if (lane == 0) *reinterpret_cast<volatile int*>(buf(b) + SM::off_h) = -1;
@@ -429,14 +469,20 @@ sweep_kernel(const SweepArgs<T> a)
             // the unit is in the header of its first chunk's buffer
             const int b = (int)(g % NBUF);
             if (!__all_sync(kFull, mbar_wait(full + b, (g / NBUF) & 1, budget))) {
-                if (lane == 0) atomicOr(a.err, kErrTimeout);
+                if (lane == 0) atomicOr(BATCH ? bt.err : a1.err, kErrTimeout);
                 return;
             }
-            task = *reinterpret_cast<volatile const int*>(buf(b) + SM::off_h);
+            const volatile int* h = reinterpret_cast<const volatile int*>(buf(b) + SM::off_h);
+            task = h[0];
             if (task < 0) return;
+            prob = h[1];
+            ltask = h[2];
         }
-        const int band = task / K;
-        const int s = task - band * K;
+        const SweepArgs<T>& a = BATCH ? bt.probs[prob] : a1;
+        const int nx = a.nx, ny = a.ny, K = a.K, nb = a.nb, nsteps = a.nsteps;
+        const int nchunks = (nsteps + SEG - 1) / SEG;
+        const int band = ltask / K;
+        const int s = ltask - band * K;
         const bool xpos = a.qmu[s] >= 0.0, ypos = a.qeta[s] >= 0.0;
         const int k = a.perm[s];
         const int jl = band * 32 + lane;
@@ -515,7 +561,7 @@ sweep_kernel(const SweepArgs<T> a)
                     }
                 }
                 if (PRE) {
-                    const int nv = min(SEG, a.nsteps - t0) * 32;   // doubles, multiple of 32
+                    const int nv = min(SEG, nsteps - t0) * 32;   // doubles, multiple of 32
                     double* rb = reinterpret_cast<double*>(bp + SM::off_r);
                     for (int v = 2 * lane; v < nv; v += 64) cp_async<16>(rb + v, rrow + (size_t)t0 * 32 + v);
                 }
@@ -551,7 +597,12 @@ sweep_kernel(const SweepArgs<T> a)
                     }
                 }
                 if (lane < SEG) reinterpret_cast<T*>(bp + SM::off_e)[lane] = ev;
-                if (lane == 0) *reinterpret_cast<volatile int*>(bp + SM::off_h) = task;
+                if (lane == 0) {
+                    volatile int* h = reinterpret_cast<volatile int*>(bp + SM::off_h);
+                    h[0] = task;
+                    h[1] = prob;
+                    h[2] = ltask;
+                }
                 mbar_arrive(full + b);
             }
             // every value of the upstream hand-off row has been taken:
@@ -623,7 +674,7 @@ sweep_kernel(const SweepArgs<T> a)
 #pragma unroll 4
                     for (int tt = 0; tt < SEG; ++tt) {
                         const int t = t0 + tt;
-                        if (t >= a.nsteps) break;
+                        if (t >= nsteps) break;
                         const T e = ein[tt];
                         const T Isouth = __shfl_sync(kFull, lane == 31 ? e : Iprev, (lane + 31) & 31);
                         const int c = t - lane;
@@ -666,11 +717,11 @@ sweep_kernel(const SweepArgs<T> a)
     __syncwarp();
     if (lane == 0) {
         __threadfence();
-        if (atomicAdd(a.exits, 1u) == (unsigned)G * (unsigned)(2 * kSweepPairs) - 1u) {
-            *a.tasks = 0u;
-            *a.arrived = 0u;
-            *a.mode = 0;
-            *a.exits = 0u;
+        if (atomicAdd(c_exits, 1u) == (unsigned)G * (unsigned)(2 * kSweepPairs) - 1u) {
+            *c_tasks = 0u;
+            *c_arrived = 0u;
+            *c_mode = 0;
+            *c_exits = 0u;
         }
     }
 }
@@ -691,7 +742,7 @@ struct MomArgs {
 // Per cell, in original direction order k = 0..K-1:
 // rho = sum w I, F = sum w Omega I, P = sum w Omega Omega I.
 template <typename T, bool WITH_F, bool WITH_P>
-__global__ void __launch_bounds__(kRedBlock) moments_kernel(const MomArgs<T> a)
+__device__ __forceinline__ void moments_body(const MomArgs<T>& a, int bid, int nblk)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* cf = reinterpret_cast<T*>(smem_raw);                     // [K][6]
@@ -708,7 +759,7 @@ __global__ void __launch_bounds__(kRedBlock) moments_kernel(const MomArgs<T> a)
         sk[k] = a.sidx[k];
     }
     __syncthreads();
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < a.N; c += gridDim.x * blockDim.x) {
+    for (int c = bid * blockDim.x + threadIdx.x; c < a.N; c += nblk * blockDim.x) {
         T r = T(0), fx = T(0), fy = T(0), pxx = T(0), pxy = T(0), pyy = T(0);
 #pragma unroll 4
         for (int k = 0; k < a.K; ++k) {
@@ -747,16 +798,25 @@ __global__ void __launch_bounds__(kRedBlock) moments_kernel(const MomArgs<T> a)
 // (outgoing: boundary cell intensity, incoming: inflow).  One warp per face;
 // lane l sums k = l, l+32, ... in order, then a fixed shuffle tree.
 template <typename T>
-__global__ void __launch_bounds__(256) bflux_kernel(int nx, int ny, int K, const T* __restrict__ I,
-                                                    const int* __restrict__ sidx, const double* __restrict__ mu,
-                                                    const double* __restrict__ eta, const double* __restrict__ w,
-                                                    const double* __restrict__ inflow, double* fb, const int* done)
+struct BfArgs {
+    int nx, ny, K;
+    const T* I;
+    const int* sidx;
+    const double* mu; const double* eta; const double* w;   // original order
+    const double* inflow;
+    double* fb;
+    const int* done;
+};
+
+template <typename T>
+__device__ __forceinline__ void bflux_body(const BfArgs<T>& a, int bid, int nblk)
 {
-    if (done && ld_volatile_int(done)) return;
+    if (a.done && ld_volatile_int(a.done)) return;
+    const int nx = a.nx, ny = a.ny, K = a.K;
     const int nbf = 2 * (nx + ny), N = nx * ny;
     const int lane = threadIdx.x & 31;
-    const int warps = (gridDim.x * blockDim.x) >> 5;
-    for (int f = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; f < nbf; f += warps) {
+    const int warps = (nblk * blockDim.x) >> 5;
+    for (int f = (bid * blockDim.x + threadIdx.x) >> 5; f < nbf; f += warps) {
         int c, axis;
         double sgn;
         if (f < ny) { c = nx * f; axis = 0; sgn = -1.0; }
@@ -765,14 +825,52 @@ __global__ void __launch_bounds__(256) bflux_kernel(int nx, int ny, int K, const
         else { c = (f - 2 * ny - nx) + nx * (ny - 1); axis = 1; sgn = 1.0; }
         T acc = T(0);
         for (int k = lane; k < K; k += 32) {
-            const double on = sgn * (axis == 0 ? mu[k] : eta[k]);
+            const double on = sgn * (axis == 0 ? a.mu[k] : a.eta[k]);
             T Iface;
-            if (on >= 0.0) Iface = I[(size_t)sidx[k] * N + c];
-            else Iface = inflow ? (T)inflow[(size_t)f * K + k] : T(0);
-            acc = fma((T)(w[k] * on), Iface, acc);
+            if (on >= 0.0) Iface = a.I[(size_t)a.sidx[k] * N + c];
+            else Iface = a.inflow ? (T)a.inflow[(size_t)f * K + k] : T(0);
+            acc = fma((T)(a.w[k] * on), Iface, acc);
         }
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-        if (lane == 0) fb[f] = (double)acc;
+        if (lane == 0) a.fb[f] = (double)acc;
+    }
+}
+
+template <typename T, bool WITH_F, bool WITH_P>
+__global__ void __launch_bounds__(kRedBlock) moments_kernel(const MomArgs<T> a)
+{
+    moments_body<T, WITH_F, WITH_P>(a, blockIdx.x, gridDim.x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) bflux_kernel(const BfArgs<T> a)
+{
+    bflux_body(a, blockIdx.x, gridDim.x);
+}
+
+// Batched moments and boundary fluxes: problem p owns blocks
+// [bstart[p], bstart[p + 1]); its first mblocks blocks take the cell moments,
+// the rest the boundary faces.
+template <typename T>
+struct MomBatchRec {
+    MomArgs<T> m;
+    BfArgs<T> f;
+    int mblocks;
+};
+
+template <typename T, bool WITH_F, bool WITH_P>
+__global__ void __launch_bounds__(kRedBlock) moments_batch_kernel(const MomBatchRec<T>* __restrict__ tab,
+                                                                  const int* __restrict__ bstart, int B)
+{
+    const int p = batch_find(bstart, B, blockIdx.x);
+    const int b0 = __ldg(bstart + p), nblk = __ldg(bstart + p + 1) - b0, lb = blockIdx.x - b0;
+    const int mb = tab[p].mblocks;
+    if (lb < mb) {
+        const MomArgs<T> a = tab[p].m;
+        moments_body<T, WITH_F, WITH_P>(a, lb, mb);
+    } else {
+        const BfArgs<T> a = tab[p].f;
+        bflux_body(a, lb - mb, nblk - mb);
     }
 }
 
@@ -787,8 +885,8 @@ int grid_for(long long n, int block, int cap)
 template <typename T, int MODE>
 size_t sweep_smem();
 
-template <typename T, int MODE, bool PRE>
-cudaError_t launch_sweep_t(Plan& P, cudaStream_t st)
+template <typename T, int MODE>
+SweepArgs<T> sweep_args(const Plan& P)
 {
     SweepArgs<T> a{};
     a.nx = P.nx; a.ny = P.ny; a.N = P.N; a.K = P.K; a.nb = P.nb; a.nsteps = P.nx + 31;
@@ -819,7 +917,36 @@ cudaError_t launch_sweep_t(Plan& P, cudaStream_t st)
     a.arrived = &P.status->sweep_arrived;
     a.mode = &P.status->sweep_mode;
     a.wait_cycles = P.wait_cycles;
-    sweep_kernel<T, MODE, PRE><<<P.sweep_grid, kSweepPairs * 64, sweep_smem<T, MODE>(), st>>>(a);
+    return a;
+}
+
+template <typename T, int MODE, bool PRE>
+cudaError_t launch_sweep_t(Plan& P, cudaStream_t st)
+{
+    const SweepArgs<T> a = sweep_args<T, MODE>(P);
+    sweep_kernel<T, MODE, PRE, false><<<P.sweep_grid, kSweepPairs * 64, sweep_smem<T, MODE>(), st>>>(a, SweepBatch<T>{});
+    return cudaGetLastError();
+}
+
+template <typename T, int MODE>
+cudaError_t launch_sweep_batch_t(const BatchTables& bt, cudaStream_t st)
+{
+    SweepBatch<T> b{};
+    b.probs = static_cast<const SweepArgs<T>*>(bt.sweep);
+    b.seg_start = bt.seg_start;
+    b.seg_prob = bt.seg_prob;
+    b.seg_band = bt.seg_band;
+    b.nseg = bt.nseg;
+    b.ntasks = bt.ntasks;
+    b.dynamic = bt.dynamic;
+    b.tasks = &bt.status->sweep_tasks;
+    b.exits = &bt.status->sweep_exits;
+    b.arrived = &bt.status->sweep_arrived;
+    b.mode = &bt.status->sweep_mode;
+    b.err = &bt.status->error;
+    b.wait_cycles = bt.wait_cycles;
+    sweep_kernel<T, MODE, sizeof(T) == 8, true><<<bt.sweep_grid, kSweepPairs * 64, sweep_smem<T, MODE>(), st>>>(
+        SweepArgs<T>{}, b);
     return cudaGetLastError();
 }
 
@@ -827,6 +954,20 @@ template <typename T>
 size_t moments_smem(int K)
 {
     return (size_t)K * (6 * sizeof(T) + sizeof(int)) + 16;
+}
+
+template <typename T>
+BfArgs<T> bflux_args(const Plan& P, double* fb_out, const int* done)
+{
+    BfArgs<T> f{};
+    f.nx = P.nx; f.ny = P.ny; f.K = P.K;
+    f.I = static_cast<const T*>(P.I);
+    f.sidx = P.sidx;
+    f.mu = P.omu; f.eta = P.oeta; f.w = P.ow;
+    f.inflow = P.inflow;
+    f.fb = fb_out;
+    f.done = done;
+    return f;
 }
 
 template <typename T>
@@ -854,7 +995,7 @@ cudaError_t launch_moments_t(const Plan& P, bool with_F, bool with_P, double* rh
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     bflux_kernel<T><<<grid_for((long long)P.nbf * 32, 256, P.num_sms * 4), 256, 0, st>>>(
-        P.nx, P.ny, P.K, static_cast<const T*>(P.I), P.sidx, a.mu, a.eta, a.w, P.inflow, fb_out, a.done);
+        bflux_args<T>(P, fb_out, a.done));
     return cudaGetLastError();
 }
 
@@ -864,33 +1005,57 @@ size_t sweep_smem()
     return SweepSmem<T, MODE != kSrcPlain, sizeof(T) == 8>::bytes;
 }
 
+template <typename T, int MODE, bool BATCH>
+cudaError_t sweep_attr()
+{
+    return cudaFuncSetAttribute(sweep_kernel<T, MODE, sizeof(T) == 8, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sweep_smem<T, MODE>());
+}
+
+// Raises the dynamic shared-memory limit of fn to at least `bytes` (never
+// lowers it: plans of different sizes may launch concurrently).
+cudaError_t raise_smem_limit(const void* fn, size_t bytes)
+{
+    static std::mutex mu;
+    static std::map<const void*, size_t> have;
+    std::lock_guard<std::mutex> g(mu);
+    size_t& h = have[fn];
+    if (bytes <= h) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) h = bytes;
+    return e;
+}
+
 template <typename T>
 cudaError_t prepare_t(int K)
 {
+    static std::once_flag once;
+    static cudaError_t first = cudaSuccess;
+    std::call_once(once, [] {
+        cudaError_t e;
+        if ((e = sweep_attr<T, kSrcPlain, false>()) != cudaSuccess ||
+            (e = sweep_attr<T, kSrcPseudoTime, false>()) != cudaSuccess ||
+            (e = sweep_attr<T, kSrcAdjoint, false>()) != cudaSuccess ||
+            (e = sweep_attr<T, kSrcPlain, true>()) != cudaSuccess ||
+            (e = sweep_attr<T, kSrcPseudoTime, true>()) != cudaSuccess)
+            first = e;
+    });
+    if (first != cudaSuccess) return first;
+    const size_t ms = moments_smem<T>(K);
     cudaError_t e;
-    const int ms = (int)moments_smem<T>(K);
-    if ((e = cudaFuncSetAttribute(sweep_kernel<T, kSrcPlain, sizeof(T) == 8>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)sweep_smem<T, kSrcPlain>())) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(sweep_kernel<T, kSrcPseudoTime, sizeof(T) == 8>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)sweep_smem<T, kSrcPseudoTime>())) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(sweep_kernel<T, kSrcAdjoint, sizeof(T) == 8>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)sweep_smem<T, kSrcAdjoint>())) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(moments_kernel<T, true, true>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, ms)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(moments_kernel<T, true, false>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, ms)) != cudaSuccess) return e;
-    return cudaFuncSetAttribute(moments_kernel<T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ms);
+    if ((e = raise_smem_limit((const void*)moments_kernel<T, true, true>, ms)) != cudaSuccess) return e;
+    if ((e = raise_smem_limit((const void*)moments_kernel<T, true, false>, ms)) != cudaSuccess) return e;
+    if ((e = raise_smem_limit((const void*)moments_kernel<T, false, false>, ms)) != cudaSuccess) return e;
+    if ((e = raise_smem_limit((const void*)moments_batch_kernel<T, true, false>, ms)) != cudaSuccess) return e;
+    return raise_smem_limit((const void*)moments_batch_kernel<T, false, false>, ms);
 }
 
-template <typename T, int MODE>
+template <typename T, int MODE, bool BATCH>
 int sweep_occupancy()
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<T, MODE, sizeof(T) == 8>, kSweepPairs * 64,
-                                                      sweep_smem<T, MODE>()) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<T, MODE, sizeof(T) == 8, BATCH>,
+                                                      kSweepPairs * 64, sweep_smem<T, MODE>()) != cudaSuccess)
         return 0;
     return n;
 }
@@ -984,6 +1149,75 @@ cudaError_t launch_moments_to(const Plan& P, bool with_F, bool with_P, double* r
     return launch_moments_t<double>(P, with_F, with_P, rho_out, Fout, Pout, gsis_correct, fb_out, force, st);
 }
 
+size_t sweep_batch_rec_bytes(int fp32)
+{
+    return fp32 ? sizeof(SweepArgs<float>) : sizeof(SweepArgs<double>);
+}
+
+void sweep_batch_rec(const Plan& P, void* out)
+{
+    if (P.fp32) {
+        const SweepArgs<float> a = P.pt ? sweep_args<float, kSrcPseudoTime>(P) : sweep_args<float, kSrcPlain>(P);
+        std::memcpy(out, &a, sizeof(a));
+    } else {
+        const SweepArgs<double> a = P.pt ? sweep_args<double, kSrcPseudoTime>(P) : sweep_args<double, kSrcPlain>(P);
+        std::memcpy(out, &a, sizeof(a));
+    }
+}
+
+cudaError_t launch_sweep_batch(const BatchTables& bt, cudaStream_t st)
+{
+    if (bt.fp32)
+        return bt.pt ? launch_sweep_batch_t<float, kSrcPseudoTime>(bt, st) : launch_sweep_batch_t<float, kSrcPlain>(bt, st);
+    return bt.pt ? launch_sweep_batch_t<double, kSrcPseudoTime>(bt, st) : launch_sweep_batch_t<double, kSrcPlain>(bt, st);
+}
+
+size_t mom_batch_rec_bytes(int fp32)
+{
+    return fp32 ? sizeof(MomBatchRec<float>) : sizeof(MomBatchRec<double>);
+}
+
+template <typename T>
+int mom_batch_rec_t(const Plan& P, bool with_F, void* out)
+{
+    MomBatchRec<T> r{};
+    r.m.nx = P.nx; r.m.ny = P.ny; r.m.N = P.N; r.m.K = P.K;
+    r.m.I = static_cast<const T*>(P.I);
+    r.m.sidx = P.sidx;
+    r.m.mu = P.omu; r.m.eta = P.oeta; r.m.w = P.ow;
+    r.m.rho = P.rho_h;
+    r.m.Fx = with_F ? P.Fx : nullptr;
+    r.m.Fy = with_F ? P.Fy : nullptr;
+    r.m.done = &P.status->done;
+    r.f = bflux_args<T>(P, P.fb, &P.status->done);
+    r.mblocks = grid_for(P.N, kRedBlock, P.num_sms * 8);
+    std::memcpy(out, &r, sizeof(r));
+    return r.mblocks + grid_for((long long)P.nbf * 32, kRedBlock, P.num_sms * 4);
+}
+
+// Batched record of the moments of one GSIS / SI iteration (rho^{m+1/2},
+// F^{m+1/2} when with_F, boundary fluxes); returns the problem's blocks.
+int mom_batch_rec(const Plan& P, bool with_F, void* out)
+{
+    return P.fp32 ? mom_batch_rec_t<float>(P, with_F, out) : mom_batch_rec_t<double>(P, with_F, out);
+}
+
+cudaError_t launch_moments_batch(const BatchTables& bt, cudaStream_t st)
+{
+    const int fp32 = bt.fp32;
+    const size_t smem = fp32 ? moments_smem<float>(bt.maxK) : moments_smem<double>(bt.maxK);
+    if (fp32) {
+        const auto* tab = static_cast<const MomBatchRec<float>*>(bt.mom);
+        if (bt.with_F) moments_batch_kernel<float, true, false><<<bt.mom_blocks, kRedBlock, smem, st>>>(tab, bt.mom_bstart, bt.B);
+        else moments_batch_kernel<float, false, false><<<bt.mom_blocks, kRedBlock, smem, st>>>(tab, bt.mom_bstart, bt.B);
+    } else {
+        const auto* tab = static_cast<const MomBatchRec<double>*>(bt.mom);
+        if (bt.with_F) moments_batch_kernel<double, true, false><<<bt.mom_blocks, kRedBlock, smem, st>>>(tab, bt.mom_bstart, bt.B);
+        else moments_batch_kernel<double, false, false><<<bt.mom_blocks, kRedBlock, smem, st>>>(tab, bt.mom_bstart, bt.B);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t prepare_kernels(int K, int fp32, int pt)
 {
     (void)pt;
@@ -996,10 +1230,12 @@ int sweep_max_active_blocks(int fp32, int pt)
     // adjoint): every warp pair must be resident, so take the smallest
     (void)pt;
     if (fp32)
-        return std::min({sweep_occupancy<float, kSrcPlain>(), sweep_occupancy<float, kSrcPseudoTime>(),
-                         sweep_occupancy<float, kSrcAdjoint>()});
-    return std::min({sweep_occupancy<double, kSrcPlain>(), sweep_occupancy<double, kSrcPseudoTime>(),
-                     sweep_occupancy<double, kSrcAdjoint>()});
+        return std::min({sweep_occupancy<float, kSrcPlain, false>(), sweep_occupancy<float, kSrcPseudoTime, false>(),
+                         sweep_occupancy<float, kSrcAdjoint, false>(), sweep_occupancy<float, kSrcPlain, true>(),
+                         sweep_occupancy<float, kSrcPseudoTime, true>()});
+    return std::min({sweep_occupancy<double, kSrcPlain, false>(), sweep_occupancy<double, kSrcPseudoTime, false>(),
+                     sweep_occupancy<double, kSrcAdjoint, false>(), sweep_occupancy<double, kSrcPlain, true>(),
+                     sweep_occupancy<double, kSrcPseudoTime, true>()});
 }
 
 }  // namespace gsis

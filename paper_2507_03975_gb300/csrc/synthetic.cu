@@ -15,6 +15,8 @@
 //  * Err(rho) (Eq. (Err_W)), convergence decision, next angular source.
 #include <cuda_runtime.h>
 
+#include <cstring>
+
 #include "gsis_internal.cuh"
 
 namespace gsis {
@@ -31,14 +33,21 @@ int grid_for(long long n, int block, int cap)
     return (int)g;
 }
 
+struct HotArgs {
+    int nx, ny;
+    const double* hw; const double* rho; const double* Fx; const double* Fy;
+    double* hotx; double* hoty;
+    const int* done;
+};
+
 // HoT = F + G / (3 sigma_t) with the gradient weights of the cell set-up.
-__global__ void hot_kernel(int nx, int ny, const double* __restrict__ hw, const double* __restrict__ rho,
-                           const double* __restrict__ Fx, const double* __restrict__ Fy, double* hotx,
-                           double* hoty, const int* done)
+__device__ __forceinline__ void hot_body(const HotArgs& a, int bid, int nblk)
 {
-    if (ld_volatile_int(done)) return;
-    const int N = nx * ny;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+    if (ld_volatile_int(a.done)) return;
+    const int nx = a.nx, ny = a.ny, N = nx * ny;
+    const double* hw = a.hw; const double* rho = a.rho; const double* Fx = a.Fx; const double* Fy = a.Fy;
+    double* hotx = a.hotx; double* hoty = a.hoty;
+    for (int c = bid * blockDim.x + threadIdx.x; c < N; c += nblk * blockDim.x) {
         const int j = c / nx, i = c - j * nx;
         const double ri = rho[c];
         double gx = 0.0, gy = 0.0;
@@ -50,6 +59,8 @@ __global__ void hot_kernel(int nx, int ny, const double* __restrict__ hw, const 
         hoty[c] = Fy[c] + gy;
     }
 }
+
+__global__ void hot_kernel(const HotArgs a) { hot_body(a, blockIdx.x, gridDim.x); }
 
 struct RhsArgs {
     int nx, ny;
@@ -66,8 +77,8 @@ struct RhsArgs {
 };
 
 // b, then r0 = b - D guess (five-point D) and the fixed-order sums r0.r0, b.b
-// (last-block ticket).
-__global__ void __launch_bounds__(kRedBlock) rhs_kernel(const RhsArgs a)
+// (last-block ticket).  Block bid of the problem's nblk blocks.
+__device__ __forceinline__ void rhs_body(const RhsArgs& a, int bid, int nblk)
 {
     __shared__ double sm[33];
     __shared__ int am_last;
@@ -76,47 +87,49 @@ __global__ void __launch_bounds__(kRedBlock) rhs_kernel(const RhsArgs a)
     const double* dx = a.dx; const double* dy = a.dy;
     const double* hotx = a.hotx; const double* hoty = a.hoty; const double* fb = a.fb;
     double lrr = 0.0, lbb = 0.0;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+    for (int c = bid * blockDim.x + threadIdx.x; c < N; c += nblk * blockDim.x) {
         const int j = c / nx, i = c - j * nx;
         const double hx = dx[i], hy = dy[j];
+        // explicit fma: the single-problem and batched kernels that inline
+        // this body then round identically
         double v = hx * hy * a.q[c];
-        if (i + 1 < nx) v -= hy * 0.5 * (hotx[c] + hotx[c + 1]);
-        if (i > 0) v += hy * 0.5 * (hotx[c] + hotx[c - 1]);
-        if (j + 1 < ny) v -= hx * 0.5 * (hoty[c] + hoty[c + nx]);
-        if (j > 0) v += hx * 0.5 * (hoty[c] + hoty[c - nx]);
+        if (i + 1 < nx) v = fma(-0.5 * hy, hotx[c] + hotx[c + 1], v);
+        if (i > 0) v = fma(0.5 * hy, hotx[c] + hotx[c - 1], v);
+        if (j + 1 < ny) v = fma(-0.5 * hx, hoty[c] + hoty[c + nx], v);
+        if (j > 0) v = fma(0.5 * hx, hoty[c] + hoty[c - nx], v);
         const double rh = a.rho_h[c];
         const double* bf = a.bface;
-        if (i == 0) v -= hy * fb[j] - bf[j] * rh;
-        if (i == nx - 1) v -= hy * fb[ny + j] - bf[ny + j] * rh;
-        if (j == 0) v -= hx * fb[2 * ny + i] - bf[2 * ny + i] * rh;
-        if (j == ny - 1) v -= hx * fb[2 * ny + nx + i] - bf[2 * ny + nx + i] * rh;
+        if (i == 0) v -= fma(hy, fb[j], -(bf[j] * rh));
+        if (i == nx - 1) v -= fma(hy, fb[ny + j], -(bf[ny + j] * rh));
+        if (j == 0) v -= fma(hx, fb[2 * ny + i], -(bf[2 * ny + i] * rh));
+        if (j == ny - 1) v -= fma(hx, fb[2 * ny + nx + i], -(bf[2 * ny + nx + i] * rh));
         a.b[c] = v;
         const double* g = a.guess;
         double dg = a.diag[c] * g[c];
-        if (i + 1 < nx) dg -= a.cx[c] * g[c + 1];
-        if (i > 0) dg -= a.cx[c - 1] * g[c - 1];
-        if (j + 1 < ny) dg -= a.cy[c] * g[c + nx];
-        if (j > 0) dg -= a.cy[c - nx] * g[c - nx];
+        if (i + 1 < nx) dg = fma(-a.cx[c], g[c + 1], dg);
+        if (i > 0) dg = fma(-a.cx[c - 1], g[c - 1], dg);
+        if (j + 1 < ny) dg = fma(-a.cy[c], g[c + nx], dg);
+        if (j > 0) dg = fma(-a.cy[c - nx], g[c - nx], dg);
         const double rv = v - dg;
         a.r0[c] = (float)rv;
-        lrr += rv * rv;
-        lbb += v * v;
+        lrr = fma(rv, rv, lrr);
+        lbb = fma(v, v, lbb);
     }
     lrr = block_sum(lrr, sm);
     lbb = block_sum(lbb, sm);
     if (threadIdx.x == 0) {
-        a.partials[blockIdx.x] = lrr;
-        a.partials[gridDim.x + blockIdx.x] = lbb;
+        a.partials[bid] = lrr;
+        a.partials[nblk + bid] = lbb;
         __threadfence();
         const unsigned t = atomicAdd(&a.status->ticket, 1u);
-        am_last = (t == gridDim.x - 1);
+        am_last = (t == (unsigned)nblk - 1u);
     }
     __syncthreads();
     if (!am_last) return;
     if (threadIdx.x < 32) {
         __threadfence();
-        const double srr = warp_sum_array(a.partials, gridDim.x);
-        const double sbb = warp_sum_array(a.partials + gridDim.x, gridDim.x);
+        const double srr = warp_sum_array(a.partials, nblk);
+        const double sbb = warp_sum_array(a.partials + nblk, nblk);
         if (threadIdx.x == 0) {
             a.norms[0] = srr;
             a.norms[1] = sbb;
@@ -124,6 +137,8 @@ __global__ void __launch_bounds__(kRedBlock) rhs_kernel(const RhsArgs a)
         }
     }
 }
+
+__global__ void __launch_bounds__(kRedBlock) rhs_kernel(const RhsArgs a) { rhs_body(a, blockIdx.x, gridDim.x); }
 
 struct UpdArgs {
     int nx, ny, N;
@@ -144,39 +159,41 @@ struct UpdArgs {
 // intensity I^{m+1/2} + (rho^{m+1} - rho^{m+1/2})/4pi (Eq. (GSIS_update));
 // the sweep keeps I^{m+1/2}, so the correction enters the source:
 // src = (sigma_s rho + q)/4pi + shift (rho - rho^{m+1/2})/4pi).
-__global__ void __launch_bounds__(kRedBlock) update_kernel(const UpdArgs a)
+__device__ __forceinline__ void update_body(const UpdArgs& a, int bid, int nblk)
 {
     __shared__ double sm[33];
     __shared__ int am_last;
     if (ld_volatile_int(&a.status->done)) return;
     double num = 0.0, den = 0.0;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < a.N; c += gridDim.x * blockDim.x) {
+    for (int c = bid * blockDim.x + threadIdx.x; c < a.N; c += nblk * blockDim.x) {
         const int j = c / a.nx, i = c - j * a.nx;
         const double V = a.dx[i] * a.dy[j];
         const double nw = a.rho_new[c], od = a.rho_m[c];
-        num += (nw - od) * (nw - od) * V;
-        den += nw * nw * V;
+        const double d = nw - od;
+        // explicit fma (identical rounding in every kernel inlining this body)
+        num = fma(d * d, V, num);
+        den = fma(nw * nw, V, den);
         a.rho_m[c] = nw;
-        double s = (a.sigma_s[c] * nw + a.q[c]) * kInvFourPi;
-        if (a.pt) s += a.shift[c] * (nw - a.rho_h[c]) * kInvFourPi;
+        double s = fma(a.sigma_s[c], nw, a.q[c]) * kInvFourPi;
+        if (a.pt) s = fma(a.shift[c] * (nw - a.rho_h[c]), kInvFourPi, s);
         a.src[c] = s;
         if (a.src_f) a.src_f[c] = (float)s;
     }
     num = block_sum(num, sm);
     den = block_sum(den, sm);
     if (threadIdx.x == 0) {
-        a.partials[blockIdx.x] = num;
-        a.partials[gridDim.x + blockIdx.x] = den;
+        a.partials[bid] = num;
+        a.partials[nblk + bid] = den;
         __threadfence();
         const unsigned t = atomicAdd(&a.status->ticket, 1u);
-        am_last = (t == gridDim.x - 1);
+        am_last = (t == (unsigned)nblk - 1u);
     }
     __syncthreads();
     if (!am_last) return;
     if (threadIdx.x < 32) {
         __threadfence();
-        const double sn = warp_sum_array(a.partials, gridDim.x);
-        const double sd = warp_sum_array(a.partials + gridDim.x, gridDim.x);
+        const double sn = warp_sum_array(a.partials, nblk);
+        const double sd = warp_sum_array(a.partials + nblk, nblk);
         if (threadIdx.x == 0) {
             double err;
             if (sd > 0.0) err = sqrt(sn / sd);
@@ -200,15 +217,29 @@ __global__ void __launch_bounds__(kRedBlock) update_kernel(const UpdArgs a)
     }
 }
 
-}  // namespace
+__global__ void __launch_bounds__(kRedBlock) update_kernel(const UpdArgs a) { update_body(a, blockIdx.x, gridDim.x); }
 
-cudaError_t launch_hot_rhs(const Plan& P, const double* rho_h, const double* Fx, const double* Fy,
-                           const double* fb, const double* guess, cudaStream_t st)
+// Batched launches: problem p owns blocks [bstart[p], bstart[p + 1]).
+template <typename A, void (*BODY)(const A&, int, int)>
+__global__ void __launch_bounds__(kRedBlock) batch_kernel(const A* __restrict__ tab, const int* __restrict__ bstart,
+                                                          int B)
 {
-    const int g = grid_for(P.N, 256, P.num_sms * 8);
-    hot_kernel<<<g, 256, 0, st>>>(P.nx, P.ny, P.hw, rho_h, Fx, Fy, P.hotx, P.hoty, &P.status->done);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    const int p = batch_find(bstart, B, blockIdx.x);
+    const int b0 = __ldg(bstart + p);
+    const A a = tab[p];
+    BODY(a, blockIdx.x - b0, __ldg(bstart + p + 1) - b0);
+}
+
+HotArgs hot_args(const Plan& P, const double* rho_h, const double* Fx, const double* Fy)
+{
+    HotArgs h{};
+    h.nx = P.nx; h.ny = P.ny; h.hw = P.hw; h.rho = rho_h; h.Fx = Fx; h.Fy = Fy;
+    h.hotx = P.hotx; h.hoty = P.hoty; h.done = &P.status->done;
+    return h;
+}
+
+RhsArgs rhs_args(const Plan& P, const double* rho_h, const double* fb, const double* guess)
+{
     RhsArgs a{};
     a.nx = P.nx; a.ny = P.ny; a.dx = P.dx; a.dy = P.dy;
     a.sigt = P.sigt; a.q = P.q; a.rho_h = rho_h; a.hotx = P.hotx; a.hoty = P.hoty; a.fb = fb; a.b = P.b;
@@ -218,11 +249,10 @@ cudaError_t launch_hot_rhs(const Plan& P, const double* rho_h, const double* Fx,
     a.partials = P.partials;
     a.norms = P.partials + (size_t)4 * kMaxCgBlocks;
     a.status = P.status;
-    rhs_kernel<<<P.red_grid, kRedBlock, 0, st>>>(a);
-    return cudaGetLastError();
+    return a;
 }
 
-cudaError_t launch_update(const Plan& P, const double* rho_new, cudaStream_t st)
+UpdArgs upd_args(const Plan& P, const double* rho_new)
 {
     UpdArgs a{};
     a.nx = P.nx; a.ny = P.ny; a.N = P.N; a.dx = P.dx; a.dy = P.dy;
@@ -233,7 +263,70 @@ cudaError_t launch_update(const Plan& P, const double* rho_new, cudaStream_t st)
     a.partials = P.partials + (size_t)9 * kMaxCgBlocks;
     a.hist = P.hist;
     a.status = P.status;
-    update_kernel<<<P.red_grid, kRedBlock, 0, st>>>(a);
+    return a;
+}
+
+}  // namespace
+
+cudaError_t launch_hot_rhs(const Plan& P, const double* rho_h, const double* Fx, const double* Fy,
+                           const double* fb, const double* guess, cudaStream_t st)
+{
+    const int g = grid_for(P.N, 256, P.num_sms * 8);
+    hot_kernel<<<g, 256, 0, st>>>(hot_args(P, rho_h, Fx, Fy));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    rhs_kernel<<<P.red_grid, kRedBlock, 0, st>>>(rhs_args(P, rho_h, fb, guess));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update(const Plan& P, const double* rho_new, cudaStream_t st)
+{
+    update_kernel<<<P.red_grid, kRedBlock, 0, st>>>(upd_args(P, rho_new));
+    return cudaGetLastError();
+}
+
+// Batched records of one GSIS / SI iteration (the arrays the per-problem
+// iteration passes); each returns the problem's blocks.
+size_t hot_batch_rec_bytes() { return sizeof(HotArgs); }
+size_t rhs_batch_rec_bytes() { return sizeof(RhsArgs); }
+size_t upd_batch_rec_bytes() { return sizeof(UpdArgs); }
+
+int hot_batch_rec(const Plan& P, void* out)
+{
+    const HotArgs h = hot_args(P, P.rho_h, P.Fx, P.Fy);
+    std::memcpy(out, &h, sizeof(h));
+    return grid_for(P.N, kRedBlock, P.num_sms * 8);
+}
+
+int rhs_batch_rec(const Plan& P, void* out)
+{
+    const RhsArgs a = rhs_args(P, P.rho_h, P.fb, P.rho_m);
+    std::memcpy(out, &a, sizeof(a));
+    return P.red_grid;
+}
+
+int upd_batch_rec(const Plan& P, bool gsis, void* out)
+{
+    const UpdArgs a = upd_args(P, gsis ? P.x : P.rho_h);
+    std::memcpy(out, &a, sizeof(a));
+    return P.red_grid;
+}
+
+cudaError_t launch_hot_rhs_batch(const BatchTables& bt, cudaStream_t st)
+{
+    batch_kernel<HotArgs, hot_body><<<bt.hot_blocks, kRedBlock, 0, st>>>(
+        static_cast<const HotArgs*>(bt.hot), bt.hot_bstart, bt.B);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    batch_kernel<RhsArgs, rhs_body><<<bt.rhs_blocks, kRedBlock, 0, st>>>(
+        static_cast<const RhsArgs*>(bt.rhs), bt.rhs_bstart, bt.B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_batch(const BatchTables& bt, cudaStream_t st)
+{
+    batch_kernel<UpdArgs, update_body><<<bt.upd_blocks, kRedBlock, 0, st>>>(
+        static_cast<const UpdArgs*>(bt.upd), bt.upd_bstart, bt.B);
     return cudaGetLastError();
 }
 

@@ -67,6 +67,25 @@ class Options(ctypes.Structure):
     ]
 
 
+class Problem(ctypes.Structure):
+    _fields_ = [
+        ("mesh", Mesh), ("quad", Quadrature),
+        ("sigma_a", ctypes.c_void_p), ("sigma_s", ctypes.c_void_p), ("q", ctypes.c_void_p),
+        ("inflow", ctypes.c_void_p), ("rho", ctypes.c_void_p), ("F", ctypes.c_void_p),
+        ("iters", ctypes.c_int), ("err", ctypes.c_double), ("status", ctypes.c_int),
+    ]
+
+
+class BatchTuning(ctypes.Structure):
+    _fields_ = [("sweep_order", ctypes.c_int), ("sweep_dynamic", ctypes.c_int),
+                ("synth_cells_per_cta", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+ORDER_PROBLEM, ORDER_BAND, ORDER_LONGEST, ORDER_BAND_LONGEST = 0, 1, 2, 3
+
 _lib = None
 
 
@@ -110,6 +129,15 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.gsis_status_string.restype = ctypes.c_char_p
     lib.gsis_last_error.argtypes = []
     lib.gsis_last_error.restype = ctypes.c_char_p
+    Pp, Tp, dp = ctypes.POINTER(Problem), ctypes.POINTER(BatchTuning), ctypes.POINTER(ctypes.c_double)
+    lib.gsis_default_batch_tuning.argtypes = [Tp]
+    lib.gsis_default_batch_tuning.restype = None
+    lib.gsis_batch_workspace_bytes.argtypes = [Pp, ctypes.c_int, Op, ctypes.POINTER(sz)]
+    lib.gsis_batch_workspace_bytes.restype = ctypes.c_int
+    lib.gsis_solve_batch.argtypes = [Pp, ctypes.c_int, Op, Tp, vp, sz, vp]
+    lib.gsis_solve_batch.restype = ctypes.c_int
+    lib.gsis_batch_autotune.argtypes = [Pp, ctypes.c_int, Op, ctypes.c_int, Tp, dp, dp, vp, sz, vp]
+    lib.gsis_batch_autotune.restype = ctypes.c_int
     for name in ("gsis_quadrature_level_symmetric", "gsis_workspace_bytes", "gsis_solve",
                  "gsis_transport_sweep", "gsis_synthetic_step"):
         getattr(lib, name).restype = ctypes.c_int
@@ -391,3 +419,82 @@ def solve_differentiable(dx, dy, mu, eta, w, sigma_a, sigma_s, q, inflow=None, o
     if _GsisSolve is None:
         _GsisSolve = _autograd_function()
     return _GsisSolve.apply(sigma_a, sigma_s, q, (dx, dy, mu, eta, w), inflow, options)
+
+
+# ------------------------------------------------------------------ batches
+def default_batch_tuning(**kw) -> BatchTuning:
+    t = BatchTuning()
+    load().gsis_default_batch_tuning(ctypes.byref(t))
+    for k, v in kw.items():
+        if not hasattr(t, k):
+            raise KeyError(k)
+        setattr(t, k, v)
+    return t
+
+
+class _Batch:
+    """C records of a list of problems; each problem is a mapping with dx, dy,
+    mu, eta, w (host arrays) and sigma_a, sigma_s, q, optional inflow
+    (float64 CUDA tensors).  Keeps every host array alive."""
+
+    def __init__(self, problems, with_outputs=True):
+        import torch
+        if not problems:
+            raise ValueError("empty batch")
+        self.args = [_Args(p["dx"], p["dy"], p["mu"], p["eta"], p["w"]) for p in problems]
+        self.arr = (Problem * len(problems))()
+        self.rho, self.F = [], []
+        for i, (p, a) in enumerate(zip(problems, self.args)):
+            N, K = a.mesh.nx * a.mesh.ny, a.quad.K
+            r = self.arr[i]
+            r.mesh, r.quad = a.mesh, a.quad
+            r.sigma_a = _dev(p["sigma_a"], N, "sigma_a")
+            r.sigma_s = _dev(p["sigma_s"], N, "sigma_s")
+            r.q = _dev(p["q"], N, "q")
+            r.inflow = _dev(p.get("inflow"), 2 * (a.mesh.nx + a.mesh.ny) * K, "inflow")
+            dev = p["sigma_a"].device
+            rho = torch.empty(N, dtype=torch.float64, device=dev) if with_outputs else None
+            F = torch.empty(2 * N, dtype=torch.float64, device=dev) if with_outputs else None
+            r.rho = _dev(rho)
+            r.F = _dev(F)
+            self.rho.append(rho)
+            self.F.append(F)
+        self.device = problems[0]["sigma_a"].device
+
+
+def batch_workspace_bytes(problems, options: Options | None = None) -> int:
+    b = _Batch(problems, with_outputs=False)
+    o = options or default_options()
+    n = ctypes.c_size_t(0)
+    _raise(load().gsis_batch_workspace_bytes(b.arr, len(problems), ctypes.byref(o), ctypes.byref(n)))
+    return int(n.value)
+
+
+def solve_batch(problems, options: Options | None = None, tuning: BatchTuning | None = None,
+                workspace=None, stream=None):
+    """gsis_solve_batch: returns dict(results=[dict(rho, F, iters, err, status)], status, workspace)."""
+    b = _Batch(problems)
+    o = options or default_options()
+    workspace = _workspace(batch_workspace_bytes(problems, o), workspace, b.device)
+    rc = load().gsis_solve_batch(b.arr, len(problems), ctypes.byref(o), ctypes.byref(tuning) if tuning else None,
+                                 ctypes.c_void_p(workspace.data_ptr()), ctypes.c_size_t(workspace.numel()),
+                                 _stream(stream))
+    _raise(rc)
+    res = [dict(rho=b.rho[i], F=b.F[i], iters=b.arr[i].iters, err=b.arr[i].err, status=b.arr[i].status)
+           for i in range(len(problems))]
+    return dict(results=res, status=rc, workspace=workspace)
+
+
+def batch_autotune(problems, options: Options | None = None, trial_iters: int = 3, workspace=None, stream=None):
+    """gsis_batch_autotune: returns dict(tuning, ms_per_iter, class_ms, workspace)."""
+    b = _Batch(problems, with_outputs=False)
+    o = options or default_options()
+    workspace = _workspace(batch_workspace_bytes(problems, o), workspace, b.device)
+    t = BatchTuning()
+    ms = ctypes.c_double(0.0)
+    cls = (ctypes.c_double * len(KERNEL_CLASSES))()
+    _raise(load().gsis_batch_autotune(b.arr, len(problems), ctypes.byref(o), trial_iters, ctypes.byref(t),
+                                      ctypes.byref(ms), cls, ctypes.c_void_p(workspace.data_ptr()),
+                                      ctypes.c_size_t(workspace.numel()), _stream(stream)))
+    return dict(tuning=t, ms_per_iter=ms.value, class_ms=dict(zip(KERNEL_CLASSES, list(cls))),
+                workspace=workspace)

@@ -237,3 +237,55 @@ def config_small() -> Problem:
 def config_channel() -> Problem:
     """256x256 cells, S12 (84 directions), 2000 / 0.2 channel, seed 2."""
     return channel_problem(256, 12, 2, name="channel_256x256_S12")
+
+
+def smooth_field(n: int, rng: np.random.Generator, modes: int = 16, kmax: int = 4) -> np.ndarray:
+    """Unit-variance smooth random field on the n x n cell centres of the unit
+    square: sum of `modes` Fourier modes with integer wave vectors
+    0 < |k| <= kmax and uniform random phases, scaled by sqrt(2/modes) (each
+    cosine has variance 1/2 over a uniform phase)."""
+    ks = [(kx, ky) for kx in range(-kmax, kmax + 1) for ky in range(-kmax, kmax + 1)
+          if 0 < kx * kx + ky * ky <= kmax * kmax]
+    pick = rng.choice(len(ks), modes, replace=False)
+    phase = rng.uniform(0.0, 2.0 * math.pi, modes)
+    x = (np.arange(n) + 0.5) / n
+    X, Y = np.meshgrid(x, x, indexing="xy")   # X varies along i (x), Y along j
+    g = np.zeros((n, n))
+    for m, idx in enumerate(pick):
+        kx, ky = ks[idx]
+        g += np.cos(2.0 * math.pi * (kx * X + ky * Y) + phase[m])
+    return (g * math.sqrt(2.0 / modes)).reshape(-1)
+
+
+def batch_problems(n: int = 64, seed: int = 4, side_range=(32, 256), orders=(8, 10, 12, 14, 16),
+                   log10_lo: float = -2.0, log10_span: float = 6.0, ratio_range=(0.5, 0.9999)) -> list:
+    """Independent square problems of uneven size for the batched solve.
+    Side = round(s0 * (s1/s0)^u), u ~ U[0,1] (log-uniform in [s0, s1]); order
+    uniform over `orders`; log10 sigma_t = log10_lo + log10_span * Phi(g) with
+    g a unit-variance smooth field (Phi the standard normal CDF, so the
+    marginal of sigma_t is log-uniform); one scattering ratio per problem,
+    uniform in ratio_range; q = 1; vacuum walls; uniform mesh on the unit
+    square (PCG64 seeded)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    s0, s1 = side_range
+    out = []
+    for p in range(n):
+        side = int(round(s0 * (s1 / s0) ** rng.uniform()))
+        order = int(orders[rng.integers(len(orders))])
+        g = smooth_field(side, rng)
+        phi = 0.5 * (1.0 + np.vectorize(math.erf)(g / math.sqrt(2.0)))
+        sig_t = 10.0 ** (log10_lo + log10_span * phi)
+        ratio = rng.uniform(*ratio_range)
+        mu, eta, w = level_symmetric_2d(order)
+        sig_s = ratio * sig_t
+        sig_a = sig_t - sig_s
+        out.append(Problem(f"batch{seed}_{p}_{side}x{side}_S{order}", side, side, uniform_mesh(side),
+                           uniform_mesh(side), mu, eta, w, sig_a, sig_s, np.ones(side * side), None))
+    return out
+
+
+def config_batch() -> list:
+    """64 problems, seed 4: sides 32-256 log-uniform, S8-S16, sigma_t
+    log-uniform in [1e-2, 1e4] on smooth fields, ratio U[0.5, 0.9999], q = 1,
+    vacuum."""
+    return batch_problems()
