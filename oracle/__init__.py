@@ -1,4 +1,4 @@
-"""FP64 CPU oracle for the steady gray-RTE source iteration and GSIS.
+"""FP64 CPU oracle for the gray-RTE source iteration and GSIS (steady and time-dependent).
 
 TEST INFRASTRUCTURE ONLY: only tests/, __graft_entry__.smoke() and bench.py's
 CPU-baseline leg may import or run anything here.  The oracle shares no code
@@ -9,6 +9,10 @@ against closed forms, invariants or brute force on tiny inputs; none is
 "parity unpinned".  The adjoint (oracle/adjoint.py) is pinned by
 tests/test_oracle_adjoint.py: dot-product identities of each transposed step
 against the forward oracle and central differences of full forward solves.
+The time-dependent radiation-material steps (oracle/timedep.py) are pinned
+by tests/test_oracle_timedep.py: brute-force solves of the fully implicit
+and the Fleck-Cummings systems on tiny meshes, equilibrium preservation,
+energy conservation and the long-step radiative-equilibrium limit.
 """
 from .gsis import (  # noqa: F401
     angular_source, transport_sweep, alsm_gradient, high_order_terms, geometry, pseudo_time_shift,
