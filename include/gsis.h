@@ -226,6 +226,57 @@ int gsis_adjoint(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis_
                  int* iters_out, double* err_out, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * Time-dependent gray radiation-material problem (Sec. 2.1, Eqs. (RTE_g),
+ * (Tm_g), emission phi = a c T^4, isotropic scattering, q a fixed volume
+ * source) by backward Euler (Sec. 4.1, Eq. (RTE_d)): nsteps steps of dt from
+ * rho^0, T^0 with the isotropic initial intensity I^0 = rho^0 / 4pi.
+ * Each step iterates, until Err(rho) < opt->tol (Eq. (Err_W)):
+ *   opt->scheme == GSIS_SCHEME_GSIS: the kinetic step (1/(c dt) on the
+ *     diagonal, I^n/(c dt) and sigma_a phi(T^m) in the source, Eqs.
+ *     (RTE_g_semi), (RTE_d_res)) and the coupled rho-T synthetic system
+ *     (Eqs. (GSIS_dse), (MSE_d), (Tm_d)), one Newton step about T^m per
+ *     iteration with T eliminated cell by cell (its diagonal gains
+ *     V (1/(c dt) + f sigma_a - sigma_a), f = (C_v/dt)/(C_v/dt + 4 a c T^3
+ *     sigma_a)); at convergence the step is the implicit discrete solution;
+ *   opt->scheme == GSIS_SCHEME_SI: source iteration with the Fleck-Cummings
+ *     linearisation about T^n (Eqs. (Tm_semi_linear), (RTE_SI),
+ *     (arti_sigmaT); mu = 1 - f with the factor 4 of the derivation).
+ * The intensities of consecutive steps stay in the workspace (two K x N
+ * arrays, FP32 with GSIS_FP32_SWEEP).
+ */
+typedef struct {
+    double dt;      /* time step, > 0 */
+    double c;       /* speed of light, > 0 */
+    double a;       /* radiation constant, > 0 */
+    double cv;      /* volumetric heat capacity C_v, > 0 */
+    int nsteps;     /* backward-Euler steps, >= 1 */
+} gsis_time_params;
+
+/* Bytes of device workspace for gsis_td_solve (the gsis_solve layout plus the
+ * previous step's intensities and seven per-cell arrays). */
+int gsis_td_workspace_bytes(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis_options* opt,
+                            size_t* bytes);
+
+/*
+ * sigma_a, sigma_s, q, inflow: as in gsis_solve (opacities do not depend on T).
+ * rho0 (>= 0), T0 (> 0): device [N] initial state.  rho, T: device [N] out,
+ * the state after the last step.  F: device [2N] out (first moment of the
+ * last sweep) or NULL.  step_iters, step_err: HOST [nsteps] out or NULL,
+ * inner iterations and final Err of every step.
+ * opt: scheme, precision, tol / max_iter / fixed_iters per step, synthetic
+ * controls, check_every, wait_limit_s; pseudo-time must be off (cfl_p, beta
+ * <= 0, else GSIS_ERR_ARG).  Synchronises the stream.
+ * Returns GSIS_OK when every step converged; GSIS_ERR_MAXITER or
+ * GSIS_ERR_DIVERGED when a step did not (the solve stops there and rho, T
+ * hold that step's last iterate); argument, CUDA, timeout, workspace errors.
+ */
+int gsis_td_solve(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis_options* opt,
+                  const gsis_time_params* tp, const double* sigma_a, const double* sigma_s, const double* q,
+                  const double* inflow, const double* rho0, const double* T0, double* rho, double* T,
+                  double* F, int* step_iters, double* step_err, void* workspace, size_t workspace_bytes,
+                  void* stream);
+
+/*
  * Batched solve: n independent steady problems, each with its own mesh,
  * quadrature, opacities, sources and inflow, iterated together under one set
  * of options.  The paper solves one problem at a time and has no counterpart

@@ -196,6 +196,11 @@ size_t layout(const Sizes& z, char* base, Plan* P)
         p.adj_inflow = reinterpret_cast<double*>(take(nbf * K * sizeof(double)));
         p.refl = reinterpret_cast<int*>(take(K * sizeof(int)));
     }
+    if (z.td) {
+        p.In = take(K * N * Ts);
+        double** td[] = {&p.td.rho_n, &p.td.T_n, &p.td.T, &p.td.cn, &p.td.cnext, &p.td.qeff, &p.td.diag0};
+        for (double** d : td) *d = reinterpret_cast<double*>(take(N * sizeof(double)));
+    }
     return off;
 }
 

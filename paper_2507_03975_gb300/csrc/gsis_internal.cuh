@@ -74,6 +74,7 @@ struct Plan {
     int sweep_grid;                 // persistent sweep CTAs
     int cg_grid;                    // cooperative synthetic CTAs
     int red_grid;                   // per-cell kernels' CTAs (Err reduction partial count)
+    double shift0;                  // 1/(c dt) added to the kinetic diagonal (time step; 0 when steady)
     int synth_cl;                   // synthetic solver: strip-solver cluster size, 0 = global-memory solver
     size_t synth_bytes;             // its dynamic shared memory
 
@@ -89,6 +90,7 @@ struct Plan {
     const float* acoef_f; const float* bcoef_f;
     const double* rsw;              // FP64: 1/d in sweep order [K][nb][nx+31][32]
     void* I;                        // [K][N] T, intensities of the last sweep (sorted s)
+    void* In;                       // [K][N] T, intensities of the previous time step (time-dependent only)
     void* edge;                     // [K][nb][nx] T, last row of each band (all-ones bytes = not yet written)
     // cell data
     const double* sigma_a; const double* sigma_s; const double* q; const double* inflow;
@@ -104,6 +106,7 @@ struct Plan {
     double* bface;                  // [nbf] boundary face area * beta
     double* hotx; double* hoty; double* b;
     double* x; double* r; double* z; double* p; double* qv;
+    const double* q_syn;            // volume source of the synthetic equation if not q (time step)
     double* partials;               // reductions scratch
     double* hist;                   // [max_iter]
     Status* status;
@@ -117,6 +120,15 @@ struct Plan {
     double* nu;                     // nu (adjoint of the synthetic equation)
     const double* g;                // dJ/drho (caller's device array)
     int* refl;                      // [K] sorted index of the reflected direction
+    // time-dependent radiation-material problem (allocated by the time-step layout only)
+    struct {
+        double* rho_n; double* T_n;     // state at t^n
+        double* T;                      // current material temperature T^m
+        double* cn;                     // isotropic correction of I^n (I^n = In + cn), per cell
+        double* cnext;                  // the correction of the current iterate (becomes cn)
+        double* qeff;                   // volume source of the synthetic equation
+        double* diag0;                  // synthetic diagonal without the time and coupling terms
+    } td;
 };
 
 // ------------------------------------------------------------ launchers
@@ -275,6 +287,50 @@ __device__ __forceinline__ int batch_find(const int* __restrict__ start, int n, 
 }
 
 // Fixed-order sum of n doubles by one warp; identical result in all lanes.
+__device__ __forceinline__ double warp_sum_array(const double* a, int n);
+
+// Err(rho) = sqrt(sum num / sum den) over the nblk blocks of one problem
+// (fixed-order partials, last-block ticket), its history entry and the stop
+// decision.  Called by every thread of the block with its block sums.
+__device__ __forceinline__ void err_reduce_decide(double num, double den, double* partials, double* hist,
+                                                  Status* S, double tol, int fixed_iters, int max_iter, int bid,
+                                                  int nblk, int* am_last)
+{
+    if (threadIdx.x == 0) {
+        partials[bid] = num;
+        partials[nblk + bid] = den;
+        __threadfence();
+        const unsigned t = atomicAdd(&S->ticket, 1u);
+        *am_last = (t == (unsigned)nblk - 1u);
+    }
+    __syncthreads();
+    if (!*am_last) return;
+    if (threadIdx.x < 32) {
+        __threadfence();
+        const double sn = warp_sum_array(partials, nblk);
+        const double sd = warp_sum_array(partials + nblk, nblk);
+        if (threadIdx.x == 0) {
+            double err;
+            if (sd > 0.0) err = sqrt(sn / sd);
+            else err = (sn == 0.0) ? 0.0 : INFINITY;
+            const int it = S->iter;
+            hist[it] = err;
+            S->iter = it + 1;
+            S->err = err;
+            int reason = kRunning;
+            if (!isfinite(err) || err > 1e6) reason = kDiverged;
+            else if (fixed_iters > 0) { if (it + 1 >= fixed_iters) reason = kFixedDone; }
+            else if (err < tol) reason = kConverged;
+            else if (it + 1 >= max_iter) reason = kMaxIter;
+            if (reason != kRunning) {
+                S->reason = reason;
+                S->done = 1;
+            }
+            S->ticket = 0u;
+        }
+    }
+}
+
 __device__ __forceinline__ double warp_sum_array(const double* a, int n)
 {
     const int lane = threadIdx.x & 31;

@@ -26,7 +26,7 @@ int fail(int code, const char* fmt, ...);
     } while (0)
 
 struct Sizes {
-    int nx, ny, K, fp32, hist, adjoint;
+    int nx, ny, K, fp32, hist, adjoint, td;
 };
 
 // Carves one problem's workspace (base may be null: size query only).

@@ -69,7 +69,7 @@ __global__ void cell_setup_kernel(int nx, int ny, const double* __restrict__ dx,
                                   const double* __restrict__ dy, const double* __restrict__ sa,
                                   const double* __restrict__ ss, const double* __restrict__ q,
                                   const double* __restrict__ inflow, int n_inflow,
-                                  double cfl_p, double beta, double* sigt, float* sigt_f,
+                                  double shift0, double cfl_p, double beta, double* sigt, float* sigt_f,
                                   double* shift, float* shift_f, double* diag, double* cx,
                                   double* cy, double* hw, double* bface, int* err)
 {
@@ -109,7 +109,7 @@ __global__ void cell_setup_kernel(int nx, int ny, const double* __restrict__ dx,
             gS = 1.0 / (3.0 * o);
         }
         const double ref = fmin(hx, hy);
-        double sh = 0.0;
+        double sh = shift0;   // 1/(c dt) of a time step (0 when steady)
         if (cfl_p > 0.0) sh += 1.0 / (cfl_p * ref);
         if (beta > 0.0) sh += th / (beta * ref);
         shift[c] = sh;
@@ -216,6 +216,7 @@ struct SweepArgs {
     const T* acoef; const T* bcoef;
     const double* rsw;
     const T* sigt; const T* shift; const T* src;
+    const T* iold;              // stored intensities of the delta form: I^m (pseudo-time) or I^n (time step)
     const T* ax; const T* ay;   // adjoint source: bx, by (src holds a)
     const double* qw;           // sorted weights (adjoint source)
     T* I; T* edge;
@@ -501,7 +502,7 @@ sweep_kernel(const SweepArgs<T> a1, const SweepBatch<T> bt)
             if (!PRE) wsrc[SM::W_SIGT] = a.sigt;
             if (PT) {
                 wsrc[SM::W_SHIFT] = a.shift;
-                wsrc[SM::W_IOLD] = Is;
+                wsrc[SM::W_IOLD] = a.iold + (size_t)s * a.N;
             }
             if (ADJ) {
                 wsrc[SM::W_SHIFT] = a.ax;
@@ -897,6 +898,7 @@ SweepArgs<T> sweep_args(const Plan& P)
     }
     a.rsw = P.rsw;
     a.I = static_cast<T*>(P.I);
+    a.iold = P.In ? static_cast<const T*>(P.In) : a.I;
     a.edge = static_cast<T*>(P.edge);
     a.inflow = P.inflow;
     if (MODE == kSrcAdjoint) {   // transposed kinetic step: reflected direction, adjoint source
@@ -1084,7 +1086,7 @@ cudaError_t launch_setup(const Plan& P, cudaStream_t st)
 cudaError_t launch_cell_setup(const Plan& P, double cfl_p, double beta, cudaStream_t st)
 {
     cell_setup_kernel<<<grid_for(P.N, 256, P.num_sms * 8), 256, 0, st>>>(
-        P.nx, P.ny, P.dx, P.dy, P.sigma_a, P.sigma_s, P.q, P.inflow, P.nbf * P.K, cfl_p, beta, P.sigt,
+        P.nx, P.ny, P.dx, P.dy, P.sigma_a, P.sigma_s, P.q, P.inflow, P.nbf * P.K, P.shift0, cfl_p, beta, P.sigt,
         P.fp32 ? P.sigt_f : nullptr, P.shift, P.fp32 ? P.shift_f : nullptr, P.diag, P.cx, P.cy, P.hw,
         P.bface, &P.status->error);
     cudaError_t e = cudaGetLastError();

@@ -181,40 +181,7 @@ __device__ __forceinline__ void update_body(const UpdArgs& a, int bid, int nblk)
     }
     num = block_sum(num, sm);
     den = block_sum(den, sm);
-    if (threadIdx.x == 0) {
-        a.partials[bid] = num;
-        a.partials[nblk + bid] = den;
-        __threadfence();
-        const unsigned t = atomicAdd(&a.status->ticket, 1u);
-        am_last = (t == (unsigned)nblk - 1u);
-    }
-    __syncthreads();
-    if (!am_last) return;
-    if (threadIdx.x < 32) {
-        __threadfence();
-        const double sn = warp_sum_array(a.partials, nblk);
-        const double sd = warp_sum_array(a.partials + nblk, nblk);
-        if (threadIdx.x == 0) {
-            double err;
-            if (sd > 0.0) err = sqrt(sn / sd);
-            else err = (sn == 0.0) ? 0.0 : INFINITY;
-            Status* S = a.status;
-            const int it = S->iter;
-            a.hist[it] = err;
-            S->iter = it + 1;
-            S->err = err;
-            int reason = kRunning;
-            if (!isfinite(err) || err > 1e6) reason = kDiverged;
-            else if (a.fixed_iters > 0) { if (it + 1 >= a.fixed_iters) reason = kFixedDone; }
-            else if (err < a.tol) reason = kConverged;
-            else if (it + 1 >= a.max_iter) reason = kMaxIter;
-            if (reason != kRunning) {
-                S->reason = reason;
-                S->done = 1;
-            }
-            S->ticket = 0u;
-        }
-    }
+    err_reduce_decide(num, den, a.partials, a.hist, a.status, a.tol, a.fixed_iters, a.max_iter, bid, nblk, &am_last);
 }
 
 __global__ void __launch_bounds__(kRedBlock) update_kernel(const UpdArgs a) { update_body(a, blockIdx.x, gridDim.x); }
@@ -242,7 +209,7 @@ RhsArgs rhs_args(const Plan& P, const double* rho_h, const double* fb, const dou
 {
     RhsArgs a{};
     a.nx = P.nx; a.ny = P.ny; a.dx = P.dx; a.dy = P.dy;
-    a.sigt = P.sigt; a.q = P.q; a.rho_h = rho_h; a.hotx = P.hotx; a.hoty = P.hoty; a.fb = fb; a.b = P.b;
+    a.sigt = P.sigt; a.q = P.q_syn ? P.q_syn : P.q; a.rho_h = rho_h; a.hotx = P.hotx; a.hoty = P.hoty; a.fb = fb; a.b = P.b;
     a.bface = P.bface;
     a.diag = P.diag; a.cx = P.cx; a.cy = P.cy; a.guess = guess;
     a.r0 = P.mg.r0;

@@ -498,3 +498,57 @@ def batch_autotune(problems, options: Options | None = None, trial_iters: int = 
                                       ctypes.c_size_t(workspace.numel()), _stream(stream)))
     return dict(tuning=t, ms_per_iter=ms.value, class_ms=dict(zip(KERNEL_CLASSES, list(cls))),
                 workspace=workspace)
+
+
+# ------------------------------------------------------------ time-dependent
+class TimeParams(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("c", ctypes.c_double), ("a", ctypes.c_double),
+                ("cv", ctypes.c_double), ("nsteps", ctypes.c_int)]
+
+
+def _td_load():
+    lib = load()
+    if not getattr(lib, "_td_bound", False):
+        vp, sz = ctypes.c_void_p, ctypes.c_size_t
+        Mp, Qp, Op = ctypes.POINTER(Mesh), ctypes.POINTER(Quadrature), ctypes.POINTER(Options)
+        lib.gsis_td_workspace_bytes.argtypes = [Mp, Qp, Op, ctypes.POINTER(sz)]
+        lib.gsis_td_workspace_bytes.restype = ctypes.c_int
+        lib.gsis_td_solve.argtypes = [Mp, Qp, Op, ctypes.POINTER(TimeParams), vp, vp, vp, vp, vp, vp, vp, vp, vp,
+                                      ctypes.POINTER(ctypes.c_int), _P, vp, sz, vp]
+        lib.gsis_td_solve.restype = ctypes.c_int
+        lib._td_bound = True
+    return lib
+
+
+def td_workspace_bytes(dx, dy, mu, eta, w, options: Options | None = None) -> int:
+    a = _Args(dx, dy, mu, eta, w)
+    o = options or default_options()
+    n = ctypes.c_size_t(0)
+    _raise(_td_load().gsis_td_workspace_bytes(ctypes.byref(a.mesh), ctypes.byref(a.quad), ctypes.byref(o),
+                                              ctypes.byref(n)))
+    return int(n.value)
+
+
+def td_solve(dx, dy, mu, eta, w, sigma_a, sigma_s, q, rho0, T0, dt, nsteps, c=1.0, a=1.0, cv=1.0,
+             inflow=None, options: Options | None = None, workspace=None, stream=None):
+    """gsis_td_solve: returns dict(rho, T, F, step_iters, step_err, status, workspace)."""
+    import torch
+    args = _Args(dx, dy, mu, eta, w)
+    o = options or default_options()
+    N, K = args.mesh.nx * args.mesh.ny, args.quad.K
+    dev = sigma_a.device
+    rho = torch.empty(N, dtype=torch.float64, device=dev)
+    T = torch.empty(N, dtype=torch.float64, device=dev)
+    F = torch.empty(2 * N, dtype=torch.float64, device=dev)
+    its = (ctypes.c_int * nsteps)()
+    errs = np.zeros(nsteps)
+    tp = TimeParams(dt, c, a, cv, nsteps)
+    workspace = _workspace(td_workspace_bytes(args.dx, args.dy, args.mu, args.eta, args.w, o), workspace, dev)
+    rc = _td_load().gsis_td_solve(
+        ctypes.byref(args.mesh), ctypes.byref(args.quad), ctypes.byref(o), ctypes.byref(tp),
+        _dev(sigma_a, N, "sigma_a"), _dev(sigma_s, N, "sigma_s"), _dev(q, N, "q"),
+        _dev(inflow, 2 * (args.mesh.nx + args.mesh.ny) * K, "inflow"), _dev(rho0, N, "rho0"), _dev(T0, N, "T0"),
+        _dev(rho), _dev(T), _dev(F), its, _hp(errs), ctypes.c_void_p(workspace.data_ptr()),
+        ctypes.c_size_t(workspace.numel()), _stream(stream))
+    _raise(rc)
+    return dict(rho=rho, T=T, F=F, step_iters=np.array(list(its)), step_err=errs, status=rc, workspace=workspace)

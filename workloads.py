@@ -289,3 +289,33 @@ def config_batch() -> list:
     log-uniform in [1e-2, 1e4] on smooth fields, ratio U[0.5, 0.9999], q = 1,
     vacuum."""
     return batch_problems()
+
+
+def channel_td_problem(n: int = 1024, order: int = 16, seed: int = 2, base: int = 256, width: int = 8,
+                       sigma_bulk: float = 2000.0, sigma_channel: float = 0.2, ratio: float = 0.999,
+                       name=None) -> Problem:
+    """The 256x256 channel geometry scaled by n/base: the base mask (`width`
+    cells wide, seed 2) with every cell replaced by an (n/base)^2 block (a 32-cell
+    wide channel at n = 1024); bulk sigma_t = 2000, channel sigma_t = 0.2,
+    scattering ratio 0.999, isotropic unit intensity entering through the
+    left wall, vacuum elsewhere, q = 0; uniform mesh on the unit square."""
+    f = n // base
+    if f < 1 or f * base != n:
+        raise ValueError("n must be a multiple of base")
+    m = np.kron(channel_mask(base, seed, width), np.ones((f, f), dtype=bool)).reshape(-1)
+    mu, eta, w = level_symmetric_2d(order)
+    sig_t = np.where(m, sigma_channel, sigma_bulk)
+    sig_s = ratio * sig_t
+    inflow = isotropic_inflow(n, n, mu, eta, {"W": 1.0})
+    return Problem(name or f"channel_td_{n}x{n}_S{order}_seed{seed}", n, n, uniform_mesh(n), uniform_mesh(n),
+                   mu, eta, w, sig_t - sig_s, sig_s, np.zeros(n * n), inflow)
+
+
+# time stepping of the radiation-material workload: backward Euler, dt = 1e-3,
+# 100 steps, c = a = C_v = 1, cold start T^0 = 0.1 with rho^0 = a c (T^0)^4
+TIMEDEP = dict(dt=1e-3, nsteps=100, c=1.0, a=1.0, cv=1.0, T0=0.1)
+
+
+def config_timedep() -> Problem:
+    """1024x1024 cells, S16 (144 directions), the channel scaled x4."""
+    return channel_td_problem()
