@@ -196,6 +196,69 @@ def batch_measure(gsis, torch, stream, hbm, steps=3):
                                "algorithmic_bytes": algo}}
 
 
+def timedep_measure(gsis, torch, stream, hbm):
+    """The time-dependent radiation-material workload: 1024x1024 cells, S16
+    (144 directions), the channel geometry scaled x4 (32-cell channel,
+    sigma_t 2000 / 0.2, ratio 0.999, unit intensity through the left wall),
+    emission sigma_a a c T^4 with a = c = C_v = 1, cold start T = 0.1,
+    100 backward-Euler steps of dt = 1e-3.  GSIS (Newton-eliminated rho-T
+    synthetic system, capped at SYNTH_CAP inner iterations) and SI with the
+    Fleck-Cummings linearisation, FP32 sweeps (Err < 1e-6 per step: the FP32
+    floor) and GSIS with FP64 sweeps (Err < 1e-8).  Device time with CUDA
+    events around each whole solve, inputs resident."""
+    p = W.config_timedep()
+    tpd = W.TIMEDEP
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    sa, ss, q, inflow = t(p.sigma_a), t(p.sigma_s), t(p.q), t(p.inflow.reshape(-1))
+    T0 = t(np.full(p.N, tpd["T0"]))
+    rho0 = t(np.full(p.N, tpd["a"] * tpd["c"] * tpd["T0"] ** 4))
+    upd = p.N * p.K
+    out = {"workload": "channel_td_1024x1024_S16 (channel x4, 32 cells wide), 100 steps of dt = 1e-3",
+           "updates_per_sweep": upd}
+    ws = None
+
+    def run(name, scheme, prec, tol, profile=False):
+        nonlocal ws
+        opt = gsis.default_options(scheme=scheme, precision=prec, tol=tol, max_iter=2000, check_every=4,
+                                   synth_rtol=1e-12, synth_max_iter=SYNTH_CAP)
+        gsis.profile_enable(profile)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = gsis.td_solve(p.dx, p.dy, p.mu, p.eta, p.w, sa, ss, q, rho0, T0, tpd["dt"], tpd["nsteps"],
+                          c=tpd["c"], a=tpd["a"], cv=tpd["cv"], inflow=inflow, options=opt, workspace=ws)
+        e1.record(stream)
+        e1.synchronize()
+        ws = r["workspace"]
+        s = e0.elapsed_time(e1) * 1e-3
+        its = r["step_iters"]
+        res = {"s": s, "status": r["status"], "tol": tol, "iters_total": int(its.sum()),
+               "iters_per_step_mean": float(its.mean()), "iters_per_step_max": int(its.max()),
+               "updates_per_s": float(its.sum()) * upd / s,
+               "T_max": float(r["T"].max()), "rho_max": float(r["rho"].max())}
+        if profile:
+            prof = gsis.profile_read()
+            res["kernel_ms"] = {k: v["total_ms"] for k, v in prof.items()}
+            sw = prof["sweep"]
+            res["sweep_ms_avg"] = sw["total_ms"] / max(1, sw["timed"])
+        gsis.profile_enable(False)
+        out[name] = res
+        return res
+
+    run("gsis_fp32", gsis.SCHEME_GSIS, gsis.FP32_SWEEP, 1e-6)
+    prof = run("gsis_fp32_instrumented", gsis.SCHEME_GSIS, gsis.FP32_SWEEP, 1e-6, profile=True)
+    run("si_fp32", gsis.SCHEME_SI, gsis.FP32_SWEEP, 1e-6)
+    ws = None   # the FP64 layout is larger
+    run("gsis_fp64", gsis.SCHEME_GSIS, gsis.FP64, 1e-8)
+    # roofline of the time-step sweep (FP32 delta form): read I^n and write I
+    # (4 + 4 B per update) plus src, sigma_t, shift (FP32) once per cell
+    algo = 8.0 * upd + 12.0 * p.N
+    ach = algo / (prof["sweep_ms_avg"] * 1e-3) / 1e9
+    out["sweep_roofline"] = {"bound": "hbm", "kernel": "sweep (fp32, time step)", "achieved": ach, "peak": hbm,
+                             "unit": "GB/s", "frac": ach / hbm, "traffic": None, "algorithmic_bytes": algo,
+                             "avg_launch_ms": prof["sweep_ms_avg"]}
+    return out
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -257,6 +320,10 @@ def run_ours(args):
     if args.batch_only:   # the batched-solve measurement alone (profiling runs)
         print(json.dumps({"batch": batch_measure(gsis, torch, torch.cuda.current_stream(),
                                                  _peaks().get("hbm_gbs", 6800.0))}))
+        return 0
+    if args.timedep_only:   # the time-dependent measurement alone (profiling runs)
+        print(json.dumps({"timedep": timedep_measure(gsis, torch, torch.cuda.current_stream(),
+                                                     _peaks().get("hbm_gbs", 6800.0))}))
         return 0
     p, cfg = _workload(args)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
@@ -362,6 +429,11 @@ def run_ours(args):
     if not args.no_adjoint:
         adj = adjoint_measure(gsis, torch, stream)
 
+    # ---- time-dependent radiation-material workload (1024^2 S16, 100 steps), once
+    timedep = None
+    if not args.no_timedep:
+        timedep = timedep_measure(gsis, torch, stream, _peaks().get("hbm_gbs", 6800.0))
+
     # ---- batched solve of 64 independent problems (autotuned), once
     batch = None
     if not args.no_batch:
@@ -425,6 +497,7 @@ def run_ours(args):
             "kernel_ms": {k: v["total_ms"] for k, v in prof.items()},
             "adjoint": adj,
             "batch": batch,
+            "timedep": timedep,
             "clocks": clocks}
     print(json.dumps(line))
     if dist:
@@ -444,6 +517,8 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-gradient measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve measurement")
     ap.add_argument("--batch-only", action="store_true", help="run only the batched-solve measurement")
+    ap.add_argument("--no-timedep", action="store_true", help="skip the time-dependent measurement")
+    ap.add_argument("--timedep-only", action="store_true", help="run only the time-dependent measurement")
     ap.add_argument("--synth-cap", type=int, default=SYNTH_CAP,
                     help="inner iterations of the synthetic solve per GSIS iteration (0: solve to 1e-12)")
     args = ap.parse_args()

@@ -52,35 +52,35 @@ struct Profiler {
 };
 Profiler g_prof;
 
-struct ProfScope {
-    int cls, nk;
-    cudaStream_t st;
-    cudaEvent_t a = nullptr, b = nullptr;
-    ProfScope(int c, int n, cudaStream_t s) : cls(c), nk(n), st(s)
-    {
-        std::lock_guard<std::mutex> g(g_prof.mu);
-        g_prof.st[cls].kernels += nk;
-        g_prof.st[cls].groups += 1;
-        if (!g_prof.on) return;
-        if (g_prof.pool.empty()) {
-            cudaEvent_t x, y;
-            if (cudaEventCreate(&x) != cudaSuccess) return;
-            if (cudaEventCreate(&y) != cudaSuccess) { cudaEventDestroy(x); return; }
-            g_prof.pool.push_back({x, y});
-        }
-        a = g_prof.pool.back().first;
-        b = g_prof.pool.back().second;
-        g_prof.pool.pop_back();
-        cudaEventRecord(a, st);
+}  // namespace
+
+ProfScope::ProfScope(int c, int n, cudaStream_t s) : cls(c), nk(n), st(s)
+{
+    std::lock_guard<std::mutex> g(g_prof.mu);
+    g_prof.st[cls].kernels += nk;
+    g_prof.st[cls].groups += 1;
+    if (!g_prof.on) return;
+    if (g_prof.pool.empty()) {
+        cudaEvent_t x, y;
+        if (cudaEventCreate(&x) != cudaSuccess) return;
+        if (cudaEventCreate(&y) != cudaSuccess) { cudaEventDestroy(x); return; }
+        g_prof.pool.push_back({x, y});
     }
-    ~ProfScope()
-    {
-        if (!a) return;
-        cudaEventRecord(b, st);
-        std::lock_guard<std::mutex> g(g_prof.mu);
-        g_prof.pending.push_back({cls, a, b});
-    }
-};
+    a = g_prof.pool.back().first;
+    b = g_prof.pool.back().second;
+    g_prof.pool.pop_back();
+    cudaEventRecord(a, st);
+}
+
+ProfScope::~ProfScope()
+{
+    if (!a) return;
+    cudaEventRecord(b, st);
+    std::lock_guard<std::mutex> g(g_prof.mu);
+    g_prof.pending.push_back({cls, a, b});
+}
+
+namespace {
 
 // After a stream synchronisation: accumulate the finished event pairs.
 void prof_harvest()
@@ -98,11 +98,6 @@ void prof_harvest()
     cudaGetLastError();   // an unfinished pair reports "not ready": not an error of the caller
 }
 
-#define TIMED(cls, nk, expr)                        \
-    do {                                            \
-        ProfScope ps_((cls), (nk), st);             \
-        CK(expr);                                   \
-    } while (0)
 
 }  // namespace
 

@@ -25,6 +25,22 @@ int fail(int code, const char* fmt, ...);
             return fail(GSIS_ERR_CUDA, "%s failed: %s", #expr, cudaGetErrorString(e_));          \
     } while (0)
 
+// Instrumentation: counts the kernels of one class launch and, when
+// profiling is on, brackets it with CUDA events on st (gsis_profile_*).
+struct ProfScope {
+    int cls, nk;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ProfScope(int c, int n, cudaStream_t s);
+    ~ProfScope();
+};
+
+#define TIMED(cls, nk, expr)                        \
+    do {                                            \
+        ProfScope ps_((cls), (nk), st);             \
+        CK(expr);                                   \
+    } while (0)
+
 struct Sizes {
     int nx, ny, K, fp32, hist, adjoint, td;
 };

@@ -197,6 +197,19 @@ __global__ void td_end_si_kernel(TdArgs a)
     }
 }
 
+cudaError_t launch_td_coef_hot_rhs(const Plan& P, const TdArgs& a, int g, cudaStream_t st)
+{
+    td_coef_kernel<<<g, kRedBlock, 0, st>>>(a);
+    const cudaError_t e = cudaGetLastError();
+    return e != cudaSuccess ? e : launch_hot_rhs(P, P.rho_h, P.Fx, P.Fy, P.fb, P.rho_m, st);
+}
+
+cudaError_t launch_td_update(const Plan& P, const TdArgs& a, cudaStream_t st)
+{
+    td_update_kernel<<<P.red_grid, kRedBlock, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
 TdArgs td_args(const Plan& P, const gsis_time_params* tp, int gsis)
 {
     TdArgs a{};
@@ -305,16 +318,14 @@ int gsis_td_solve(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis
         while (launched < nmax) {
             const int batch = std::min(opt->check_every, nmax - launched);
             for (int b = 0; b < batch; ++b) {
-                CK(launch_sweep(P, st));
-                CK(launch_moments_to(P, gsis, false, P.rho_h, nullptr, nullptr, false, P.fb, false, st));
+                TIMED(GSIS_KCLASS_SWEEP, 1, launch_sweep(P, st));
+                TIMED(GSIS_KCLASS_MOMENTS, 2,
+                      launch_moments_to(P, gsis, false, P.rho_h, nullptr, nullptr, false, P.fb, false, st));
                 if (gsis) {
-                    td_coef_kernel<<<g, kRedBlock, 0, st>>>(a);
-                    CK(cudaGetLastError());
-                    CK(launch_hot_rhs(P, P.rho_h, P.Fx, P.Fy, P.fb, P.rho_m, st));
-                    CK(launch_synthetic_solve(P, P.rho_m, P.x, st));
+                    TIMED(GSIS_KCLASS_HOT_RHS, 3, launch_td_coef_hot_rhs(P, a, g, st));
+                    TIMED(GSIS_KCLASS_SYNTH, 1, launch_synthetic_solve(P, P.rho_m, P.x, st));
                 }
-                td_update_kernel<<<P.red_grid, kRedBlock, 0, st>>>(a);
-                CK(cudaGetLastError());
+                TIMED(GSIS_KCLASS_UPDATE, 1, launch_td_update(P, a, st));
             }
             launched += batch;
             if ((rc = read_status(S, P, st))) return rc;
