@@ -13,6 +13,10 @@ The time-dependent radiation-material steps (oracle/timedep.py) are pinned
 by tests/test_oracle_timedep.py: brute-force solves of the fully implicit
 and the Fleck-Cummings systems on tiny meshes, equilibrium preservation,
 energy conservation and the long-step radiative-equilibrium limit.
+The UW2 kinetic step (oracle/uw2.py) is pinned by tests/test_oracle_uw2.py:
+exactness on linear fields, the Barth-Jespersen bound, the zero-limiter
+reduction to the UW1 oracle, conservation, second-order convergence on a
+manufactured solution and convergence in the diffusion limit.
 """
 from .gsis import (  # noqa: F401
     angular_source, transport_sweep, alsm_gradient, high_order_terms, geometry, pseudo_time_shift,

@@ -208,3 +208,51 @@ int oracle_sweep_transposed(int nx, int ny, const double* dx, const double* dy, 
     }
     return 0;
 }
+
+/*
+ * Increment system of the delta form (Sec. 4.1, Eqs. (RTE_d_increment),
+ * (delta_Iij), (RTE_d_mtx), (elem_mtx); Sec. 4.3, Eq. (elem_main_shifted)):
+ * for every ordinate k,
+ *   d_ii dI_i + sum_{faces f of i with Omega.n < 0, neighbour j} d_ij dI_j = R_i,
+ *   d_ii = shift_i + sigma_t,i + sum_{Omega.n >= 0} (Omega.n A_f)/V_i,
+ *   d_ij = (Omega.n_f A_f)/V_i,
+ * first-order upwind increments with dI = 0 on inflow faces (the inflow is
+ * fixed), solved by visiting the cells in upwind order.  R and dI are [K][N]
+ * (R per unit volume); shift may be NULL.
+ */
+int oracle_sweep_delta(int nx, int ny, const double* dx, const double* dy, int K,
+                       const double* mu, const double* eta, const double* sigma_t,
+                       const double* shift, const double* R, double* dI)
+{
+    const int N = nx * ny;
+    for (int k = 0; k < K; ++k) {
+        const double m = mu[k], e = eta[k];
+        const double* Rk = R + (size_t)k * N;
+        double* dk = dI + (size_t)k * N;
+        const int i0 = (m >= 0.0) ? 0 : nx - 1, di = (m >= 0.0) ? 1 : -1;
+        const int j0 = (e >= 0.0) ? 0 : ny - 1, dj = (e >= 0.0) ? 1 : -1;
+        for (int jj = 0; jj < ny; ++jj) {
+            const int j = j0 + dj * jj;
+            for (int ii = 0; ii < nx; ++ii) {
+                const int i = i0 + di * ii;
+                const int c = i + nx * j;
+                const double V = dx[i] * dy[j];
+                const double An[4] = {dy[j], dy[j], dx[i], dx[i]};   /* W E S N */
+                const double on[4] = {-m, m, -e, e};                 /* Omega . n */
+                double dii = sigma_t[c] + (shift ? shift[c] : 0.0);
+                double lower = 0.0;
+                for (int f = 0; f < 4; ++f) {
+                    const double oa = on[f] * An[f];
+                    if (on[f] >= 0.0) {
+                        dii += oa / V;
+                    } else {
+                        const int nb = neighbour(nx, ny, i, j, f);
+                        if (nb >= 0) lower += oa / V * dk[nb];
+                    }
+                }
+                dk[c] = (Rk[c] - lower) / dii;
+            }
+        }
+    }
+    return 0;
+}
