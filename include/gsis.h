@@ -92,6 +92,12 @@ typedef struct {
     int check_every;       /* iterations between host reads of the device status; default 16 */
     int stall_window;      /* GSIS_ERR_STALLED after this many checks without a new minimum of Err; 0 = off */
     double wait_limit_s;   /* bound of every device-side wait, seconds; default 2.0 */
+    int spatial_order;     /* face values of the kinetic step: 1 = first-order upwind (default),
+                              2 = second-order upwind (Eqs. (Ii,k), (Iij)) solved in the delta
+                              form of Eqs. (RTE_d_increment), (RTE_d_res), (RTE_d_mtx): UW2
+                              residual, first-order upwind increment sweep; gsis_solve only */
+    int limiter;           /* spatial_order 2: 0 = Barth-Jespersen (the paper's, default),
+                              1 = none (unlimited reconstruction) */
 } gsis_options;
 
 /* Fills *opt with the defaults listed above (scheme GSIS, precision FP64). */

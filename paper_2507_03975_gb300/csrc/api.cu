@@ -191,6 +191,16 @@ size_t layout(const Sizes& z, char* base, Plan* P)
         p.adj_inflow = reinterpret_cast<double*>(take(nbf * K * sizeof(double)));
         p.refl = reinterpret_cast<int*>(take(K * sizeof(int)));
     }
+    if (z.order == 2) {
+        p.R = take(K * N * Ts);
+        p.corr = reinterpret_cast<double*>(take(N * sizeof(double)));
+        p.gw = reinterpret_cast<double*>(take(4 * N * sizeof(double)));
+        if (z.fp32) {
+            p.corr_f = reinterpret_cast<float*>(take(N * sizeof(float)));
+            p.gw_f = reinterpret_cast<float*>(take(4 * N * sizeof(float)));
+            p.sigt_d = reinterpret_cast<float*>(take(N * sizeof(float)));
+        }
+    }
     if (z.td) {
         p.In = take(K * N * Ts);
         double** td[] = {&p.td.rho_n, &p.td.T_n, &p.td.T, &p.td.cn, &p.td.cnext, &p.td.qeff, &p.td.diag0};
@@ -242,6 +252,8 @@ int check_opt(const gsis_options* o)
     if (!(o->synth_rtol >= 0.0) || o->synth_max_iter < 0) return fail(GSIS_ERR_ARG, "bad synthetic controls");
     if (o->check_every < 1) return fail(GSIS_ERR_ARG, "check_every must be >= 1");
     if (!(o->wait_limit_s > 0.0) || o->wait_limit_s > 3600.0) return fail(GSIS_ERR_ARG, "wait_limit_s out of range");
+    if (o->spatial_order != 1 && o->spatial_order != 2) return fail(GSIS_ERR_ARG, "spatial_order must be 1 or 2");
+    if (o->limiter != 0 && o->limiter != 1) return fail(GSIS_ERR_ARG, "limiter must be 0 or 1");
     if (!std::isfinite(o->cfl_p) || !std::isfinite(o->beta)) return fail(GSIS_ERR_ARG, "bad pseudo-time controls");
     return GSIS_OK;
 }
@@ -272,6 +284,8 @@ int prepare(Plan& P, const gsis_mesh* mesh, const gsis_quadrature* quad, const g
     P.fixed_iters = opt->fixed_iters;
     P.synth_rtol = opt->synth_rtol;
     P.synth_max_iter = opt->synth_max_iter;
+    P.order = opt->spatial_order;
+    P.limiter = opt->limiter;
     P.sigma_a = sa;
     P.sigma_s = ss;
     P.q = q;
@@ -356,6 +370,7 @@ Sizes sizes_of(const gsis_mesh* m, const gsis_quadrature* q, const gsis_options*
     z.K = q ? q->K : 0;
     z.fp32 = o->precision == GSIS_FP32_SWEEP;
     z.hist = std::max(o->max_iter, o->fixed_iters);
+    z.order = o->spatial_order;
     return z;
 }
 
@@ -368,6 +383,12 @@ void gsis::set_last_error(int code, const char* msg)
 }
 
 namespace {
+
+cudaError_t launch_uw2_kinetic(Plan& P, cudaStream_t st)
+{
+    const cudaError_t e = launch_uw2_residual(P, st);
+    return e != cudaSuccess ? e : launch_delta_sweep(P, st);
+}
 
 bool uniform_spacing(const double* h, int n)
 {
@@ -425,6 +446,8 @@ void gsis_default_options(gsis_options* o)
     o->check_every = 16;
     o->stall_window = 0;
     o->wait_limit_s = 2.0;
+    o->spatial_order = 1;
+    o->limiter = 0;
 }
 
 const char* gsis_status_string(int s)
@@ -507,7 +530,11 @@ int gsis_solve(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis_op
     while (launched < nmax) {
         const int batch = std::min(opt->check_every, nmax - launched);
         for (int b = 0; b < batch; ++b) {
-            TIMED(GSIS_KCLASS_SWEEP, 1, launch_sweep(P, st));
+            if (P.order == 2) {   // UW2 residual, then the first-order increment sweep
+                TIMED(GSIS_KCLASS_SWEEP, 2, launch_uw2_kinetic(P, st));
+            } else {
+                TIMED(GSIS_KCLASS_SWEEP, 1, launch_sweep(P, st));
+            }
             TIMED(GSIS_KCLASS_MOMENTS, 2,
                   launch_moments_to(P, gsis, false, P.rho_h, nullptr, nullptr, false, P.fb, false, st));
             if (gsis) {
@@ -561,6 +588,7 @@ int gsis_transport_sweep(const gsis_mesh* mesh, const gsis_quadrature* quad, con
     gsis_options o = *opt;
     o.cfl_p = 0.0;
     o.beta = 0.0;
+    o.spatial_order = 1;
     const Sizes z = sizes_of(mesh, quad, &o);
     if ((rc = check_ws(workspace, workspace_bytes, layout(z, nullptr, nullptr)))) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -588,6 +616,7 @@ int gsis_synthetic_step(const gsis_mesh* mesh, const gsis_options* opt, const do
     gsis_options o = *opt;
     o.cfl_p = 0.0;
     o.beta = 0.0;
+    o.spatial_order = 1;
     const Sizes z = sizes_of(mesh, nullptr, &o);
     if ((rc = check_ws(workspace, workspace_bytes, layout(z, nullptr, nullptr)))) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -632,6 +661,7 @@ int gsis_adjoint(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis_
     if (!sigma_a || !sigma_s || !q || !rho_star || !dJ_drho || !grad_sigma_a || !grad_sigma_s)
         return fail(GSIS_ERR_ARG, "a required device pointer is NULL");
     if (opt->scheme != GSIS_SCHEME_GSIS) return fail(GSIS_ERR_ARG, "the adjoint is that of the GSIS solution");
+    if (opt->spatial_order != 1) return fail(GSIS_ERR_ARG, "the adjoint covers first-order upwind face values");
     if (opt->cfl_p > 0.0 || opt->beta > 0.0)
         return fail(GSIS_ERR_ARG, "the adjoint is that of the steady GSIS map without pseudo-time");
     if (!uniform_spacing(mesh->dx, mesh->nx) || !uniform_spacing(mesh->dy, mesh->ny))

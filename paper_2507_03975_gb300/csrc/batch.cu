@@ -102,6 +102,7 @@ int check_problems(const gsis_problem* probs, int n, const gsis_options* opt, bo
 {
     int rc;
     if ((rc = check_opt(opt))) return rc;
+    if (opt->spatial_order != 1) return fail(GSIS_ERR_ARG, "the batched solve runs first-order upwind face values");
     if (!probs) return fail(GSIS_ERR_ARG, "probs is NULL");
     if (n < 1 || n > kMaxBatch) return fail(GSIS_ERR_ARG, "batch of %d problems out of range [1, %d]", n, kMaxBatch);
     for (int p = 0; p < n; ++p) {

@@ -75,6 +75,8 @@ struct Plan {
     int cg_grid;                    // cooperative synthetic CTAs
     int red_grid;                   // per-cell kernels' CTAs (Err reduction partial count)
     double shift0;                  // 1/(c dt) added to the kinetic diagonal (time step; 0 when steady)
+    int order;                      // kinetic face values: 1 first-order upwind, 2 second-order (delta form)
+    int limiter;                    // order 2: 0 Barth-Jespersen, 1 none
     int synth_cl;                   // synthetic solver: strip-solver cluster size, 0 = global-memory solver
     size_t synth_bytes;             // its dynamic shared memory
 
@@ -107,6 +109,11 @@ struct Plan {
     double* hotx; double* hoty; double* b;
     double* x; double* r; double* z; double* p; double* qv;
     const double* q_syn;            // volume source of the synthetic equation if not q (time step)
+    // second-order upwind (order 2): residual, isotropic correction of the stored I, gradient weights
+    void* R;                        // [K][N] T, residual per unit volume of the UW2 equations
+    double* corr; float* corr_f;    // I^m = I + corr (per cell; FP32 copy for the FP32 sweep)
+    double* gw; float* gw_f;        // [4][N] least-squares weights of I: E, W, N, S
+    float* sigt_d;                  // FP32 sweep: sigma_t + pseudo-time shift (increment diagonal)
     double* partials;               // reductions scratch
     double* hist;                   // [max_iter]
     Status* status;
@@ -152,6 +159,10 @@ cudaError_t plan_synthetic(Plan& P);   // before the first solve launch (no runt
 cudaError_t launch_synthetic_solve(const Plan& P, const double* guess, double* out, cudaStream_t st);
 int mg_cluster_size();
 cudaError_t launch_update(const Plan& P, const double* rho_new, cudaStream_t st);
+// second-order upwind (csrc/uw2.cu, sweep in csrc/sweep.cu)
+cudaError_t launch_uw2_residual(const Plan& P, cudaStream_t st);     // R from I + corr and the source
+cudaError_t launch_delta_sweep(Plan& P, cudaStream_t st);           // I <- I + corr + dI
+cudaError_t launch_uw2_bflux(const Plan& P, double* fb_out, const int* done, cudaStream_t st);
 // adjoint (csrc/adjoint.cu, sweep in csrc/sweep.cu)
 cudaError_t launch_adjoint_sweep(Plan& P, cudaStream_t st);
 cudaError_t launch_synth_resid(const Plan& P, const double* b, const double* guess, cudaStream_t st);

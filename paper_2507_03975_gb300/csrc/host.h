@@ -42,7 +42,7 @@ struct ProfScope {
     } while (0)
 
 struct Sizes {
-    int nx, ny, K, fp32, hist, adjoint, td;
+    int nx, ny, K, fp32, hist, adjoint, td, order;
 };
 
 // Carves one problem's workspace (base may be null: size query only).

@@ -71,7 +71,8 @@ __global__ void cell_setup_kernel(int nx, int ny, const double* __restrict__ dx,
                                   const double* __restrict__ inflow, int n_inflow,
                                   double shift0, double cfl_p, double beta, double* sigt, float* sigt_f,
                                   double* shift, float* shift_f, double* diag, double* cx,
-                                  double* cy, double* hw, double* bface, int* err)
+                                  double* cy, double* hw, double* bface, double* gw, float* gw_f,
+                                  float* sigt_d, int* err)
 {
     const int N = nx * ny;
     if (inflow)
@@ -114,6 +115,7 @@ __global__ void cell_setup_kernel(int nx, int ny, const double* __restrict__ dx,
         if (beta > 0.0) sh += th / (beta * ref);
         shift[c] = sh;
         if (shift_f) shift_f[c] = (float)sh;
+        if (sigt_d) sigt_d[c] = (float)(st + sh);
         // D = V sigma_a + sum_int A Gamma + sum_bnd A beta
         double d = hx * hy * a + hy * (gE + gW) + hx * (gN + gS);
         const double bx = 2.0 / (3.0 * st * hx) + 0.25, by = 2.0 / (3.0 * st * hy) + 0.25;
@@ -141,6 +143,14 @@ __global__ void cell_setup_kernel(int nx, int ny, const double* __restrict__ dx,
             hw[N + c] = dW * fx;
             hw[2 * N + c] = dN * fy;
             hw[3 * N + c] = dS * fy;
+            if (gw) {   // the same least-squares gradient for the intensities (no 1/(3 sigma_t))
+                const double gx = sx > 0.0 ? 1.0 / sx : 0.0, gy = sy > 0.0 ? 1.0 / sy : 0.0;
+                const double g4[4] = {dE * gx, dW * gx, dN * gy, dS * gy};
+                for (int t = 0; t < 4; ++t) {
+                    gw[(size_t)t * N + c] = g4[t];
+                    if (gw_f) gw_f[(size_t)t * N + c] = (float)g4[t];
+                }
+            }
         }
         // boundary faces: area * beta (Eq. (macro_bc_delta_flux)), faces W, E, S, N
         if (i == 0) bface[j] = hy * bx;
@@ -208,7 +218,10 @@ __global__ void source_kernel(int N, const double* __restrict__ ss, const double
 // Source of the sweep: isotropic (plain), isotropic plus the pseudo-time
 // term shift * I^m (delta form), or the adjoint source
 // w_s (a - mu_s bx - eta_s by) of the transposed kinetic step.
-constexpr int kSrcPlain = 0, kSrcPseudoTime = 1, kSrcAdjoint = 2;
+// kSrcDelta: the increment sweep of the second-order upwind delta form
+// (Eqs. (RTE_d_increment), (delta_Iij), (RTE_d_mtx)): source = the residual
+// R[s][cell], zero increment on inflow faces, stored result I + corr + dI.
+constexpr int kSrcPlain = 0, kSrcPseudoTime = 1, kSrcAdjoint = 2, kSrcDelta = 3;
 
 template <typename T>
 struct SweepArgs {
@@ -358,7 +371,7 @@ template <typename T, int MODE, bool PRE, bool BATCH>
 __global__ void __launch_bounds__(kSweepPairs * 64, 1)
 sweep_kernel(const SweepArgs<T> a1, const SweepBatch<T> bt)
 {
-    constexpr bool PT = MODE == kSrcPseudoTime, ADJ = MODE == kSrcAdjoint;
+    constexpr bool PT = MODE == kSrcPseudoTime, ADJ = MODE == kSrcAdjoint, DELTA = MODE == kSrcDelta;
     using SM = SweepSmem<T, MODE != kSrcPlain, PRE>;
     using B = Bits<T>;
     constexpr int SEG = SM::SEG, NBUF = SM::NBUF, RS = SM::RS, NW = SM::NW;
@@ -507,6 +520,11 @@ sweep_kernel(const SweepArgs<T> a1, const SweepBatch<T> bt)
             if (ADJ) {
                 wsrc[SM::W_SHIFT] = a.ax;
                 wsrc[SM::W_IOLD] = a.ay;
+            }
+            if (DELTA) {   // residual and stored intensity of this ordinate, correction per cell
+                wsrc[SM::W_SRC] = a.src + (size_t)s * a.N;
+                wsrc[SM::W_SHIFT] = a.shift;
+                wsrc[SM::W_IOLD] = a.iold + (size_t)s * a.N;
             }
             const T* arow = a.acoef + (size_t)s * nx;
             const double* rrow = PRE ? a.rsw + ((size_t)s * nb + band) * (size_t)a.nsteps * 32 : nullptr;
@@ -668,7 +686,10 @@ sweep_kernel(const SweepArgs<T> a1, const SweepBatch<T> bt)
                         const T Inew = acc * rinv;
                         IW = Inew;
                         Iprev = Inew;
-                        B::put(Ic + tt * dc, Inew);
+                        if (DELTA)
+                            B::put(Ic + tt * dc, (wb[SM::W_IOLD * SM::WIN + tt] + wb[SM::W_SHIFT * SM::WIN + tt]) + Inew);
+                        else
+                            B::put(Ic + tt * dc, Inew);
                         if (put_edge) B::store(ec + tt, Inew);
                     }
                 } else {
@@ -701,7 +722,11 @@ sweep_kernel(const SweepArgs<T> a1, const SweepBatch<T> bt)
                             acc = fma(bj, Isouth, acc);
                             Inew = acc * rinv;
                             IW = Inew;
-                            B::put(Is + base0 + lane * dr + c * dc, Inew);
+                            if (DELTA)
+                                B::put(Is + base0 + lane * dr + c * dc,
+                                       (wb[SM::W_IOLD * SM::WIN + tt] + wb[SM::W_SHIFT * SM::WIN + tt]) + Inew);
+                            else
+                                B::put(Is + base0 + lane * dr + c * dc, Inew);
                             if (put_edge) B::store(eo + c, Inew);
                         }
                         Iprev = Inew;
@@ -910,6 +935,15 @@ SweepArgs<T> sweep_args(const Plan& P)
         a.I = static_cast<T*>(P.Iadj);
         a.inflow = P.adj_inflow;
     }
+    if (MODE == kSrcDelta) {   // increment sweep: residual source, zero inflow increment, correction
+        a.src = static_cast<const T*>(P.R);
+        if constexpr (sizeof(T) == 8) a.shift = P.corr;
+        else {
+            a.shift = P.corr_f;
+            a.sigt = P.sigt_d;
+        }
+        a.inflow = nullptr;
+    }
     a.qw = P.qw;
     a.perm = P.perm; a.qmu = P.qmu; a.qeta = P.qeta;
     a.err = &P.status->error;
@@ -996,6 +1030,7 @@ cudaError_t launch_moments_t(const Plan& P, bool with_F, bool with_P, double* rh
     else moments_kernel<T, false, false><<<grid, kRedBlock, smem, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (P.order == 2) return launch_uw2_bflux(P, fb_out, a.done, st);   // reconstructed outgoing faces
     bflux_kernel<T><<<grid_for((long long)P.nbf * 32, 256, P.num_sms * 4), 256, 0, st>>>(
         bflux_args<T>(P, fb_out, a.done));
     return cudaGetLastError();
@@ -1038,6 +1073,7 @@ cudaError_t prepare_t(int K)
         if ((e = sweep_attr<T, kSrcPlain, false>()) != cudaSuccess ||
             (e = sweep_attr<T, kSrcPseudoTime, false>()) != cudaSuccess ||
             (e = sweep_attr<T, kSrcAdjoint, false>()) != cudaSuccess ||
+            (e = sweep_attr<T, kSrcDelta, false>()) != cudaSuccess ||
             (e = sweep_attr<T, kSrcPlain, true>()) != cudaSuccess ||
             (e = sweep_attr<T, kSrcPseudoTime, true>()) != cudaSuccess)
             first = e;
@@ -1088,7 +1124,7 @@ cudaError_t launch_cell_setup(const Plan& P, double cfl_p, double beta, cudaStre
     cell_setup_kernel<<<grid_for(P.N, 256, P.num_sms * 8), 256, 0, st>>>(
         P.nx, P.ny, P.dx, P.dy, P.sigma_a, P.sigma_s, P.q, P.inflow, P.nbf * P.K, P.shift0, cfl_p, beta, P.sigt,
         P.fp32 ? P.sigt_f : nullptr, P.shift, P.fp32 ? P.shift_f : nullptr, P.diag, P.cx, P.cy, P.hw,
-        P.bface, &P.status->error);
+        P.bface, P.gw, P.gw_f, P.sigt_d, &P.status->error);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (!P.fp32) {
@@ -1108,7 +1144,13 @@ cudaError_t launch_init_state(const Plan& P, cudaStream_t st)
     fill_kernel<<<g, 256, 0, st>>>(P.rho_h, P.N, 0.0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (P.pt) {   // I^0 = 0 (the delta form reads it)
+    if (P.order == 2) {   // no correction of the initial intensities
+        fill_kernel<<<g, 256, 0, st>>>(P.corr, P.N, 0.0);
+        if (P.fp32) fillf_kernel<<<g, 256, 0, st>>>(P.corr_f, P.N, 0.f);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (P.pt || P.order == 2) {   // I^0 = 0 (the delta form reads it)
         const size_t n = (size_t)P.K * P.N;
         if (P.fp32) fillf_kernel<<<grid_for((long long)n, 256, P.num_sms * 16), 256, 0, st>>>(static_cast<float*>(P.I), n, 0.f);
         else fill_kernel<<<grid_for((long long)n, 256, P.num_sms * 16), 256, 0, st>>>(static_cast<double*>(P.I), n, 0.0);
@@ -1132,6 +1174,11 @@ cudaError_t launch_sweep(Plan& P, cudaStream_t st)
                     : launch_sweep_t<float, kSrcPlain, false>(P, st);
     }
     return P.pt ? launch_sweep_t<double, kSrcPseudoTime, true>(P, st) : launch_sweep_t<double, kSrcPlain, true>(P, st);
+}
+
+cudaError_t launch_delta_sweep(Plan& P, cudaStream_t st)
+{
+    return P.fp32 ? launch_sweep_t<float, kSrcDelta, false>(P, st) : launch_sweep_t<double, kSrcDelta, true>(P, st);
 }
 
 cudaError_t launch_adjoint_sweep(Plan& P, cudaStream_t st)
@@ -1233,10 +1280,12 @@ int sweep_max_active_blocks(int fp32, int pt)
     (void)pt;
     if (fp32)
         return std::min({sweep_occupancy<float, kSrcPlain, false>(), sweep_occupancy<float, kSrcPseudoTime, false>(),
-                         sweep_occupancy<float, kSrcAdjoint, false>(), sweep_occupancy<float, kSrcPlain, true>(),
+                         sweep_occupancy<float, kSrcAdjoint, false>(), sweep_occupancy<float, kSrcDelta, false>(),
+                         sweep_occupancy<float, kSrcPlain, true>(),
                          sweep_occupancy<float, kSrcPseudoTime, true>()});
     return std::min({sweep_occupancy<double, kSrcPlain, false>(), sweep_occupancy<double, kSrcPseudoTime, false>(),
-                     sweep_occupancy<double, kSrcAdjoint, false>(), sweep_occupancy<double, kSrcPlain, true>(),
+                     sweep_occupancy<double, kSrcAdjoint, false>(), sweep_occupancy<double, kSrcDelta, false>(),
+                     sweep_occupancy<double, kSrcPlain, true>(),
                      sweep_occupancy<double, kSrcPseudoTime, true>()});
 }
 

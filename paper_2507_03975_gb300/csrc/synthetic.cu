@@ -146,6 +146,7 @@ struct UpdArgs {
     const double* sigma_s; const double* q; const double* shift;
     const double* rho_new; double* rho_m; const double* rho_h;
     double* src; float* src_f;
+    double* corr; float* corr_f;   // second-order delta form: isotropic correction of I (or null)
     int pt;
     double tol;
     int fixed_iters, max_iter;
@@ -178,6 +179,11 @@ __device__ __forceinline__ void update_body(const UpdArgs& a, int bid, int nblk)
         if (a.pt) s = fma(a.shift[c] * (nw - a.rho_h[c]), kInvFourPi, s);
         a.src[c] = s;
         if (a.src_f) a.src_f[c] = (float)s;
+        if (a.corr) {   // I^{m+1} = I^{m+1/2} + (rho^{m+1} - rho^{m+1/2})/4pi, kept per cell
+            const double cc = (nw - a.rho_h[c]) * kInvFourPi;
+            a.corr[c] = cc;
+            if (a.corr_f) a.corr_f[c] = (float)cc;
+        }
     }
     num = block_sum(num, sm);
     den = block_sum(den, sm);
@@ -226,7 +232,10 @@ UpdArgs upd_args(const Plan& P, const double* rho_new)
     a.sigma_s = P.sigma_s; a.q = P.q; a.shift = P.shift;
     a.rho_new = rho_new; a.rho_m = P.rho_m; a.rho_h = P.rho_h;
     a.src = P.src; a.src_f = P.fp32 ? P.src_f : nullptr;
-    a.pt = P.pt; a.tol = P.tol; a.fixed_iters = P.fixed_iters; a.max_iter = P.max_iter;
+    a.pt = P.pt && P.order == 1;   // second order: the correction is carried explicitly
+    a.corr = P.order == 2 ? P.corr : nullptr;
+    a.corr_f = P.order == 2 && P.fp32 ? P.corr_f : nullptr;
+    a.tol = P.tol; a.fixed_iters = P.fixed_iters; a.max_iter = P.max_iter;
     a.partials = P.partials + (size_t)9 * kMaxCgBlocks;
     a.hist = P.hist;
     a.status = P.status;

@@ -247,6 +247,7 @@ int check_tp(const gsis_time_params* tp, const gsis_options* opt)
     if (tp->nsteps < 1 || tp->nsteps > 100000000) return fail(GSIS_ERR_ARG, "nsteps out of range");
     if (opt->cfl_p > 0.0 || opt->beta > 0.0)
         return fail(GSIS_ERR_ARG, "the time-dependent solve takes no pseudo-time (cfl_p, beta <= 0)");
+    if (opt->spatial_order != 1) return fail(GSIS_ERR_ARG, "the time-dependent solve runs first-order upwind face values");
     return GSIS_OK;
 }
 

@@ -64,6 +64,7 @@ class Options(ctypes.Structure):
         ("max_iter", ctypes.c_int), ("fixed_iters", ctypes.c_int), ("synth_rtol", ctypes.c_double),
         ("synth_max_iter", ctypes.c_int), ("cfl_p", ctypes.c_double), ("beta", ctypes.c_double),
         ("check_every", ctypes.c_int), ("stall_window", ctypes.c_int), ("wait_limit_s", ctypes.c_double),
+        ("spatial_order", ctypes.c_int), ("limiter", ctypes.c_int),
     ]
 
 

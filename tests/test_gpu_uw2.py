@@ -1,0 +1,119 @@
+"""GPU second-order upwind (UW2) solve (gsis_solve with spatial_order = 2)
+against the FP64 oracle (oracle/uw2.py) on the same seeded inputs.
+
+Tolerances: FP64, fixed iterations or converged: 1e-10 relative (max norm)
+in rho, F and the second moment; FP32 sweeps (FP32 residual, increment
+sweep and moments; FP64 synthetic solve), converged: 1e-5 in rho."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import uw2 as U
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def gs():
+    import torch
+    from paper_2507_03975_gb300 import build, gsis
+    build.build()
+    gsis.load()
+    torch.cuda.set_device(0)
+    return gsis
+
+
+def _t(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def _solve(gs, p, **kw):
+    opt = gs.default_options(spatial_order=2, **kw)
+    return gs.solve(p.dx, p.dy, p.mu, p.eta, p.w, _t(p.sigma_a), _t(p.sigma_s), _t(p.q),
+                    None if p.inflow is None else _t(p.inflow.reshape(-1)), opt)
+
+
+CASES = [
+    ("random_30x22_S4", lambda: W.random_problem(30, 22, order=4, seed=61, ratio_range=(0.2, 0.9))),
+    ("random_41x35_S6_vacuum", lambda: W.random_problem(41, 35, order=6, seed=62, with_inflow=False)),
+    ("ragged_70x33_S4", lambda: W.random_problem(70, 33, order=4, seed=63)),
+    ("channel_64_S8", lambda: W.channel_problem(64, 8, 2, width=2, sigma_bulk=200.0)),
+]
+
+
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("scheme,limiter", [("gsis", "bj"), ("si", "bj"), ("gsis", "none")])
+def test_fixed_iterations_match_oracle(gs, name, make, scheme, limiter):
+    p = make()
+    m = 5
+    o = U.solve(p, scheme, fixed_iters=m, limiter=limiter)
+    r = _solve(gs, p, scheme=gs.SCHEME_GSIS if scheme == "gsis" else gs.SCHEME_SI, fixed_iters=m, max_iter=m,
+               synth_rtol=1e-14, synth_max_iter=3000, limiter=0 if limiter == "bj" else 1)
+    assert r["iters"] == m
+    assert rel(r["rho"].cpu().numpy(), o["rho"]) < TOL64
+    np.testing.assert_allclose(r["history"], o["history"], rtol=1e-7)
+    N = p.N
+    F, P = r["F"].cpu().numpy(), r["P"].cpu().numpy()
+    s = np.abs(o["rho"]).max()
+    assert np.abs(F[:N] - o["Fx"]).max() / s < TOL64
+    assert np.abs(F[N:] - o["Fy"]).max() / s < TOL64
+    assert np.abs(P[:N] - o["Pxx"]).max() / s < TOL64
+
+
+def test_converged_gsis_matches_oracle(gs):
+    p = W.random_problem(36, 28, order=6, seed=64, ratio_range=(0.3, 0.95))
+    o = U.solve(p, "gsis", tol=1e-11)
+    r = _solve(gs, p, tol=1e-11, synth_rtol=1e-14, synth_max_iter=3000)
+    assert r["status"] == gs.GSIS_OK
+    assert abs(r["iters"] - o["iters"]) <= 1
+    assert rel(r["rho"].cpu().numpy(), o["rho"]) < TOL64
+
+
+def test_pseudo_time_matches_oracle(gs):
+    p = W.channel_problem(64, 8, 2, width=2)   # 2000 / 0.2 jump
+    o = U.solve(p, "gsis", fixed_iters=6, beta=10.0)
+    r = _solve(gs, p, fixed_iters=6, max_iter=6, beta=10.0, synth_rtol=1e-14, synth_max_iter=3000)
+    assert rel(r["rho"].cpu().numpy(), o["rho"]) < TOL64
+
+
+def test_fp32_sweeps_converged(gs):
+    p = W.random_problem(40, 30, order=6, seed=65, ratio_range=(0.3, 0.9))
+    o = U.solve(p, "gsis", tol=1e-11)
+    r = _solve(gs, p, precision=gs.FP32_SWEEP, tol=1e-6, max_iter=400, stall_window=4, synth_rtol=1e-13,
+               synth_max_iter=3000)
+    assert r["status"] in (gs.GSIS_OK, gs.GSIS_ERR_STALLED)
+    assert rel(r["rho"].cpu().numpy(), o["rho"]) < TOL32
+
+
+def test_channel_full_size_parity(gs):
+    """The 256x256 S12 channel workload with UW2 and the benchmark's
+    pseudo-time (beta = 10): three GSIS iterations against the oracle."""
+    p = W.config_channel()
+    o = U.solve(p, "gsis", fixed_iters=3, beta=10.0)
+    r = _solve(gs, p, fixed_iters=3, max_iter=3, beta=10.0, synth_rtol=1e-14, synth_max_iter=3000)
+    assert rel(r["rho"].cpu().numpy(), o["rho"]) < TOL64
+
+
+def test_second_order_only_where_supported(gs):
+    p = W.random_problem(8, 8, order=4, seed=66)
+    opt = gs.default_options(spatial_order=2)
+    sa, ss, q = _t(p.sigma_a), _t(p.sigma_s), _t(p.q)
+    with pytest.raises(gs.GsisError) as e:
+        gs.adjoint(p.dx, p.dy, p.mu, p.eta, p.w, sa, ss, q, _t(np.ones(p.N)), _t(np.ones(p.N)), options=opt)
+    assert e.value.status == gs.GSIS_ERR_ARG
+    with pytest.raises(gs.GsisError) as e:
+        gs.td_solve(p.dx, p.dy, p.mu, p.eta, p.w, sa, ss, q, _t(np.ones(p.N)), _t(np.ones(p.N)), 0.1, 1,
+                    options=opt)
+    assert e.value.status == gs.GSIS_ERR_ARG
+    with pytest.raises(gs.GsisError) as e:
+        gs.solve(p.dx, p.dy, p.mu, p.eta, p.w, sa, ss, q, None, gs.default_options(spatial_order=3))
+    assert e.value.status == gs.GSIS_ERR_ARG
