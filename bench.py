@@ -260,6 +260,39 @@ def timedep_measure(gsis, torch, stream, hbm):
     return out
 
 
+def uw2_measure(gsis, torch, stream, p, sa, ss, q, inflow, flush):
+    """The channel workload with second-order upwind face values (the paper's
+    transport scheme): GSIS, FP64, beta = 10, Err < 1e-8, synthetic solve
+    capped at SYNTH_CAP inner iterations; Barth-Jespersen limiter and
+    unlimited reconstruction.  Device time with CUDA events (L2 flushed
+    before each solve), a second, instrumented solve for the class times."""
+    out = {"workload": "channel_256x256_S12_seed2, UW2", "tol": TOL}
+    for name, lim in (("barth_jespersen", 0), ("unlimited", 1)):
+        opt = gsis.default_options(scheme=gsis.SCHEME_GSIS, precision=gsis.FP64, tol=TOL, beta=BETA, max_iter=3000,
+                                   check_every=16, stall_window=8, synth_rtol=1e-12, synth_max_iter=SYNTH_CAP,
+                                   spatial_order=2, limiter=lim)
+        res = {}
+        for prof in (False, True):
+            gsis.profile_enable(prof)
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = gsis.solve(p.dx, p.dy, p.mu, p.eta, p.w, sa, ss, q, inflow, opt, want_P=False)
+            e1.record(stream)
+            e1.synchronize()
+            if not prof:
+                s = e0.elapsed_time(e1) * 1e-3
+                res = {"s": s, "iters": r["iters"], "status": r["status"], "err": r["err"],
+                       "updates_per_s": r["iters"] * p.N * p.K / s}
+            else:
+                pr = gsis.profile_read()
+                res["kernel_ms_per_iter"] = {k: v["total_ms"] / max(1, r["iters"]) for k, v in pr.items()
+                                             if k != "setup"}
+        gsis.profile_enable(False)
+        out[name] = res
+    return out
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -425,6 +458,11 @@ def run_ours(args):
         si = {"s": e0.elapsed_time(e1) * 1e-3, "iters": rs["iters"], "status": rs["status"],
               "updates_per_s": rs["iters"] * p.N * p.K / (e0.elapsed_time(e1) * 1e-3)}
 
+    # ---- the same workload with second-order upwind face values, once
+    uw2 = None
+    if not args.no_uw2:
+        uw2 = uw2_measure(gsis, torch, stream, p, sa, ss, q, inflow, flush)
+
     # ---- adjoint (gradient of a detector functional, 64x64 S8 workload), once
     adj = None
     if not args.no_adjoint:
@@ -499,6 +537,7 @@ def run_ours(args):
             "adjoint": adj,
             "batch": batch,
             "timedep": timedep,
+            "uw2": uw2,
             "clocks": clocks}
     print(json.dumps(line))
     if dist:
@@ -519,6 +558,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve measurement")
     ap.add_argument("--batch-only", action="store_true", help="run only the batched-solve measurement")
     ap.add_argument("--no-timedep", action="store_true", help="skip the time-dependent measurement")
+    ap.add_argument("--no-uw2", action="store_true", help="skip the second-order upwind measurement")
     ap.add_argument("--timedep-only", action="store_true", help="run only the time-dependent measurement")
     ap.add_argument("--synth-cap", type=int, default=SYNTH_CAP,
                     help="inner iterations of the synthetic solve per GSIS iteration (0: solve to 1e-12)")

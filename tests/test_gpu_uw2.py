@@ -70,11 +70,14 @@ def test_fixed_iterations_match_oracle(gs, name, make, scheme, limiter):
 
 
 def test_converged_gsis_matches_oracle(gs):
-    p = W.random_problem(36, 28, order=6, seed=64, ratio_range=(0.3, 0.95))
-    o = U.solve(p, "gsis", tol=1e-11)
-    r = _solve(gs, p, tol=1e-11, synth_rtol=1e-14, synth_max_iter=3000)
-    assert r["status"] == gs.GSIS_OK
-    assert abs(r["iters"] - o["iters"]) <= 1
+    """The 64x64 S8 workload to Err < 1e-8 with the unlimited reconstruction
+    (with the Barth-Jespersen limiter Err settles near 2e-7 there: the
+    limiter's switching makes a limit cycle, in the oracle as on the GPU)."""
+    p = W.config_small()
+    o = U.solve(p, "gsis", tol=1e-8, limiter="none")
+    r = _solve(gs, p, tol=1e-8, limiter=1, synth_rtol=1e-14, synth_max_iter=3000, check_every=1)
+    assert o["converged"] and r["status"] == gs.GSIS_OK
+    assert r["iters"] == o["iters"]
     assert rel(r["rho"].cpu().numpy(), o["rho"]) < TOL64
 
 
@@ -86,11 +89,11 @@ def test_pseudo_time_matches_oracle(gs):
 
 
 def test_fp32_sweeps_converged(gs):
-    p = W.random_problem(40, 30, order=6, seed=65, ratio_range=(0.3, 0.9))
-    o = U.solve(p, "gsis", tol=1e-11)
+    p = W.config_small()
+    o = U.solve(p, "gsis", tol=1e-11, limiter="none")
     r = _solve(gs, p, precision=gs.FP32_SWEEP, tol=1e-6, max_iter=400, stall_window=4, synth_rtol=1e-13,
-               synth_max_iter=3000)
-    assert r["status"] in (gs.GSIS_OK, gs.GSIS_ERR_STALLED)
+               synth_max_iter=3000, limiter=1)
+    assert o["converged"] and r["status"] in (gs.GSIS_OK, gs.GSIS_ERR_STALLED)
     assert rel(r["rho"].cpu().numpy(), o["rho"]) < TOL32
 
 
