@@ -150,6 +150,8 @@ size_t layout(const Sizes& z, char* base, Plan* P)
     p.hw = reinterpret_cast<double*>(take(4 * N * sizeof(double)));
     p.bface = reinterpret_cast<double*>(take(nbf * sizeof(double)));
     p.partials = reinterpret_cast<double*>(take(11 * (size_t)kMaxCgBlocks * sizeof(double)));
+    p.mg_gslots_d = reinterpret_cast<double*>(take(6 * (size_t)kMaxCgBlocks * sizeof(double)));
+    p.mg_gslots_f = reinterpret_cast<float*>(take(6 * (size_t)kMaxCgBlocks * sizeof(float)));
     // multigrid hierarchy: 2x2 aggregation down to a single cell
     {
         MgPlan& g = p.mg;

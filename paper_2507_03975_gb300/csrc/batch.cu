@@ -153,6 +153,8 @@ int batch_setup(Batch& b, const gsis_problem* probs, int n, const gsis_options* 
         b.P[p].status = b.statuses + p;   // all status blocks side by side: one read per check
         if ((rc = prepare(b.P[p], &q.mesh, &q.quad, opt, q.sigma_a, q.sigma_s, q.q, q.inflow, st)))
             return fail(rc, "problem %d: %s", p, gsis_last_error());
+        // synthetic solves run on concurrent branches: no grid-wide (every-SM) solver here
+        b.P[p].synth_grid = 0;
         CK(launch_init_state(b.P[p], st));
     }
     b.pt = b.P[0].pt;

@@ -45,6 +45,7 @@ struct Status {
     long long synth_iters_total;      // summed over the solve
     double err;                       // last Err(rho)
     double synth_relres;              // last synthetic relative residual
+    unsigned int mg_bar[2];           // grid-wide synthetic solver barrier: arrivals, generation
 };
 
 // Multigrid hierarchy of the synthetic operator (level 0 = the mesh).
@@ -78,6 +79,8 @@ struct Plan {
     int order;                      // kinetic face values: 1 first-order upwind, 2 second-order (delta form)
     int limiter;                    // order 2: 0 Barth-Jespersen, 1 none
     int synth_cl;                   // synthetic solver: strip-solver cluster size, 0 = global-memory solver
+    int synth_grid;                 // global-memory solver over a cooperative grid of this many CTAs (0: one cluster)
+    double* mg_gslots_d; float* mg_gslots_f;   // its reduction slots [3][2][kMaxCgBlocks]
     size_t synth_bytes;             // its dynamic shared memory
 
     // mesh

@@ -108,6 +108,10 @@ struct MgArgs {
     int max_iter, nu;
     float inner_rtol, omega, alpha;
     Status* status;
+    // grid-wide form: reduction slots [3][2][gridDim] and the barrier words
+    double* gslots_d; float* gslots_f;
+    unsigned* gbar;                 // [0] arrivals, [1] generation
+    long long wait_cycles;
 };
 
 // Work distribution of one level: the whole cluster, or CTA 0 alone.
@@ -237,6 +241,123 @@ class ClusterCtx {
     int rank_, nblk_;
 };
 
+// The same interface over a whole cooperative grid (one CTA per SM): the
+// fine levels spread over every SM.  The barrier is a counter and a
+// generation word in global memory; every wait is bounded, and after a
+// time-out (the status's timeout bit) later barriers return at once so that
+// every CTA finishes.  Sums: each CTA's partial in a rotating global table,
+// then every warp adds the table in a fixed order (same bits everywhere).
+class GridCtx {
+  public:
+    __device__ GridCtx(const MgArgs& a) : a_(a) {}
+    __device__ void sync()
+    {
+        __syncthreads();
+        if (threadIdx.x == 0 && !ld_volatile_int(&a_.status->error)) {
+            volatile unsigned* gen = a_.gbar + 1;
+            const unsigned g = *gen;
+            __threadfence();
+            if (atomicAdd(a_.gbar, 1u) == gridDim.x - 1) {
+                a_.gbar[0] = 0u;
+                __threadfence();
+                atomicAdd(a_.gbar + 1, 1u);
+            } else {
+                const long long t0 = clock64();
+                while (*gen == g) {
+                    if (clock64() - t0 > a_.wait_cycles) {
+                        atomicOr(&a_.status->error, kErrTimeout);
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+            }
+            __threadfence();
+        }
+        __syncthreads();
+    }
+    __device__ int rank() const { return blockIdx.x; }
+    __device__ Range range(bool local) const
+    {
+        if (local) return Range{(int)threadIdx.x, (int)blockDim.x, blockIdx.x == 0};
+        return Range{(int)(blockIdx.x * blockDim.x + threadIdx.x), (int)(gridDim.x * blockDim.x), true};
+    }
+    __device__ void sum2f(float a, float b, float out[2], float*, int& rot)
+    {
+        a = blockf(a);
+        b = blockf(b);
+        float* tab = a_.gslots_f + (size_t)rot * 2 * gridDim.x;
+        if (threadIdx.x == 0) {
+            tab[2 * blockIdx.x] = a;
+            tab[2 * blockIdx.x + 1] = b;
+        }
+        sync();
+        const int lane = threadIdx.x & 31;
+        float s0 = 0.f, s1 = 0.f;
+        for (int r = lane; r < (int)gridDim.x; r += 32) {
+            s0 += __ldcg(tab + 2 * r);
+            s1 += __ldcg(tab + 2 * r + 1);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            s0 += __shfl_xor_sync(kFull, s0, o);
+            s1 += __shfl_xor_sync(kFull, s1, o);
+        }
+        out[0] = s0;
+        out[1] = s1;
+        rot = (rot + 1) % 3;
+    }
+    __device__ void sum2d(double a, double b, double out[2], double*, int& rot)
+    {
+        a = blockd(a);
+        b = blockd(b);
+        double* tab = a_.gslots_d + (size_t)rot * 2 * gridDim.x;
+        if (threadIdx.x == 0) {
+            tab[2 * blockIdx.x] = a;
+            tab[2 * blockIdx.x + 1] = b;
+        }
+        sync();
+        const int lane = threadIdx.x & 31;
+        double s0 = 0.0, s1 = 0.0;
+        for (int r = lane; r < (int)gridDim.x; r += 32) {
+            s0 += __ldcg(tab + 2 * r);
+            s1 += __ldcg(tab + 2 * r + 1);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            s0 += __shfl_xor_sync(kFull, s0, o);
+            s1 += __shfl_xor_sync(kFull, s1, o);
+        }
+        out[0] = s0;
+        out[1] = s1;
+        rot = (rot + 1) % 3;
+    }
+
+  private:
+    __device__ float blockf(float v)
+    {
+        __shared__ float w[32];
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+        __syncthreads();
+        if (lane == 0) w[wid] = v;
+        __syncthreads();
+        float t = lane < nw ? w[lane] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
+        return t;
+    }
+    __device__ double blockd(double v)
+    {
+        __shared__ double w[32];
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+        __syncthreads();
+        if (lane == 0) w[wid] = v;
+        __syncthreads();
+        double t = lane < nw ? w[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
+        return t;
+    }
+    const MgArgs& a_;
+};
+
 __device__ __forceinline__ float apply_S(const MgLevelDev& L, const float* v, int c)
 {
     const int j = c / L.nx, i = c - j * L.nx;
@@ -312,7 +433,8 @@ __device__ void vcycle_local(const MgLevelDev* S, int l0, int nl, int nu, float 
 // z = M^{-1} s: one V-cycle; input in lv[0].r, output in lv[0].t.  Levels
 // above local_from are spread over the cluster (L2 data, cluster barriers);
 // the rest run in CTA 0 on its shared-memory copy S.
-__device__ void vcycle(const MgArgs& a, const MgLevelDev* S, ClusterCtx& cx)
+template <class Ctx>
+__device__ void vcycle(const MgArgs& a, const MgLevelDev* S, Ctx& cx)
 {
     constexpr int U = 4;
     const int nl = a.nl, lf = a.local_from;
@@ -399,13 +521,13 @@ __device__ void vcycle(const MgArgs& a, const MgLevelDev* S, ClusterCtx& cx)
     }
 }
 
-__global__ void __launch_bounds__(kMgBlock) mg_solve_kernel(const MgArgs a)
+template <class Ctx>
+__device__ __forceinline__ void mg_solve_body(const MgArgs& a, Ctx& cx)
 {
     constexpr int U = 4;   // cells per thread whose loads are in flight together
     __shared__ float slots_f[6];
     __shared__ double slots_d[6];
     extern __shared__ __align__(16) float mg_smem[];
-    ClusterCtx cx(a.local_from);
     if (ld_volatile_int(&a.status->done)) return;   // same value in every CTA (set by an earlier kernel)
     // shared-memory copy of the local levels (used by CTA 0 only)
     __shared__ MgLevelDev S[kMaxLevels];
@@ -560,6 +682,20 @@ __global__ void __launch_bounds__(kMgBlock) mg_solve_kernel(const MgArgs a)
     cx.sync();
 }
 
+__global__ void __launch_bounds__(kMgBlock) mg_solve_kernel(const MgArgs a)
+{
+    ClusterCtx cx(a.local_from);
+    mg_solve_body(a, cx);
+}
+
+// The same solver over a cooperative grid of one CTA per SM (meshes whose
+// strip plan does not fit a cluster's shared memory).
+__global__ void __launch_bounds__(kMgBlock) mg_solve_grid_kernel(const MgArgs a)
+{
+    GridCtx cx(a);
+    mg_solve_body(a, cx);
+}
+
 // ------------------------------------------------------------ strip solver
 // The same iteration (FP64 refinement around FP32 MG-PCG, identical cycle)
 // with every level resident in the cluster's shared memory.  Levels 0..ld
@@ -576,6 +712,7 @@ __global__ void __launch_bounds__(kMgBlock) mg_solve_kernel(const MgArgs a)
 constexpr int kSA_D = 0, kSA_ID = 1, kSA_CX = 2, kSA_CY = 3, kSA_X = 4, kSA_T = 5, kSA_R = 6;
 constexpr int kSA_P = 7, kSA_DL = 8;   // level 0 only
 constexpr int kMaxCl = 16;
+constexpr long long kGridMinCells = 128 * 128;   // the grid-wide solver from this many cells on
 
 struct SLevel {
     int nx, ny;
@@ -1276,6 +1413,10 @@ MgArgs fallback_args(const Plan& P, const double* guess, double* out, size_t& sm
     a.omega = 0.8f;
     a.alpha = 1.8f;
     a.status = P.status;
+    a.gslots_d = P.mg_gslots_d;
+    a.gslots_f = P.mg_gslots_f;
+    a.gbar = P.status->mg_bar;
+    a.wait_cycles = P.wait_cycles;
     int off = 0;
     for (int l = P.mg.local_from; l < P.mg.nl; ++l) {
         a.loff[l] = off;
@@ -1312,7 +1453,19 @@ cudaError_t plan_synthetic(Plan& P)
     size_t smem = 0;
     (void)fallback_args(P, nullptr, nullptr, smem);
     P.synth_bytes = smem;
-    return raise_limit((const void*)mg_solve_kernel, smem);
+    P.synth_grid = 0;
+    cudaError_t e = raise_limit((const void*)mg_solve_kernel, smem);
+    if (e != cudaSuccess) return e;
+    // large meshes: the same solver over a cooperative grid of every SM
+    if ((long long)P.N >= kGridMinCells && raise_limit((const void*)mg_solve_grid_kernel, smem) == cudaSuccess) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mg_solve_grid_kernel, kMgBlock, smem) ==
+                cudaSuccess && per_sm >= 1) {
+            P.synth_grid = std::min(kMaxCgBlocks, per_sm * P.num_sms);
+        }
+        cudaGetLastError();
+    }
+    return cudaSuccess;
 }
 
 // The solver plan_synthetic chose.
@@ -1327,7 +1480,12 @@ cudaError_t launch_synthetic_solve(const Plan& P, const double* guess, double* o
         return launch_cluster((const void*)mg_strip_kernel, args, P.synth_cl, bytes, st);
     }
     size_t smem = 0;
-    const MgArgs a = fallback_args(P, guess, out, smem);
+    MgArgs a = fallback_args(P, guess, out, smem);
+    if (P.synth_grid > 0) {
+        void* args[] = {&a};
+        return cudaLaunchCooperativeKernel((const void*)mg_solve_grid_kernel, dim3(P.synth_grid), dim3(kMgBlock),
+                                           args, smem, st);
+    }
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(P.mg.cluster);
     cfg.blockDim = dim3(kMgBlock);

@@ -91,7 +91,9 @@ def test_sweep_is_deterministic(gs):
     assert bool((a["rho"] == b["rho"]).all()) and bool((a["F"] == b["F"]).all())
 
 
-@pytest.mark.parametrize("seed,shape", [(11, (40, 37)), (12, (9, 70)), (13, (1, 5))])
+# (320, 300): no strip plan fits a cluster's shared memory, so the
+# global-memory solver runs over a cooperative grid of every SM
+@pytest.mark.parametrize("seed,shape", [(11, (40, 37)), (12, (9, 70)), (13, (1, 5)), (14, (320, 300))])
 def test_synthetic_step_parity(gs, seed, shape):
     p = W.random_problem(shape[0], shape[1], order=6, seed=seed)
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -122,6 +124,7 @@ def _solve(gs, p, **kw):
 
 SOLVE_CASES = [
     ("random_40x37_S6", lambda: W.random_problem(40, 37, order=6, seed=21, ratio_range=(0.5, 0.99))),
+    ("random_320x300_S4_grid_solver", lambda: W.random_problem(320, 300, order=4, seed=22, ratio_range=(0.5, 0.99))),
     ("uniform_64_S8", lambda: W.config_small()),
     ("channel_64_S8", lambda: W.channel_problem(64, 8, 2, width=2, sigma_bulk=200.0)),
 ]
