@@ -13,6 +13,9 @@ The time-dependent radiation-material steps (oracle/timedep.py) are pinned
 by tests/test_oracle_timedep.py: brute-force solves of the fully implicit
 and the Fleck-Cummings systems on tiny meshes, equilibrium preservation,
 energy conservation and the long-step radiative-equilibrium limit.
+The adjoint of a time-dependent GSIS run (oracle/td_adjoint.py) is pinned by
+tests/test_oracle_td_adjoint.py: central differences of full forward runs
+with respect to the opacities and the initial state.
 The UW2 kinetic step (oracle/uw2.py) is pinned by tests/test_oracle_uw2.py:
 exactness on linear fields, the Barth-Jespersen bound, the zero-limiter
 reduction to the UW1 oracle, conservation, second-order convergence on a
