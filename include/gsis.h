@@ -283,6 +283,51 @@ int gsis_td_solve(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis
                   void* stream);
 
 /*
+ * Gradient of J = dJ_drho . rho^N + dJ_dT . T^N, a functional of the state
+ * after a time-dependent GSIS run (gsis_td_solve with GSIS_SCHEME_GSIS), with
+ * respect to the per-cell opacities and the initial state, by the adjoint of
+ * every backward-Euler step (reverse mode).  The paper has no counterpart of
+ * this call: it differentiates the discrete equations gsis_td_solve solves.
+ *   Step n's converged result is the fixed point of the kinetic step
+ *   (Eqs. (RTE_g_semi), (RTE_d)), the synthetic balance (Eqs. (GSIS_dse),
+ *   (MSE_d)) and the material equation (Eq. (Tm_d)); its adjoint, with T
+ *   eliminated cell by cell, is a transposed GSIS iteration with the step's
+ *   Newton-eliminated synthetic operator, the effective scattering
+ *   sigma_s + (1 - f) sigma_a and the transposed sweep with 1/(c dt) on the
+ *   diagonal, iterated to opt->tol on Err (Eq. (Err_W)) of the adjoint
+ *   density; one more transposed sweep per step carries the adjoint of the
+ *   intensities to the previous step.
+ * Checkpointing: the forward run keeps the input state of every
+ *   checkpoint_every-th step; the reverse pass recomputes one segment of
+ *   checkpoint_every steps at a time from its checkpoint (one extra forward
+ *   run in all) and keeps that segment's fixed points.  Device memory:
+ *   ceil(nsteps / checkpoint_every) + checkpoint_every intensity arrays
+ *   (K x N, FP32 with GSIS_FP32_SWEEP) on top of the solve's layout; the
+ *   gradient does not depend on checkpoint_every (the recomputation repeats
+ *   the same arithmetic).
+ * Arguments as in gsis_td_solve; dJ_drho, dJ_dT: device [N] or NULL (zero).
+ * rho, T: device [N] out or NULL, the state after the last step.
+ * grad_sigma_a, grad_sigma_s: device [N] out.  grad_rho0, grad_T0: device
+ * [N] out or NULL (the initial intensity is rho^0/4pi).  adj_iters: HOST
+ * [nsteps] out or NULL, adjoint iterations of every step.
+ * Requirements (else GSIS_ERR_ARG): opt->scheme == GSIS_SCHEME_GSIS, no
+ *   pseudo-time, spatial_order 1, uniform dx and dy, a quadrature closed
+ *   under Omega -> -Omega with equal weights, checkpoint_every >= 1.
+ * Returns GSIS_OK; a forward step's or an adjoint step's status when one did
+ * not converge (GSIS_ERR_MAXITER / GSIS_ERR_DIVERGED; the gradient is still
+ * written unless a step diverged); argument, CUDA, timeout or workspace
+ * errors.  Synchronises the stream.
+ */
+int gsis_td_adjoint_workspace_bytes(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis_options* opt,
+                                    const gsis_time_params* tp, int checkpoint_every, size_t* bytes);
+int gsis_td_adjoint(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis_options* opt,
+                    const gsis_time_params* tp, int checkpoint_every, const double* sigma_a, const double* sigma_s,
+                    const double* q, const double* inflow, const double* rho0, const double* T0,
+                    const double* dJ_drho, const double* dJ_dT, double* rho, double* T, double* grad_sigma_a,
+                    double* grad_sigma_s, double* grad_rho0, double* grad_T0, int* adj_iters, void* workspace,
+                    size_t workspace_bytes, void* stream);
+
+/*
  * Batched solve: n independent steady problems, each with its own mesh,
  * quadrature, opacities, sources and inflow, iterated together under one set
  * of options.  The paper solves one problem at a time and has no counterpart

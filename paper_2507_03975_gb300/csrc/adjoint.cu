@@ -110,8 +110,9 @@ __global__ void hbar_kernel(int nx, int ny, const double* __restrict__ dx, const
 __global__ void rbar_kernel(int nx, int ny, int K, const double* __restrict__ dx, const double* __restrict__ dy,
                             const double* __restrict__ hw, const double* __restrict__ bface,
                             const double* __restrict__ ow, const double* __restrict__ nu,
-                            const double* __restrict__ hx, const double* __restrict__ hy, double* rb,
-                            float* rb_f, float* hx_f, float* hy_f, double* inflow_adj, const int* done)
+                            const double* __restrict__ hx, const double* __restrict__ hy,
+                            const double* __restrict__ extra, double* rb, float* rb_f, float* hx_f, float* hy_f,
+                            double* inflow_adj, const int* done)
 {
     if (ld_volatile_int(done)) return;
     const int N = nx * ny;
@@ -127,6 +128,7 @@ __global__ void rbar_kernel(int nx, int ny, int K, const double* __restrict__ dx
         if (i == nx - 1) v += bface[ny + j] * n0;
         if (j == 0) v += bface[2 * ny + i] * n0;
         if (j == ny - 1) v += bface[2 * ny + nx + i] * n0;
+        if (extra) v += extra[c];
         rb[c] = v;
         if (rb_f) {
             rb_f[c] = (float)v;
@@ -277,10 +279,67 @@ struct GradArgs {
 // with b depending on sigma_t through the HoT weights and the boundary beta,
 // D through Gamma_f = 2/(3 (sig_c h_c + sig_n h_n)) (Eq. (Gamma_ij_com2)),
 // beta_f = 2/(3 sig_c h) + 1/4 and V sigma_a on the diagonal.
+// nu.(db/dsigma_c) - nu.(dD/dsigma_c) rho* of cell c: b depends on sigma_t
+// through the HoT weights and the boundary beta, D through
+// Gamma_f = 2/(3 (sig_c h_c + sig_n h_n)) (Eq. (Gamma_ij_com2)) and
+// beta_f = 2/(3 sig_c h) + 1/4 (V sigma_a on the diagonal is left to the caller).
+template <typename T>
+__device__ double synthetic_sigma_terms(const GradArgs<T>& a, int c)
+{
+    const int nx = a.nx, ny = a.ny;
+    const int j = c / nx, i = c - j * nx;
+    const double st = a.sigt[c], r0 = a.rho[c], n0 = a.nu[c], hxc = a.dx[i], hyc = a.dy[j];
+    double E = 0.0;
+    // -nu.(dD/dsigma_c) rho*: interior faces
+    auto face = [&](int nb, double hc, double hn, double A) {
+        const double den = st * hc + a.sigt[nb] * hn;
+        const double dG = -2.0 * hc / (3.0 * den * den);
+        E -= A * dG * (n0 - a.nu[nb]) * (r0 - a.rho[nb]);
+    };
+    if (i + 1 < nx) face(c + 1, hxc, a.dx[i + 1], hyc);
+    if (i > 0) face(c - 1, hxc, a.dx[i - 1], hyc);
+    if (j + 1 < ny) face(c + nx, hyc, a.dy[j + 1], hxc);
+    if (j > 0) face(c - nx, hyc, a.dy[j - 1], hxc);
+    // boundary faces: beta in D (-) and in b (+ A beta rho_1/2)
+    auto bnd = [&](double h, double A) {
+        const double dB = -2.0 / (3.0 * st * st * h);
+        E += A * dB * n0 * (a.rho_h[c] - r0);
+    };
+    if (i == 0) bnd(hxc, hyc);
+    if (i == nx - 1) bnd(hxc, hyc);
+    if (j == 0) bnd(hyc, hxc);
+    if (j == ny - 1) bnd(hyc, hxc);
+    // nu.(db/dsigma) through the HoT weights of c and of its neighbours
+    auto hotx = [&](int ci) {
+        const int jj = ci / nx, ii = ci - jj * nx;
+        const bool P = ii + 1 < nx, M = ii > 0;
+        return hot_deriv(a.sigt[ci], a.rho_h[ci], a.dx[ii], P, P ? a.sigt[ci + 1] : 1.0,
+                         P ? a.rho_h[ci + 1] : 0.0, P ? a.dx[ii + 1] : 0.0, M, M ? a.sigt[ci - 1] : 1.0,
+                         M ? a.rho_h[ci - 1] : 0.0, M ? a.dx[ii - 1] : 0.0);
+    };
+    auto hoty = [&](int ci) {
+        const int jj = ci / nx;
+        const bool P = jj + 1 < ny, M = jj > 0;
+        return hot_deriv(a.sigt[ci], a.rho_h[ci], a.dy[jj], P, P ? a.sigt[ci + nx] : 1.0,
+                         P ? a.rho_h[ci + nx] : 0.0, P ? a.dy[jj + 1] : 0.0, M, M ? a.sigt[ci - nx] : 1.0,
+                         M ? a.rho_h[ci - nx] : 0.0, M ? a.dy[jj - 1] : 0.0);
+    };
+    E += a.hx[c] * hotx(c).dself + a.hy[c] * hoty(c).dself;
+    if (i > 0) E += a.hx[c - 1] * hotx(c - 1).dplus;        // c is the + neighbour of W
+    if (i + 1 < nx) E += a.hx[c + 1] * hotx(c + 1).dminus;  // c is the - neighbour of E
+    if (j > 0) E += a.hy[c - nx] * hoty(c - nx).dplus;
+    if (j + 1 < ny) E += a.hy[c + nx] * hoty(c + nx).dminus;
+    return E;
+}
+
+// dJ/dsigma_a, dJ/dsigma_s of cell c = explicit derivative of the Lagrangian:
+//   kinetic:    sum_k phi_k (ds/dsigma - I_k dd/dsigma_t)   (ds_c/dsigma_s,c = rho*_c / 4pi)
+//   synthetic:  nu.(db/dsigma) - nu.(dD/dsigma) rho*  (synthetic_sigma_terms, and
+//               -V nu rho* from V sigma_a on the diagonal)
 template <typename T>
 __global__ void adj_grad_kernel(const GradArgs<T> a)
 {
-    const int nx = a.nx, ny = a.ny, N = a.N;
+    const int nx = a.nx, N = a.N;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
         const int j = c / nx, i = c - j * nx;
         double sphi = 0.0, sphiI = 0.0;
@@ -289,50 +348,103 @@ __global__ void adj_grad_kernel(const GradArgs<T> a)
             sphi += ph;
             sphiI += ph * (double)a.I[(size_t)a.refl[s] * N + c];
         }
-        const double st = a.sigt[c], r0 = a.rho[c], n0 = a.nu[c], hxc = a.dx[i], hyc = a.dy[j];
-        const double V = hxc * hyc;
-        double E = 0.0;
-        // -nu.(dD/dsigma_c) rho*: interior faces
-        auto face = [&](int nb, double hc, double hn, double A) {
-            const double den = st * hc + a.sigt[nb] * hn;
-            const double dG = -2.0 * hc / (3.0 * den * den);
-            E -= A * dG * (n0 - a.nu[nb]) * (r0 - a.rho[nb]);
-        };
-        if (i + 1 < nx) face(c + 1, hxc, a.dx[i + 1], hyc);
-        if (i > 0) face(c - 1, hxc, a.dx[i - 1], hyc);
-        if (j + 1 < ny) face(c + nx, hyc, a.dy[j + 1], hxc);
-        if (j > 0) face(c - nx, hyc, a.dy[j - 1], hxc);
-        // boundary faces: beta in D (-) and in b (+ A beta rho_1/2)
-        auto bnd = [&](double h, double A) {
-            const double dB = -2.0 / (3.0 * st * st * h);
-            E += A * dB * n0 * (a.rho_h[c] - r0);
-        };
-        if (i == 0) bnd(hxc, hyc);
-        if (i == nx - 1) bnd(hxc, hyc);
-        if (j == 0) bnd(hyc, hxc);
-        if (j == ny - 1) bnd(hyc, hxc);
-        // nu.(db/dsigma) through the HoT weights of c and of its neighbours
-        auto hotx = [&](int ci) {
-            const int jj = ci / nx, ii = ci - jj * nx;
-            const bool P = ii + 1 < nx, M = ii > 0;
-            return hot_deriv(a.sigt[ci], a.rho_h[ci], a.dx[ii], P, P ? a.sigt[ci + 1] : 1.0,
-                             P ? a.rho_h[ci + 1] : 0.0, P ? a.dx[ii + 1] : 0.0, M, M ? a.sigt[ci - 1] : 1.0,
-                             M ? a.rho_h[ci - 1] : 0.0, M ? a.dx[ii - 1] : 0.0);
-        };
-        auto hoty = [&](int ci) {
-            const int jj = ci / nx;
-            const bool P = jj + 1 < ny, M = jj > 0;
-            return hot_deriv(a.sigt[ci], a.rho_h[ci], a.dy[jj], P, P ? a.sigt[ci + nx] : 1.0,
-                             P ? a.rho_h[ci + nx] : 0.0, P ? a.dy[jj + 1] : 0.0, M, M ? a.sigt[ci - nx] : 1.0,
-                             M ? a.rho_h[ci - nx] : 0.0, M ? a.dy[jj - 1] : 0.0);
-        };
-        E += a.hx[c] * hotx(c).dself + a.hy[c] * hoty(c).dself;
-        if (i > 0) E += a.hx[c - 1] * hotx(c - 1).dplus;        // c is the + neighbour of W
-        if (i + 1 < nx) E += a.hx[c + 1] * hotx(c + 1).dminus;  // c is the - neighbour of E
-        if (j > 0) E += a.hy[c - nx] * hoty(c - nx).dplus;
-        if (j + 1 < ny) E += a.hy[c + nx] * hoty(c + nx).dminus;
+        const double r0 = a.rho[c], n0 = a.nu[c];
+        const double V = a.dx[i] * a.dy[j];
+        const double E = synthetic_sigma_terms(a, c);
         a.grad_ss[c] = r0 * kInvFourPi * sphi - sphiI + E;
         a.grad_sa[c] = -sphiI + E - V * n0 * r0;
+    }
+}
+
+// ---------------------------------------------------- time-step adjoint
+// Step n of a backward-Euler GSIS run at its fixed point (I^h, rho, T), with
+// kappa = 4 a c T^3, D2 = C_v/dt + kappa sigma_a, f = (C_v/dt)/D2 and the
+// adjoints (I', rho', T') of its output state, carried as phi' (I' = phi'/(c dt)):
+//   A_k^T phi_k = y_I,k + (db/dI_k)^T nu,  y_I,k = (phi'_k - w_k sum_j phi'_j/4pi)/(c dt),
+//   D' nu = y_rho + sigma_a y_T/D2 + ((sigma_s + (1 - f) sigma_a)/4pi) sum_k phi_k,
+//   D' = D_steady + diag(V (1/(c dt) + f sigma_a - sigma_a)),
+//   tau = (y_T + (sigma_a kappa/4pi) sum_k phi_k + V sigma_a kappa nu)/D2.
+// The part of phi from the carried intensities, chi_k = A_k^{-T}(phi'_k/(c dt)),
+// is one transposed sweep per step; the isotropic part of y_I joins rho_bar.
+struct TdAdjArgs {
+    int nx, ny, N;
+    const double* dx; const double* dy;
+    const double* sigma_a; const double* sigma_s;
+    TdAdjVecs v;
+    double* diag;
+};
+
+__global__ void td_adj_setup_kernel(const TdAdjArgs a)
+{
+    const TdAdjVecs& v = a.v;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < a.N; c += gridDim.x * blockDim.x) {
+        const int j = c / a.nx, i = c - j * a.nx;
+        const double V = a.dx[i] * a.dy[j];
+        const double sa = a.sigma_a[c], t = v.T[c];
+        const double kap = 4.0 * v.ac * t * t * t;
+        const double D2 = fma(kap, sa, v.cv_dt);
+        const double f = v.cv_dt / D2;
+        a.diag[c] = fma(V, v.inv_cdt + fma(f, sa, -sa), v.diag0[c]);
+        v.sig_eff[c] = fma(1.0 - f, sa, a.sigma_s[c]);
+        v.c0[c] = v.ybar_rho[c] + sa * v.ybar_T[c] / D2;
+        v.rb_extra[c] = -v.inv_cdt * v.sphi[c] * kInvFourPi;
+    }
+}
+
+// c = c0 + (sig_eff/4pi) sum_k chi_k; the first lam and right-hand side.
+template <typename T>
+__global__ void td_adj_start_kernel(const TdAdjArgs a, int K, double* lam, double* b)
+{
+    const TdAdjVecs& v = a.v;
+    const T* chi = static_cast<const T*>(v.chi);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < a.N; c += gridDim.x * blockDim.x) {
+        double sx = 0.0;
+        if (chi)
+            for (int s = 0; s < K; ++s) sx += (double)chi[(size_t)s * a.N + c];
+        const double cv = fma(v.sig_eff[c] * kInvFourPi, sx, v.c0[c]);
+        v.c0[c] = cv;
+        lam[c] = cv;
+        b[c] = cv;
+    }
+}
+
+// phi = phi_A + chi (carried to the previous step), tau, the step's explicit
+// terms added to the gradient, and the adjoints of the step's input state:
+//   y_rho' = (V nu + sum_k phi_k/4pi)/(c dt),  y_T' = tau C_v/dt.
+// Explicit terms beyond the steady ones (sigma_a only): the emission in the
+// kinetic source (phi(T)/4pi) sum_k phi_k, in the synthetic balance
+// V nu phi(T), and the material equation tau (rho - phi(T)).
+template <typename T>
+__global__ void td_adj_grad_kernel(const GradArgs<T> a, const TdAdjArgs t)
+{
+    const TdAdjVecs& v = t.v;
+    const T* chi = static_cast<const T*>(v.chi);
+    T* carry = static_cast<T*>(v.carry);
+    const int nx = a.nx, N = a.N;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+        const int j = c / nx, i = c - j * nx;
+        double sphi = 0.0, sphiI = 0.0;
+        for (int s = 0; s < a.K; ++s) {
+            const size_t o = (size_t)s * N + c;
+            T ph = a.phi[o];
+            if (chi) ph += chi[o];
+            carry[o] = ph;
+            sphi += (double)ph;
+            sphiI += (double)ph * (double)a.I[(size_t)a.refl[s] * N + c];
+        }
+        const double r0 = a.rho[c], n0 = a.nu[c];
+        const double V = a.dx[i] * a.dy[j];
+        const double sa = t.sigma_a[c], tc = v.T[c];
+        const double kap = 4.0 * v.ac * tc * tc * tc;
+        const double D2 = fma(kap, sa, v.cv_dt);
+        const double emis = v.ac * tc * tc * tc * tc;
+        const double tau = (v.ybar_T[c] + sa * kap * (kInvFourPi * sphi + V * n0)) / D2;
+        const double E = synthetic_sigma_terms(a, c);
+        a.grad_ss[c] += r0 * kInvFourPi * sphi - sphiI + E;
+        a.grad_sa[c] += -sphiI + E - V * n0 * r0 + emis * kInvFourPi * sphi + V * n0 * emis + tau * (r0 - emis);
+        v.ybar_rho[c] = v.inv_cdt * fma(V, n0, kInvFourPi * sphi);
+        v.ybar_T[c] = tau * v.cv_dt;
+        v.sphi[c] = sphi;
     }
 }
 
@@ -350,7 +462,7 @@ cudaError_t launch_adj_update_t(const Plan& P, cudaStream_t st)
     AdjUpdArgs<T> a{};
     a.nx = P.nx; a.ny = P.ny; a.N = P.N; a.K = P.K;
     a.dx = P.dx; a.dy = P.dy;
-    a.sigma_s = P.sigma_s; a.g = P.g;
+    a.sigma_s = P.adj_sig ? P.adj_sig : P.sigma_s; a.g = P.g;
     a.phi = static_cast<const T*>(P.Iadj);
     a.lam = P.lam; a.b = P.b;
     a.tol = P.tol; a.fixed_iters = P.fixed_iters; a.max_iter = P.max_iter;
@@ -361,8 +473,20 @@ cudaError_t launch_adj_update_t(const Plan& P, cudaStream_t st)
     return cudaGetLastError();
 }
 
+
+TdAdjArgs td_adj_args(const Plan& P, const TdAdjVecs& v)
+{
+    TdAdjArgs a{};
+    a.nx = P.nx; a.ny = P.ny; a.N = P.N;
+    a.dx = P.dx; a.dy = P.dy;
+    a.sigma_a = P.sigma_a; a.sigma_s = P.sigma_s;
+    a.v = v;
+    a.diag = P.diag;
+    return a;
+}
+
 template <typename T>
-cudaError_t launch_adj_grad_t(const Plan& P, double* gsa, double* gss, cudaStream_t st)
+GradArgs<T> grad_args(const Plan& P, double* gsa, double* gss)
 {
     GradArgs<T> a{};
     a.nx = P.nx; a.ny = P.ny; a.N = P.N; a.K = P.K;
@@ -372,11 +496,33 @@ cudaError_t launch_adj_grad_t(const Plan& P, double* gsa, double* gss, cudaStrea
     a.I = static_cast<const T*>(P.I);
     a.refl = P.refl;
     a.grad_sa = gsa; a.grad_ss = gss;
-    adj_grad_kernel<T><<<grid_for(P.N, 128, P.num_sms * 8), 128, 0, st>>>(a);
-    return cudaGetLastError();
+    return a;
 }
 
 }  // namespace
+
+cudaError_t launch_td_adjoint_setup(const Plan& P, const TdAdjVecs& v, cudaStream_t st)
+{
+    td_adj_setup_kernel<<<grid_for(P.N, 256, P.num_sms * 8), 256, 0, st>>>(td_adj_args(P, v));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_td_adjoint_start(const Plan& P, const TdAdjVecs& v, cudaStream_t st)
+{
+    const int g = grid_for(P.N, 256, P.num_sms * 8);
+    if (P.fp32) td_adj_start_kernel<float><<<g, 256, 0, st>>>(td_adj_args(P, v), P.K, P.lam, P.b);
+    else td_adj_start_kernel<double><<<g, 256, 0, st>>>(td_adj_args(P, v), P.K, P.lam, P.b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_td_adjoint_gradient(const Plan& P, const TdAdjVecs& v, double* grad_sa, double* grad_ss,
+                                       cudaStream_t st)
+{
+    const int g = grid_for(P.N, 128, P.num_sms * 8);
+    if (P.fp32) td_adj_grad_kernel<float><<<g, 128, 0, st>>>(grad_args<float>(P, grad_sa, grad_ss), td_adj_args(P, v));
+    else td_adj_grad_kernel<double><<<g, 128, 0, st>>>(grad_args<double>(P, grad_sa, grad_ss), td_adj_args(P, v));
+    return cudaGetLastError();
+}
 
 cudaError_t launch_synth_resid(const Plan& P, const double* b, const double* guess, cudaStream_t st)
 {
@@ -392,14 +538,21 @@ cudaError_t launch_adjoint_rhs(const Plan& P, const double* nu_new, cudaStream_t
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     rbar_kernel<<<g, 256, 0, st>>>(P.nx, P.ny, P.K, P.dx, P.dy, P.hw, P.bface, P.ow, P.nu, P.adj_x, P.adj_y,
-                                   P.adj_a, P.fp32 ? P.adj_a_f : nullptr, P.adj_x_f, P.adj_y_f, P.adj_inflow,
-                                   &P.status->done);
+                                   P.adj_rb_extra, P.adj_a, P.fp32 ? P.adj_a_f : nullptr, P.adj_x_f, P.adj_y_f,
+                                   P.adj_inflow, &P.status->done);
     return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_update(const Plan& P, cudaStream_t st)
 {
     return P.fp32 ? launch_adj_update_t<float>(P, st) : launch_adj_update_t<double>(P, st);
+}
+
+template <typename T>
+cudaError_t launch_adj_grad_t(const Plan& P, double* gsa, double* gss, cudaStream_t st)
+{
+    adj_grad_kernel<T><<<grid_for(P.N, 128, P.num_sms * 8), 128, 0, st>>>(grad_args<T>(P, gsa, gss));
+    return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_gradient(const Plan& P, double* grad_sa, double* grad_ss, cudaStream_t st)

@@ -384,13 +384,7 @@ void gsis::set_last_error(int code, const char* msg)
     g_last_error = msg ? msg : "";
 }
 
-namespace {
-
-cudaError_t launch_uw2_kinetic(Plan& P, cudaStream_t st)
-{
-    const cudaError_t e = launch_uw2_residual(P, st);
-    return e != cudaSuccess ? e : launch_delta_sweep(P, st);
-}
+namespace gsis {
 
 bool uniform_spacing(const double* h, int n)
 {
@@ -426,6 +420,16 @@ bool reflection_table(const gsis_quadrature* quad, std::vector<int>& refl)
         if (refl[s] < 0) return false;
     }
     return true;
+}
+
+}  // namespace gsis
+
+namespace {
+
+cudaError_t launch_uw2_kinetic(Plan& P, cudaStream_t st)
+{
+    const cudaError_t e = launch_uw2_residual(P, st);
+    return e != cudaSuccess ? e : launch_delta_sweep(P, st);
 }
 
 }  // namespace

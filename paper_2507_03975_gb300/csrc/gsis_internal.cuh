@@ -130,6 +130,9 @@ struct Plan {
     double* nu;                     // nu (adjoint of the synthetic equation)
     const double* g;                // dJ/drho (caller's device array)
     int* refl;                      // [K] sorted index of the reflected direction
+    const float* adj_sigt_f;        // FP32 transposed sweep: its diagonal sigma_t (+ 1/(c dt)); sigt_f when null
+    const double* adj_rb_extra;     // per-cell term added to rho_bar_1/2 (time step adjoint), or null
+    const double* adj_sig;          // scattering coefficient of the adjoint update; sigma_s when null
     // time-dependent radiation-material problem (allocated by the time-step layout only)
     struct {
         double* rho_n; double* T_n;     // state at t^n
@@ -172,6 +175,27 @@ cudaError_t launch_synth_resid(const Plan& P, const double* b, const double* gue
 cudaError_t launch_adjoint_rhs(const Plan& P, const double* nu_new, cudaStream_t st);   // nu, h_bar, rho_bar, inflow
 cudaError_t launch_adjoint_update(const Plan& P, cudaStream_t st);
 cudaError_t launch_adjoint_gradient(const Plan& P, double* grad_sa, double* grad_ss, cudaStream_t st);
+// Pseudo-time-form sweep with the given per-cell source, stored intensities
+// and output (no inflow): out_s = A_s^{-1}(src + shift iold_s).
+cudaError_t launch_sweep_pt_into(Plan& P, const void* src, const void* iold, void* out, cudaStream_t st);
+
+// Adjoint of one backward-Euler step of the time-dependent GSIS run (the
+// vectors of the step and of its carry to the previous step).
+struct TdAdjVecs {
+    const double* T;            // T of the step's fixed point
+    const double* diag0;        // synthetic diagonal without time and coupling terms
+    double* sig_eff;            // sigma_s + (1 - f) sigma_a
+    double* c0;                 // y_bar_rho + sigma_a y_bar_T / D2 (then + sig_eff/4pi sum chi)
+    double* rb_extra;           // -(1/(c dt)) sum_k phi'_k / 4pi
+    double* ybar_rho; double* ybar_T; double* sphi;   // carry: adjoints of rho^n, T^n; sum_k phi_k
+    const void* chi;            // [K][N] T, transposed solve of the carried intensities (null: zero)
+    void* carry;                // [K][N] T, phi of the step (out)
+    double inv_cdt, ac, cv_dt;
+};
+cudaError_t launch_td_adjoint_setup(const Plan& P, const TdAdjVecs& v, cudaStream_t st);   // D', sig_eff, c0, rb_extra
+cudaError_t launch_td_adjoint_start(const Plan& P, const TdAdjVecs& v, cudaStream_t st);   // c, lam = b = c
+cudaError_t launch_td_adjoint_gradient(const Plan& P, const TdAdjVecs& v, double* grad_sa, double* grad_ss,
+                                       cudaStream_t st);   // accumulate, carry, next y_bar
 
 // ------------------------------------------------------------ batches
 // Device tables of a batched solve (every problem's arguments of one

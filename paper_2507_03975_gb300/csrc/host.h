@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <cstddef>
+#include <vector>
 
 #include "gsis.h"
 #include "gsis_internal.cuh"
@@ -58,5 +59,11 @@ int prepare(Plan& P, const gsis_mesh* mesh, const gsis_quadrature* quad, const g
 // Copies the status block back (synchronising st) and maps device error bits.
 int read_status(Status& S, const Plan& P, cudaStream_t st);
 Sizes sizes_of(const gsis_mesh* m, const gsis_quadrature* q, const gsis_options* o);
+// All spacings equal (relative 1e-12).
+bool uniform_spacing(const double* h, int n);
+// Sorted index (quadrant-major, as in prepare) of the reflected direction
+// -Omega of every sorted direction; false if the set is not closed under
+// the reflection with equal weights.
+bool reflection_table(const gsis_quadrature* quad, std::vector<int>& refl);
 
 }  // namespace gsis

@@ -931,6 +931,7 @@ SweepArgs<T> sweep_args(const Plan& P)
             a.src = P.adj_a; a.ax = P.adj_x; a.ay = P.adj_y;
         } else {
             a.src = P.adj_a_f; a.ax = P.adj_x_f; a.ay = P.adj_y_f;
+            if (P.adj_sigt_f) a.sigt = P.adj_sigt_f;
         }
         a.I = static_cast<T*>(P.Iadj);
         a.inflow = P.adj_inflow;
@@ -1184,6 +1185,26 @@ cudaError_t launch_delta_sweep(Plan& P, cudaStream_t st)
 cudaError_t launch_adjoint_sweep(Plan& P, cudaStream_t st)
 {
     return P.fp32 ? launch_sweep_t<float, kSrcAdjoint, false>(P, st) : launch_sweep_t<double, kSrcAdjoint, true>(P, st);
+}
+
+template <typename T>
+cudaError_t launch_sweep_pt_into_t(Plan& P, const void* src, const void* iold, void* out, cudaStream_t st)
+{
+    constexpr bool PRE = sizeof(T) == 8;
+    SweepArgs<T> a = sweep_args<T, kSrcPseudoTime>(P);
+    a.src = static_cast<const T*>(src);
+    a.iold = static_cast<const T*>(iold);
+    a.I = static_cast<T*>(out);
+    a.inflow = nullptr;
+    sweep_kernel<T, kSrcPseudoTime, PRE, false>
+        <<<P.sweep_grid, kSweepPairs * 64, sweep_smem<T, kSrcPseudoTime>(), st>>>(a, SweepBatch<T>{});
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_pt_into(Plan& P, const void* src, const void* iold, void* out, cudaStream_t st)
+{
+    return P.fp32 ? launch_sweep_pt_into_t<float>(P, src, iold, out, st)
+                  : launch_sweep_pt_into_t<double>(P, src, iold, out, st);
 }
 
 // Moments of the last sweep into the given outputs: rho always, F when

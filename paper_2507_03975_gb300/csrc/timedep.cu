@@ -251,6 +251,156 @@ int check_tp(const gsis_time_params* tp, const gsis_options* opt)
     return GSIS_OK;
 }
 
+// One backward-Euler step from the state held in the plan (rho_m, T, the
+// correction cnext and In: I^n = In + cn); leaves the step's last iterate
+// (I = I^{m+1/2}, rho_h, rho_m, T, cnext) and its status in S.
+int run_step(Plan& P, const gsis_time_params* tp, const gsis_options* opt, int gsis, Status& S, cudaStream_t st)
+{
+    int rc;
+    const int g = grid_for(P.N, kRedBlock, P.num_sms * 8);
+    const int nmax = opt->fixed_iters > 0 ? opt->fixed_iters : opt->max_iter;
+    const TdArgs a = td_args(P, tp, gsis);
+    CK(cudaMemsetAsync(P.status, 0, sizeof(Status), st));
+    td_begin_kernel<<<g, kRedBlock, 0, st>>>(a);
+    CK(cudaGetLastError());
+    if (gsis) {   // multigrid hierarchy of the step's operator (coupling at T^n)
+        td_coef_kernel<<<g, kRedBlock, 0, st>>>(a);
+        CK(cudaGetLastError());
+        CK(launch_mg_setup(P, st));
+    }
+    td_source_kernel<<<g, kRedBlock, 0, st>>>(a);
+    CK(cudaGetLastError());
+    int launched = 0;
+    while (launched < nmax) {
+        const int batch = std::min(opt->check_every, nmax - launched);
+        for (int b = 0; b < batch; ++b) {
+            TIMED(GSIS_KCLASS_SWEEP, 1, launch_sweep(P, st));
+            TIMED(GSIS_KCLASS_MOMENTS, 2,
+                  launch_moments_to(P, gsis, false, P.rho_h, nullptr, nullptr, false, P.fb, false, st));
+            if (gsis) {
+                TIMED(GSIS_KCLASS_HOT_RHS, 3, launch_td_coef_hot_rhs(P, a, g, st));
+                TIMED(GSIS_KCLASS_SYNTH, 1, launch_synthetic_solve(P, P.rho_m, P.x, st));
+            }
+            TIMED(GSIS_KCLASS_UPDATE, 1, launch_td_update(P, a, st));
+        }
+        launched += batch;
+        if ((rc = read_status(S, P, st))) return rc;
+        if (S.done) break;
+    }
+    if (!gsis) {
+        td_end_si_kernel<<<g, kRedBlock, 0, st>>>(a);
+        CK(cudaGetLastError());
+    }
+    return GSIS_OK;
+}
+
+int step_result(const Status& S, int n)
+{
+    if (S.reason == kDiverged) return fail(GSIS_ERR_DIVERGED, "step %d: Err = %g after %d iterations", n, S.err, S.iter);
+    if (S.reason != kConverged && S.reason != kFixedDone)
+        return fail(GSIS_ERR_MAXITER, "step %d: Err = %g after %d iterations", n, S.err, S.iter);
+    return GSIS_OK;
+}
+
+// Start of a run: the step-independent synthetic diagonal, rho^0, T^0 and
+// I^0 = rho^0/4pi in In.
+int td_start(Plan& P, const gsis_time_params* tp, int gsis, const double* rho0, const double* T0, cudaStream_t st)
+{
+    const int g = grid_for(P.N, kRedBlock, P.num_sms * 8);
+    const TdArgs a = td_args(P, tp, gsis);
+    CK(cudaMemcpyAsync(P.td.diag0, P.diag, (size_t)P.N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    td_init_kernel<<<g, kRedBlock, 0, st>>>(a, rho0, T0);
+    CK(cudaGetLastError());
+    const size_t n = (size_t)P.K * P.N;
+    const int gi = grid_for((long long)n, 256, P.num_sms * 16);
+    if (P.fp32) fill_iso_kernel<float><<<gi, 256, 0, st>>>(static_cast<float*>(P.In), P.K, P.N, rho0);
+    else fill_iso_kernel<double><<<gi, 256, 0, st>>>(static_cast<double*>(P.In), P.K, P.N, rho0);
+    CK(cudaGetLastError());
+    return GSIS_OK;
+}
+
+__global__ void add_f_kernel(float* out, const float* __restrict__ a, const float* __restrict__ b, int n)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) out[c] = a[c] + b[c];
+}
+
+// Storage of the time-step adjoint after the solve layout: the transposed
+// solve of the carried intensities (chi) and the carry (phi), a zero source,
+// the FP32 transposed-sweep diagonal, six per-cell vectors, the checkpoints
+// (every C-th step's input state: In, cnext, rho, T) and the records of one
+// segment of C steps (each step's I^{m+1/2}, rho^{m+1/2}, rho, T).
+struct AdjStore {
+    void* chi; void* carry; void* zero;
+    float* sigt_shift_f;
+    double* sig_eff; double* c0; double* rb_extra; double* ybar_rho; double* ybar_T; double* sphi;
+    std::vector<void*> ck_I, rec_I;
+    std::vector<double*> ck_v, rec_v;   // 3 N doubles each
+};
+
+size_t adj_store(const Sizes& z, int nck, int seg, char* base, AdjStore* A)
+{
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char* {
+        char* p = base ? base + off : nullptr;
+        off += (bytes + kAlign - 1) / kAlign * kAlign;
+        return p;
+    };
+    const size_t N = (size_t)z.nx * z.ny, K = (size_t)z.K;
+    const size_t Ts = z.fp32 ? sizeof(float) : sizeof(double);
+    AdjStore tmp;
+    AdjStore& a = A ? *A : tmp;
+    a.chi = take(K * N * Ts);
+    a.carry = take(K * N * Ts);
+    a.zero = take(N * Ts);
+    a.sigt_shift_f = z.fp32 ? reinterpret_cast<float*>(take(N * sizeof(float))) : nullptr;
+    double** v[] = {&a.sig_eff, &a.c0, &a.rb_extra, &a.ybar_rho, &a.ybar_T, &a.sphi};
+    for (double** d : v) *d = reinterpret_cast<double*>(take(N * sizeof(double)));
+    a.ck_I.assign(nck, nullptr);
+    a.ck_v.assign(nck, nullptr);
+    for (int i = 0; i < nck; ++i) {
+        a.ck_I[i] = take(K * N * Ts);
+        a.ck_v[i] = reinterpret_cast<double*>(take(3 * N * sizeof(double)));
+    }
+    a.rec_I.assign(seg, nullptr);
+    a.rec_v.assign(seg, nullptr);
+    for (int i = 0; i < seg; ++i) {
+        a.rec_I[i] = take(K * N * Ts);
+        a.rec_v[i] = reinterpret_cast<double*>(take(3 * N * sizeof(double)));
+    }
+    return off;
+}
+
+Sizes td_adj_sizes(const gsis_mesh* m, const gsis_quadrature* q, const gsis_options* o)
+{
+    Sizes z = td_sizes(m, q, o);
+    z.adjoint = 1;
+    return z;
+}
+
+int check_td_adjoint(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis_options* opt,
+                     const gsis_time_params* tp, int checkpoint_every, std::vector<int>* refl)
+{
+    int rc;
+    if ((rc = check_mesh(mesh)) || (rc = check_quad(quad)) || (rc = check_opt(opt)) || (rc = check_tp(tp, opt)))
+        return rc;
+    if (opt->scheme != GSIS_SCHEME_GSIS) return fail(GSIS_ERR_ARG, "the adjoint is that of the GSIS time steps");
+    if (checkpoint_every < 1) return fail(GSIS_ERR_ARG, "checkpoint_every must be >= 1");
+    if (!uniform_spacing(mesh->dx, mesh->nx) || !uniform_spacing(mesh->dy, mesh->ny))
+        return fail(GSIS_ERR_ARG, "the adjoint needs a uniform mesh (transposed sweep = reflected sweep)");
+    std::vector<int> r;
+    if (!reflection_table(quad, r))
+        return fail(GSIS_ERR_ARG, "the adjoint needs a quadrature closed under Omega -> -Omega with equal weights");
+    if (refl) *refl = r;
+    return GSIS_OK;
+}
+
+size_t td_adj_bytes(const Sizes& z, int nsteps, int C)
+{
+    const int seg = std::min(C, nsteps);
+    const int nck = (nsteps + C - 1) / C;
+    return layout(z, nullptr, nullptr) + adj_store(z, nck, seg, nullptr, nullptr);
+}
+
 }  // namespace
 
 extern "C" {
@@ -285,71 +435,188 @@ int gsis_td_solve(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis
     const int gsis = opt->scheme == GSIS_SCHEME_GSIS;
     P.pt = 1;                 // the delta-form sweep: shift 1/(c dt), I_old = I^n
     P.q_syn = P.td.qeff;
-    const int g = grid_for(P.N, kRedBlock, P.num_sms * 8);
-    TdArgs a = td_args(P, tp, gsis);
-    CK(cudaMemcpyAsync(P.td.diag0, P.diag, (size_t)P.N * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    td_init_kernel<<<g, kRedBlock, 0, st>>>(a, rho0, T0);
-    CK(cudaGetLastError());
-    {
-        const size_t n = (size_t)P.K * P.N;
-        const int gi = grid_for((long long)n, 256, P.num_sms * 16);
-        if (P.fp32) fill_iso_kernel<float><<<gi, 256, 0, st>>>(static_cast<float*>(P.In), P.K, P.N, rho0);
-        else fill_iso_kernel<double><<<gi, 256, 0, st>>>(static_cast<double*>(P.In), P.K, P.N, rho0);
+    if ((rc = td_start(P, tp, gsis, rho0, T0, st))) return rc;
+    Status S{};
+    if ((rc = read_status(S, P, st))) return rc;
+
+    int result = GSIS_OK;
+    for (int n = 0; n < tp->nsteps; ++n) {
+        if (n > 0) std::swap(P.I, P.In);   // I^n = the last sweep's intensities (+ cn)
+        if ((rc = run_step(P, tp, opt, gsis, S, st))) return rc;
+        if (step_iters) step_iters[n] = S.iter;
+        if (step_err) step_err[n] = S.err;
+        if ((result = step_result(S, n)) != GSIS_OK) break;
+    }
+    if (F) CK(launch_moments_to(P, true, false, P.rho_h, F, nullptr, false, P.fb, true, st));
+    CK(cudaMemcpyAsync(rho, P.rho_m, (size_t)P.N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(T, P.td.T, (size_t)P.N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    return result;
+}
+
+int gsis_td_adjoint_workspace_bytes(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis_options* opt,
+                                    const gsis_time_params* tp, int checkpoint_every, size_t* bytes)
+{
+    int rc;
+    if ((rc = check_td_adjoint(mesh, quad, opt, tp, checkpoint_every, nullptr))) return rc;
+    if (!bytes) return fail(GSIS_ERR_ARG, "bytes is NULL");
+    *bytes = td_adj_bytes(td_adj_sizes(mesh, quad, opt), tp->nsteps, checkpoint_every);
+    return GSIS_OK;
+}
+
+int gsis_td_adjoint(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis_options* opt,
+                    const gsis_time_params* tp, int checkpoint_every, const double* sigma_a, const double* sigma_s,
+                    const double* q, const double* inflow, const double* rho0, const double* T0,
+                    const double* dJ_drho, const double* dJ_dT, double* rho, double* T, double* grad_sigma_a,
+                    double* grad_sigma_s, double* grad_rho0, double* grad_T0, int* adj_iters, void* workspace,
+                    size_t workspace_bytes, void* stream)
+{
+    int rc;
+    std::vector<int> refl;
+    if ((rc = check_td_adjoint(mesh, quad, opt, tp, checkpoint_every, &refl))) return rc;
+    if (!sigma_a || !sigma_s || !q || !rho0 || !T0 || !grad_sigma_a || !grad_sigma_s)
+        return fail(GSIS_ERR_ARG, "a required device pointer is NULL");
+    const Sizes z = td_adj_sizes(mesh, quad, opt);
+    const int nsteps = tp->nsteps, C = std::min(checkpoint_every, nsteps);
+    const int nck = (nsteps + C - 1) / C;
+    if ((rc = check_ws(workspace, workspace_bytes, td_adj_bytes(z, nsteps, C)))) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Plan P{};
+    const size_t main = layout(z, static_cast<char*>(workspace), &P);
+    AdjStore A;
+    adj_store(z, nck, C, static_cast<char*>(workspace) + main, &A);
+    P.shift0 = 1.0 / (tp->c * tp->dt);
+    if ((rc = prepare(P, mesh, quad, opt, sigma_a, sigma_s, q, inflow, st))) return rc;
+    P.pt = 1;
+    P.q_syn = P.td.qeff;
+    const size_t N = (size_t)P.N, KN = (size_t)P.K * P.N;
+    const size_t Ts = P.fp32 ? sizeof(float) : sizeof(double), Nd = N * sizeof(double);
+    CK(cudaMemcpyAsync(P.refl, refl.data(), refl.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    if ((rc = td_start(P, tp, 1, rho0, T0, st))) return rc;
+    CK(cudaMemsetAsync(A.zero, 0, N * Ts, st));
+    if (P.fp32) {
+        add_f_kernel<<<grid_for(P.N, 256, P.num_sms * 8), 256, 0, st>>>(A.sigt_shift_f, P.sigt_f, P.shift_f, P.N);
         CK(cudaGetLastError());
     }
     Status S{};
     if ((rc = read_status(S, P, st))) return rc;
 
-    const int nmax = opt->fixed_iters > 0 ? opt->fixed_iters : opt->max_iter;
-    int result = GSIS_OK;
-    for (int n = 0; n < tp->nsteps; ++n) {
-        if (n > 0) std::swap(P.I, P.In);   // I^n = the last sweep's intensities (+ cn)
-        a = td_args(P, tp, gsis);
-        CK(cudaMemsetAsync(P.status, 0, sizeof(Status), st));
-        td_begin_kernel<<<g, kRedBlock, 0, st>>>(a);
-        CK(cudaGetLastError());
-        if (gsis) {   // multigrid hierarchy of the step's operator (coupling at T^n)
-            td_coef_kernel<<<g, kRedBlock, 0, st>>>(a);
-            CK(cudaGetLastError());
-            CK(launch_mg_setup(P, st));
+    // forward run, keeping the input state of every C-th step
+    void* const I0 = P.I;
+    void* const In0 = P.In;
+    double* const rho_m0 = P.rho_m;
+    double* const rho_h0 = P.rho_h;
+    double* const T0d = P.td.T;
+    auto save_state = [&](double* v) -> int {
+        CK(cudaMemcpyAsync(v, P.td.cnext, Nd, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(v + N, P.rho_m, Nd, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(v + 2 * N, P.td.T, Nd, cudaMemcpyDeviceToDevice, st));
+        return GSIS_OK;
+    };
+    for (int n = 0; n < nsteps; ++n) {
+        if (n > 0) std::swap(P.I, P.In);
+        if (n % C == 0) {
+            CK(cudaMemcpyAsync(A.ck_I[n / C], P.In, KN * Ts, cudaMemcpyDeviceToDevice, st));
+            if ((rc = save_state(A.ck_v[n / C]))) return rc;
         }
-        td_source_kernel<<<g, kRedBlock, 0, st>>>(a);
-        CK(cudaGetLastError());
-        int launched = 0;
-        while (launched < nmax) {
-            const int batch = std::min(opt->check_every, nmax - launched);
-            for (int b = 0; b < batch; ++b) {
-                TIMED(GSIS_KCLASS_SWEEP, 1, launch_sweep(P, st));
-                TIMED(GSIS_KCLASS_MOMENTS, 2,
-                      launch_moments_to(P, gsis, false, P.rho_h, nullptr, nullptr, false, P.fb, false, st));
-                if (gsis) {
-                    TIMED(GSIS_KCLASS_HOT_RHS, 3, launch_td_coef_hot_rhs(P, a, g, st));
-                    TIMED(GSIS_KCLASS_SYNTH, 1, launch_synthetic_solve(P, P.rho_m, P.x, st));
-                }
-                TIMED(GSIS_KCLASS_UPDATE, 1, launch_td_update(P, a, st));
-            }
-            launched += batch;
-            if ((rc = read_status(S, P, st))) return rc;
-            if (S.done) break;
-        }
-        if (!gsis) {
-            td_end_si_kernel<<<g, kRedBlock, 0, st>>>(a);
-            CK(cudaGetLastError());
-        }
-        if (step_iters) step_iters[n] = S.iter;
-        if (step_err) step_err[n] = S.err;
-        if (S.reason == kDiverged) {
-            result = fail(GSIS_ERR_DIVERGED, "step %d: Err = %g after %d iterations", n, S.err, S.iter);
-            break;
-        }
-        if (S.reason != kConverged && S.reason != kFixedDone) {
-            result = fail(GSIS_ERR_MAXITER, "step %d: Err = %g after %d iterations", n, S.err, S.iter);
-            break;
-        }
+        if ((rc = run_step(P, tp, opt, 1, S, st))) return rc;
+        if ((rc = step_result(S, n))) return rc;
     }
-    if (F) CK(launch_moments_to(P, true, false, P.rho_h, F, nullptr, false, P.fb, true, st));
-    CK(cudaMemcpyAsync(rho, P.rho_m, (size_t)P.N * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    CK(cudaMemcpyAsync(T, P.td.T, (size_t)P.N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (rho) CK(cudaMemcpyAsync(rho, P.rho_m, Nd, cudaMemcpyDeviceToDevice, st));
+    if (T) CK(cudaMemcpyAsync(T, P.td.T, Nd, cudaMemcpyDeviceToDevice, st));
+
+    // reverse sweep over the segments: recompute the segment's steps from its
+    // checkpoint, then the step adjoints last to first
+    TdAdjVecs v{};
+    v.diag0 = P.td.diag0;
+    v.sig_eff = A.sig_eff; v.c0 = A.c0; v.rb_extra = A.rb_extra;
+    v.ybar_rho = A.ybar_rho; v.ybar_T = A.ybar_T; v.sphi = A.sphi;
+    v.carry = A.carry;
+    v.inv_cdt = 1.0 / (tp->c * tp->dt);
+    v.ac = tp->a * tp->c;
+    v.cv_dt = tp->cv / tp->dt;
+    if (dJ_drho) CK(cudaMemcpyAsync(A.ybar_rho, dJ_drho, Nd, cudaMemcpyDeviceToDevice, st));
+    else CK(cudaMemsetAsync(A.ybar_rho, 0, Nd, st));
+    if (dJ_dT) CK(cudaMemcpyAsync(A.ybar_T, dJ_dT, Nd, cudaMemcpyDeviceToDevice, st));
+    else CK(cudaMemsetAsync(A.ybar_T, 0, Nd, st));
+    CK(cudaMemsetAsync(A.sphi, 0, Nd, st));
+    CK(cudaMemsetAsync(grad_sigma_a, 0, Nd, st));
+    CK(cudaMemsetAsync(grad_sigma_s, 0, Nd, st));
+    CK(cudaMemsetAsync(P.nu, 0, Nd, st));
+    const int nmax = opt->fixed_iters > 0 ? opt->fixed_iters : opt->max_iter;
+    bool have_carry = false;
+    int result = GSIS_OK;
+    for (int sg = nck - 1; sg >= 0; --sg) {
+        const int n0 = sg * C, n1 = std::min(n0 + C, nsteps);
+        // the segment's input state
+        P.I = I0; P.In = In0; P.rho_m = rho_m0; P.rho_h = rho_h0; P.td.T = T0d;
+        CK(cudaMemcpyAsync(P.td.cnext, A.ck_v[sg], Nd, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(P.rho_m, A.ck_v[sg] + N, Nd, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(P.td.T, A.ck_v[sg] + 2 * N, Nd, cudaMemcpyDeviceToDevice, st));
+        for (int r = 0; r < n1 - n0; ++r) {
+            P.In = r == 0 ? A.ck_I[sg] : A.rec_I[r - 1];
+            P.I = A.rec_I[r];
+            if ((rc = run_step(P, tp, opt, 1, S, st))) return rc;
+            if ((rc = step_result(S, n0 + r))) return rc;
+            double* rv = A.rec_v[r];
+            CK(cudaMemcpyAsync(rv, P.rho_h, Nd, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(rv + N, P.rho_m, Nd, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(rv + 2 * N, P.td.T, Nd, cudaMemcpyDeviceToDevice, st));
+        }
+        for (int r = n1 - n0 - 1; r >= 0; --r) {
+            const int n = n0 + r;
+            // the step's fixed point
+            P.I = A.rec_I[r];
+            P.rho_h = A.rec_v[r];
+            P.rho_m = A.rec_v[r] + N;
+            v.T = A.rec_v[r] + 2 * N;
+            v.chi = have_carry ? A.chi : nullptr;
+            P.g = A.c0;
+            P.adj_sig = A.sig_eff;
+            P.adj_rb_extra = A.rb_extra;
+            P.adj_sigt_f = A.sigt_shift_f;
+            CK(cudaMemsetAsync(P.status, 0, sizeof(Status), st));
+            TIMED(GSIS_KCLASS_SETUP, 1, launch_td_adjoint_setup(P, v, st));
+            CK(launch_mg_setup(P, st));
+            if (have_carry) TIMED(GSIS_KCLASS_SWEEP, 1, launch_sweep_pt_into(P, A.zero, A.carry, A.chi, st));
+            TIMED(GSIS_KCLASS_SETUP, 1, launch_td_adjoint_start(P, v, st));
+            // transposed GSIS iteration of the step: lam = c + (sig_eff/4pi) sum_k phi_A,k(D'^{-1} lam)
+            auto pass = [&](bool update) -> int {
+                TIMED(GSIS_KCLASS_HOT_RHS, 1, launch_synth_resid(P, P.b, P.nu, st));
+                TIMED(GSIS_KCLASS_SYNTH, 1, launch_synthetic_solve(P, P.nu, P.x, st));
+                TIMED(GSIS_KCLASS_HOT_RHS, 2, launch_adjoint_rhs(P, P.x, st));
+                TIMED(GSIS_KCLASS_SWEEP, 1, launch_adjoint_sweep(P, st));
+                if (update) TIMED(GSIS_KCLASS_UPDATE, 1, launch_adjoint_update(P, st));
+                return GSIS_OK;
+            };
+            int launched = 0;
+            while (launched < nmax) {
+                const int batch = std::min(opt->check_every, nmax - launched);
+                for (int b = 0; b < batch; ++b)
+                    if ((rc = pass(true))) return rc;
+                launched += batch;
+                if ((rc = read_status(S, P, st))) return rc;
+                if (S.done) break;
+            }
+            if (adj_iters) adj_iters[n] = S.iter;
+            if (S.reason == kDiverged) {
+                result = fail(GSIS_ERR_DIVERGED, "adjoint of step %d: Err = %g after %d iterations", n, S.err, S.iter);
+            } else if (S.reason != kConverged && S.reason != kFixedDone && result == GSIS_OK) {
+                result = fail(GSIS_ERR_MAXITER, "adjoint of step %d: Err = %g after %d iterations", n, S.err, S.iter);
+            }
+            // nu and phi at the final lam, the step's gradient terms and its carry
+            CK(cudaMemsetAsync(&P.status->done, 0, sizeof(int), st));
+            if ((rc = pass(false))) return rc;
+            TIMED(GSIS_KCLASS_UPDATE, 1, launch_td_adjoint_gradient(P, v, grad_sigma_a, grad_sigma_s, st));
+            if ((rc = read_status(S, P, st))) return rc;
+            have_carry = true;
+            if (result == GSIS_ERR_DIVERGED) break;
+        }
+        if (result == GSIS_ERR_DIVERGED) break;
+    }
+    P.I = I0; P.In = In0; P.rho_m = rho_m0; P.rho_h = rho_h0; P.td.T = T0d;
+    if (grad_rho0) CK(cudaMemcpyAsync(grad_rho0, A.ybar_rho, Nd, cudaMemcpyDeviceToDevice, st));
+    if (grad_T0) CK(cudaMemcpyAsync(grad_T0, A.ybar_T, Nd, cudaMemcpyDeviceToDevice, st));
     CK(cudaStreamSynchronize(st));
     return result;
 }

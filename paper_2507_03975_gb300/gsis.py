@@ -553,3 +553,64 @@ def td_solve(dx, dy, mu, eta, w, sigma_a, sigma_s, q, rho0, T0, dt, nsteps, c=1.
         ctypes.c_size_t(workspace.numel()), _stream(stream))
     _raise(rc)
     return dict(rho=rho, T=T, F=F, step_iters=np.array(list(its)), step_err=errs, status=rc, workspace=workspace)
+
+
+def _td_adj_load():
+    lib = _td_load()
+    if not getattr(lib, "_td_adj_bound", False):
+        vp, sz = ctypes.c_void_p, ctypes.c_size_t
+        Mp, Qp, Op = ctypes.POINTER(Mesh), ctypes.POINTER(Quadrature), ctypes.POINTER(Options)
+        Tp = ctypes.POINTER(TimeParams)
+        lib.gsis_td_adjoint_workspace_bytes.argtypes = [Mp, Qp, Op, Tp, ctypes.c_int, ctypes.POINTER(sz)]
+        lib.gsis_td_adjoint_workspace_bytes.restype = ctypes.c_int
+        lib.gsis_td_adjoint.argtypes = [Mp, Qp, Op, Tp, ctypes.c_int] + [vp] * 14 + [ctypes.POINTER(ctypes.c_int),
+                                                                                     vp, sz, vp]
+        lib.gsis_td_adjoint.restype = ctypes.c_int
+        lib._td_adj_bound = True
+    return lib
+
+
+def td_adjoint_workspace_bytes(dx, dy, mu, eta, w, dt, nsteps, checkpoint_every, c=1.0, a=1.0, cv=1.0,
+                               options: Options | None = None) -> int:
+    ar = _Args(dx, dy, mu, eta, w)
+    o = options or default_options()
+    tp = TimeParams(dt, c, a, cv, nsteps)
+    n = ctypes.c_size_t(0)
+    _raise(_td_adj_load().gsis_td_adjoint_workspace_bytes(ctypes.byref(ar.mesh), ctypes.byref(ar.quad),
+                                                          ctypes.byref(o), ctypes.byref(tp),
+                                                          int(checkpoint_every), ctypes.byref(n)))
+    return int(n.value)
+
+
+def td_adjoint(dx, dy, mu, eta, w, sigma_a, sigma_s, q, rho0, T0, dt, nsteps, dJ_drho=None, dJ_dT=None,
+               checkpoint_every=None, c=1.0, a=1.0, cv=1.0, inflow=None, options: Options | None = None,
+               workspace=None, stream=None):
+    """gsis_td_adjoint: gradient of dJ_drho . rho^N + dJ_dT . T^N after a
+    time-dependent GSIS run with respect to sigma_a, sigma_s, rho^0, T^0.
+    checkpoint_every defaults to ceil(sqrt(nsteps)).  Returns dict(grad_sigma_a,
+    grad_sigma_s, grad_rho0, grad_T0, rho, T, adj_iters, status, workspace)."""
+    import math as _m
+
+    import torch
+    ar = _Args(dx, dy, mu, eta, w)
+    o = options or default_options()
+    N, K = ar.mesh.nx * ar.mesh.ny, ar.quad.K
+    if checkpoint_every is None:
+        checkpoint_every = max(1, _m.isqrt(nsteps - 1) + 1 if nsteps > 1 else 1)
+    dev = sigma_a.device
+    out = {k: torch.empty(N, dtype=torch.float64, device=dev)
+           for k in ("rho", "T", "grad_sigma_a", "grad_sigma_s", "grad_rho0", "grad_T0")}
+    its = (ctypes.c_int * nsteps)()
+    tp = TimeParams(dt, c, a, cv, nsteps)
+    workspace = _workspace(td_adjoint_workspace_bytes(ar.dx, ar.dy, ar.mu, ar.eta, ar.w, dt, nsteps,
+                                                      checkpoint_every, c, a, cv, o), workspace, dev)
+    rc = _td_adj_load().gsis_td_adjoint(
+        ctypes.byref(ar.mesh), ctypes.byref(ar.quad), ctypes.byref(o), ctypes.byref(tp), int(checkpoint_every),
+        _dev(sigma_a, N, "sigma_a"), _dev(sigma_s, N, "sigma_s"), _dev(q, N, "q"),
+        _dev(inflow, 2 * (ar.mesh.nx + ar.mesh.ny) * K, "inflow"), _dev(rho0, N, "rho0"), _dev(T0, N, "T0"),
+        _dev(dJ_drho, N, "dJ_drho"), _dev(dJ_dT, N, "dJ_dT"), _dev(out["rho"]), _dev(out["T"]),
+        _dev(out["grad_sigma_a"]), _dev(out["grad_sigma_s"]), _dev(out["grad_rho0"]), _dev(out["grad_T0"]), its,
+        ctypes.c_void_p(workspace.data_ptr()), ctypes.c_size_t(workspace.numel()), _stream(stream))
+    _raise(rc)
+    out.update(adj_iters=np.array(list(its)), status=rc, workspace=workspace, checkpoint_every=checkpoint_every)
+    return out

@@ -111,3 +111,46 @@ def test_binding_refuses_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(gsis, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         gsis.load()
+
+
+def test_td_adjoint_checks_and_storage(gs):
+    """gsis_td_adjoint_workspace_bytes: argument checks (GSIS only, uniform
+    mesh, reflection-closed quadrature, no pseudo-time, checkpoint_every >= 1)
+    and the storage of ceil(nsteps/C) checkpoints plus one C-step segment."""
+    mu, eta, w = gs.quadrature_level_symmetric(4)
+    dx = np.full(16, 1 / 16)
+    ok = gs.default_options()
+
+    def nb(nsteps, C, o=ok, ddx=dx):
+        return gs.td_adjoint_workspace_bytes(ddx, dx, mu, eta, w, 0.1, nsteps, C, options=o)
+
+    for bad in (dict(o=gs.default_options(scheme=gs.SCHEME_SI)), dict(o=gs.default_options(beta=1.0)),
+                dict(ddx=np.linspace(0.5, 1.5, 16) / 16.0)):
+        with pytest.raises(gs.GsisError) as e:
+            nb(4, 2, **bad)
+        assert e.value.status == gs.GSIS_ERR_ARG
+    with pytest.raises(gs.GsisError):
+        nb(4, 0)
+    KN8 = len(w) * 16 * 16 * 8
+    # one more checkpoint or one more segment step costs one intensity array (plus per-cell vectors)
+    assert KN8 <= nb(9, 3) - nb(6, 3) < 2 * KN8          # 3 -> 2 checkpoints
+    assert KN8 <= nb(12, 6) - nb(12, 4) < 2 * KN8        # 2 checkpoints + 6 steps vs 3 + 4: one array more
+    assert nb(5, 5) == nb(5, 9)                           # the segment never exceeds the run
+
+
+def test_td_adjoint_binding_rejects_before_device_use(gs):
+    """The binding's argument list matches the C signature: a call with the
+    SI scheme returns GSIS_ERR_ARG before any device pointer is touched."""
+    mu, eta, w = gs.quadrature_level_symmetric(4)
+    a = gs._Args(np.full(8, 0.125), np.full(8, 0.125), mu, eta, w)
+    tp = gs.TimeParams(0.1, 1.0, 1.0, 1.0, 3)
+    dummy = ctypes.c_void_p(0x1000)   # never dereferenced
+    its = (ctypes.c_int * 3)()
+    lib = gs._td_adj_load()
+    rc = lib.gsis_td_adjoint(ctypes.byref(a.mesh), ctypes.byref(a.quad),
+                             ctypes.byref(gs.default_options(scheme=gs.SCHEME_SI)), ctypes.byref(tp), 2,
+                             *([dummy] * 14), its, ctypes.c_void_p(256), ctypes.c_size_t(1 << 40), None)
+    assert rc == gs.GSIS_ERR_ARG
+    rc = lib.gsis_td_adjoint(ctypes.byref(a.mesh), ctypes.byref(a.quad), ctypes.byref(gs.default_options()),
+                             ctypes.byref(tp), 2, *([dummy] * 14), its, None, ctypes.c_size_t(0), None)
+    assert rc == gs.GSIS_ERR_WORKSPACE
