@@ -37,7 +37,7 @@ METRIC = "cell-direction updates/s and time-to-converge (GSIS vs SI) on 1 GB300;
 UNIT = "cell-direction updates/s"
 TOL = 1e-8
 BETA = 10.0   # local pseudo-time control (Sec. 4.3) the 2000/0.2 opacity jump needs
-SWEEP_CAPTURE_SHA256 = "fdeafb7a982b55ff"   # sweep.cu at the ncu capture behind _sweep_traffic()
+SWEEP_CAPTURE_SHA256 = "db45d439aea64456"   # sweep.cu at the ncu capture behind _sweep_traffic()
 SYNTH_CAP = 2  # inner iterations of the synthetic solve per GSIS iteration (capped sub-iterations, Sec. 4.2)
 TD_SYNTH_CAP = 4  # the same cap on the 1024^2 time-dependent workload (its measured optimum: 2 -> 19, 4 -> 8 iterations per step)
 
@@ -109,14 +109,14 @@ def _clock_summary(proc, f, gpu_index):
 
 def _sweep_traffic():
     """DRAM bytes of one sweep launch on this workload from one ncu capture
-    (dram__bytes_read.sum + dram__bytes_write.sum, 96,124,416 + 3,909,632;
+    (dram__bytes_read.sum + dram__bytes_write.sum, 96,147,456 + 4,076,032;
     profiles/sweep_kernel_channel256.md), or None once the sweep source differs
     from the one that was captured."""
     import hashlib
     src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2507_03975_gb300", "csrc", "sweep.cu")
     with open(src, "rb") as f:
         digest = hashlib.sha256(f.read()).hexdigest()
-    return 100_034_048 if digest.startswith(SWEEP_CAPTURE_SHA256) else None
+    return 100_223_488 if digest.startswith(SWEEP_CAPTURE_SHA256) else None
 
 
 def adjoint_measure(gsis, torch, stream):
@@ -260,6 +260,61 @@ def timedep_measure(gsis, torch, stream, hbm):
     return out
 
 
+TD_ADJ_STEPS = 10
+
+
+def td_adjoint_measure(gsis, torch, stream):
+    """Gradient of J = sum of rho^N over the channel cells next to the left
+    wall after TD_ADJ_STEPS steps of the time-dependent workload (1024^2 S16,
+    dt = 1e-3, cold start), with respect to sigma_a, sigma_s, rho^0 and T^0:
+    FP32 sweeps, forward steps and adjoint iterations to Err < 1e-6,
+    checkpoints every ceil(sqrt(steps)) steps.  Device time with CUDA events
+    around the forward run alone and around the whole adjoint call (forward
+    run with checkpoints, one recomputation, the step adjoints), inputs
+    resident; a second instrumented call gives the kernel classes."""
+    p = W.config_timedep()
+    tpd = W.TIMEDEP
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    sa, ss, q, inflow = t(p.sigma_a), t(p.sigma_s), t(p.q), t(p.inflow.reshape(-1))
+    T0 = t(np.full(p.N, tpd["T0"]))
+    rho0 = t(np.full(p.N, tpd["a"] * tpd["c"] * tpd["T0"] ** 4))
+    cols = np.arange(p.N) % p.nx
+    g = t((((p.sigma_a + p.sigma_s) < 1.0) & (cols < 64)).astype(np.float64))
+    n = TD_ADJ_STEPS
+    opt = gsis.default_options(scheme=gsis.SCHEME_GSIS, precision=gsis.FP32_SWEEP, tol=1e-6, max_iter=2000,
+                               check_every=4, synth_rtol=1e-12, synth_max_iter=TD_SYNTH_CAP)
+    kw = dict(c=tpd["c"], a=tpd["a"], cv=tpd["cv"], inflow=inflow, options=opt)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return r, e0.elapsed_time(e1) * 1e-3
+
+    f, s_fwd = timed(lambda: gsis.td_solve(p.dx, p.dy, p.mu, p.eta, p.w, sa, ss, q, rho0, T0, tpd["dt"], n, **kw))
+    adj = lambda ws=None: gsis.td_adjoint(p.dx, p.dy, p.mu, p.eta, p.w, sa, ss, q, rho0, T0, tpd["dt"], n,
+                                          dJ_drho=g, workspace=ws, **kw)
+    r, s_adj = timed(adj)
+    gsis.profile_enable(True)
+    r2, _ = timed(lambda: adj(r["workspace"]))
+    prof = gsis.profile_read()
+    gsis.profile_enable(False)
+    same = bool(torch.equal(r["grad_sigma_a"], r2["grad_sigma_a"]))
+    return {"workload": f"channel_td_1024x1024_S16, {n} steps of dt = 1e-3, J = sum of rho^N over the channel "
+                        "cells of the first 64 columns",
+            "precision": "fp32 sweeps, fp64 synthetic solve / material / gradient terms", "tol": 1e-6,
+            "checkpoint_every": r["checkpoint_every"], "status": r["status"],
+            "forward_s": s_fwd, "forward_iters": int(f["step_iters"].sum()),
+            "adjoint_call_s": s_adj, "adjoint_over_forward": s_adj / s_fwd,
+            "adj_iters_per_step_mean": float(np.mean(r["adj_iters"])),
+            "workspace_gb": r["workspace"].numel() / 1e9,
+            "kernel_ms": {k: v["total_ms"] for k, v in prof.items()},
+            "repeat_bit_equal": same,
+            "grad_sigma_a_max": float(r["grad_sigma_a"].abs().max())}
+
+
 def uw2_measure(gsis, torch, stream, p, sa, ss, q, inflow, flush):
     """The channel workload with second-order upwind face values (the paper's
     transport scheme): GSIS, FP64, beta = 10, Err < 1e-8, synthetic solve
@@ -358,6 +413,9 @@ def run_ours(args):
     if args.timedep_only:   # the time-dependent measurement alone (profiling runs)
         print(json.dumps({"timedep": timedep_measure(gsis, torch, torch.cuda.current_stream(),
                                                      _peaks().get("hbm_gbs", 6800.0))}))
+        return 0
+    if args.td_adjoint_only:   # the time-dependent adjoint measurement alone
+        print(json.dumps({"td_adjoint": td_adjoint_measure(gsis, torch, torch.cuda.current_stream())}))
         return 0
     p, cfg = _workload(args)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
@@ -473,6 +531,11 @@ def run_ours(args):
     if not args.no_timedep:
         timedep = timedep_measure(gsis, torch, stream, _peaks().get("hbm_gbs", 6800.0))
 
+    # ---- adjoint of the time-dependent run (10 steps, checkpointed), once
+    td_adj = None
+    if not args.no_td_adjoint:
+        td_adj = td_adjoint_measure(gsis, torch, stream)
+
     # ---- batched solve of 64 independent problems (autotuned), once
     batch = None
     if not args.no_batch:
@@ -537,6 +600,7 @@ def run_ours(args):
             "adjoint": adj,
             "batch": batch,
             "timedep": timedep,
+            "td_adjoint": td_adj,
             "uw2": uw2,
             "clocks": clocks}
     print(json.dumps(line))
@@ -559,6 +623,8 @@ def main():
     ap.add_argument("--batch-only", action="store_true", help="run only the batched-solve measurement")
     ap.add_argument("--no-timedep", action="store_true", help="skip the time-dependent measurement")
     ap.add_argument("--no-uw2", action="store_true", help="skip the second-order upwind measurement")
+    ap.add_argument("--no-td-adjoint", action="store_true", help="skip the time-dependent adjoint measurement")
+    ap.add_argument("--td-adjoint-only", action="store_true", help="run only the time-dependent adjoint measurement")
     ap.add_argument("--timedep-only", action="store_true", help="run only the time-dependent measurement")
     ap.add_argument("--synth-cap", type=int, default=SYNTH_CAP,
                     help="inner iterations of the synthetic solve per GSIS iteration (0: solve to 1e-12)")
