@@ -62,6 +62,20 @@ def _dist():
     return ws, rank, local
 
 
+def replica_totals(dist, units, ms, device):
+    """Whole-job totals of independent replicas: the units every rank
+    processed (sum) and the slowest rank's timed milliseconds (max); with no
+    process group, the local values."""
+    if dist is None:
+        return float(units), float(ms)
+    import torch
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(t.item())
+
+
 def _clock_sampler():
     """nvidia-smi clocks/throttle sampling during the timed region."""
     f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
@@ -465,14 +479,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     prof = gsis.profile_read()
     gsis.profile_enable(False)
-    total_ms = sum(step_ms)
+    units, total_ms = replica_totals(dist, sum(iters) * p.N * p.K, sum(step_ms), dev)
     if dist:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
         dist.barrier()
-    n_ranks = max(ws, 1)
-    units = sum(iters) * p.N * p.K * n_ranks
     value = units / (total_ms * 1e-3)
 
     # ---- end to end through the C ABI: pinned host inputs in, result out
@@ -497,7 +506,10 @@ def run_ours(args):
         e2e_iters.append(r["iters"])
     h2d = sum(h.numel() * 8 for h in h_in)
     d2h = (h_rho.numel() + h_F.numel()) * 8
-    e2e_value = (sum(e2e_iters) * p.N * p.K / (sum(e2e_ms) * 1e-3) * n_ranks) if e2e_ms else None
+    e2e_value = None
+    if e2e_ms:
+        e2e_units, e2e_total = replica_totals(dist, sum(e2e_iters) * p.N * p.K, sum(e2e_ms), dev)
+        e2e_value = e2e_units / (e2e_total * 1e-3)
 
     # ---- time-to-converge of plain source iteration on the same problem (once)
     si = None
@@ -588,7 +600,7 @@ def run_ours(args):
                "sample": f"2 oracle GSIS iterations of the same workload ({dt:.1f} s, includes the oracle's "
                          "one-off sparse LU)"}
 
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": n_ranks, "steps": args.steps,
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": max(ws, 1), "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
             "time_to_converge": {"gsis": {"s": total_ms / args.steps * 1e-3, "iters": iters[0],
