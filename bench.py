@@ -9,7 +9,7 @@ over steps and ranks.  L2 is flushed (512 MiB write) before every step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
---impl reference times the FP64 CPU oracle (the reference of this build) on a
+--impl reference times the FP64 CPU oracle (the reference arm) on a
 bounded sample of the same workload on the host cores.  Under torchrun every
 rank runs an independent replica (no collective in the data path); rank 0
 prints one JSON line.
@@ -561,10 +561,17 @@ def run_ours(args):
             dist.destroy_process_group()
         return 0
 
-    # ---- roofline of the dominant kernel class (algorithmic work per launch, see DESIGN.md §5)
+    # ---- roofline of the dominant kernel class (algorithmic work per launch)
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
-    FP64_PEAK = 1250.0   # GFLOP/s, GB300 FP64 rate (FMA microbenchmark: 1252)
+    # GFLOP/s: the FP64 FMA rate measured in this run (independent FMA chains
+    # filling every SM, gsis_measure_fp64_fma); nominal 1250 if it fails
+    try:
+        FP64_PEAK = gsis.measure_fp64_fma()
+        fp64_src = "measured in this run: FP64 FMA kernel (gsis_measure_fp64_fma)"
+    except Exception as ex:   # noqa: BLE001
+        FP64_PEAK = 1250.0
+        fp64_src = f"nominal GB300 FP64 rate 1.25 TFLOP/s (measurement failed: {ex})"
     shares = {k: v["total_ms"] for k, v in prof.items()}
     tot = sum(shares.values()) or 1.0
     upd = p.N * p.K
@@ -596,7 +603,8 @@ def run_ours(args):
     roof.update({"traffic": _sweep_traffic() if dom == "sweep" else None,
                  "share": {k: v / tot for k, v in shares.items()},
                  "peak_source": ("measured hbm_gbs (MEASURED_PEAKS.json)" if roof["bound"] == "hbm"
-                                 else "GB300 FP64 rate 1.25 TFLOP/s (nominal; FMA microbenchmark 1.25)"),
+                                 else fp64_src),
+                 "fp64_fma_gflops": FP64_PEAK,
                  "others": {k: model(k) for k in ("sweep", "moments", "synth") if k != dom}})
 
     cpu = None

@@ -328,6 +328,16 @@ int gsis_td_adjoint(const gsis_mesh* mesh, const gsis_quadrature* quad, const gs
                     size_t workspace_bytes, void* stream);
 
 /*
+ * Measured FP64 FMA rate of the current device in GFLOP/s (host out),
+ * the denominator of the FP64-ALU-bound kernels' rooflines.  The paper has
+ * no counterpart: a measurement helper.  One kernel of independent
+ * dependent-FMA chains over 8 blocks of 256 threads per SM, best of three
+ * timed launches (CUDA events on the stream) after one warm-up.  No device
+ * memory is allocated.  Synchronises the stream.
+ */
+int gsis_measure_fp64_fma(double* gflops, void* stream);
+
+/*
  * Batched solve: n independent steady problems, each with its own mesh,
  * quadrature, opacities, sources and inflow, iterated together under one set
  * of options.  The paper solves one problem at a time and has no counterpart

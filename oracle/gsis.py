@@ -16,7 +16,7 @@ follows the paper's statement of it, in the paper's order:
        solve the finite-volume synthetic equation for rho^{m+1}.
   Err  (Sec. 6, Eq. (Err_W)).
 
-Readings where the paper is silent or ambiguous (each is listed in the design doc):
+Readings where the paper is silent or ambiguous:
   * steady state: 1/(c dt) = 0, hatted cross sections equal the plain ones;
   * diffusion part of the face flux is the compact two-point flux
     Gamma_ij (rho_i - rho_j) (Eq. (Gamma_ij_def)), which Appendix A states is

@@ -42,7 +42,7 @@ Eqs. (MSE_d), (Tm_d), (MSE_d1), (MSE_d2), (elem_mtx_M)):
   At the fixed point the linearisation is exact: the step's result is the
   fully implicit discrete solution (Eqs. (RTE_d), (MSE_d), (Tm_d)).
 
-Readings (listed in DESIGN.md):
+Readings:
   * the printed mu = a c T^3 dt sigma_a / (C_v + a c T^3 dt sigma_a) lacks
     the factor 4 that Eq. (Tm_semi_linear) gives; the derivation is followed
     (mu = 1 - f with kappa = 4 a c T^3);

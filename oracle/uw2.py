@@ -27,7 +27,7 @@ SI: rho^{m+1} = rho^{m+1/2}.  GSIS: the steady synthetic step of
 oracle/gsis.py, then I^{m+1} = I^{m+1/2} + (rho^{m+1} - rho^{m+1/2})/4pi
 (Eq. (GSIS_update)).  Initial I^0 = 0, rho^0 = 0.
 
-Readings (listed in the design doc): the gradient of I uses the same adaptive
+Readings: the gradient of I uses the same adaptive
 least squares as rho; the limiter's neighbourhood is the interior face
 neighbours; incoming boundary faces take the prescribed inflow (no
 reconstruction); psi is applied to both gradient components.  Besides the

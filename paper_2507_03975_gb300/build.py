@@ -13,7 +13,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libgsis.so")
 
-CU_SOURCES = ["sweep.cu", "synthetic.cu", "mg.cu", "api.cu", "batch.cu", "timedep.cu", "uw2.cu", "noalloc.cu", "adjoint.cu"]
+CU_SOURCES = ["sweep.cu", "synthetic.cu", "mg.cu", "api.cu", "batch.cu", "timedep.cu", "uw2.cu", "noalloc.cu", "adjoint.cu", "peak.cu"]
 CPP_SOURCES = ["quadrature.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -614,3 +614,15 @@ def td_adjoint(dx, dy, mu, eta, w, sigma_a, sigma_s, q, rho0, T0, dt, nsteps, dJ
     _raise(rc)
     out.update(adj_iters=np.array(list(its)), status=rc, workspace=workspace, checkpoint_every=checkpoint_every)
     return out
+
+
+def measure_fp64_fma(stream=None) -> float:
+    """gsis_measure_fp64_fma: the device's FP64 FMA rate in GFLOP/s."""
+    lib = load()
+    if not getattr(lib, "_peak_bound", False):
+        lib.gsis_measure_fp64_fma.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+        lib.gsis_measure_fp64_fma.restype = ctypes.c_int
+        lib._peak_bound = True
+    g = ctypes.c_double(0.0)
+    _raise(lib.gsis_measure_fp64_fma(ctypes.byref(g), _stream(stream)))
+    return float(g.value)
