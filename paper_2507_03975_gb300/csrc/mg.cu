@@ -712,7 +712,10 @@ __global__ void __launch_bounds__(kMgBlock) mg_solve_grid_kernel(const MgArgs a)
 constexpr int kSA_D = 0, kSA_ID = 1, kSA_CX = 2, kSA_CY = 3, kSA_X = 4, kSA_T = 5, kSA_R = 6;
 constexpr int kSA_P = 7, kSA_DL = 8;   // level 0 only
 constexpr int kMaxCl = 16;
-constexpr long long kGridMinCells = 128 * 128;   // the grid-wide solver from this many cells on
+// The grid-wide solver above this many cells: smaller meshes that miss the
+// strip plan by a few kilobytes (e.g. 234^2) stay on the cluster form, which
+// the batched solve also runs, so both give the same bits.
+constexpr long long kGridMinCells = 256 * 256;
 
 struct SLevel {
     int nx, ny;
@@ -1457,7 +1460,7 @@ cudaError_t plan_synthetic(Plan& P)
     cudaError_t e = raise_limit((const void*)mg_solve_kernel, smem);
     if (e != cudaSuccess) return e;
     // large meshes: the same solver over a cooperative grid of every SM
-    if ((long long)P.N >= kGridMinCells && raise_limit((const void*)mg_solve_grid_kernel, smem) == cudaSuccess) {
+    if ((long long)P.N > kGridMinCells && raise_limit((const void*)mg_solve_grid_kernel, smem) == cudaSuccess) {
         int per_sm = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mg_solve_grid_kernel, kMgBlock, smem) ==
                 cudaSuccess && per_sm >= 1) {
