@@ -372,6 +372,10 @@ __global__ void __launch_bounds__(kSweepPairs * 64, 1)
 sweep_kernel(const SweepArgs<T> a1, const SweepBatch<T> bt)
 {
     constexpr bool PT = MODE == kSrcPseudoTime, ADJ = MODE == kSrcAdjoint, DELTA = MODE == kSrcDelta;
+    // FP32: results collected in shared memory and written out per chunk in
+    // coarser stores (fewer store instructions per step); FP64 writes each
+    // result at once (there the write-out would sit on the band hand-off path)
+    constexpr bool STAGE = sizeof(T) == 4;
     using SM = SweepSmem<T, MODE != kSrcPlain, PRE>;
     using B = Bits<T>;
     constexpr int SEG = SM::SEG, NBUF = SM::NBUF, RS = SM::RS, NW = SM::NW;
@@ -650,8 +654,9 @@ sweep_kernel(const SweepArgs<T> a1, const SweepBatch<T> bt)
                     if (lane == 0) atomicOr(a.err, kErrTimeout);
                     return;
                 }
-                const unsigned char* bp = buf(b);
-                const T* wb = reinterpret_cast<const T*>(bp) + lane * RS;
+                unsigned char* bp = buf(b);
+                // the lane's row; with STAGE its source slots collect the results
+                T* wb = reinterpret_cast<T*>(bp) + lane * RS;
                 const T* ab = reinterpret_cast<const T*>(bp + SM::off_a) + 31 - lane;
                 const double* rb = reinterpret_cast<const double*>(bp + SM::off_r) + lane;
                 const T* ein = reinterpret_cast<const T*>(bp + SM::off_e);
@@ -686,10 +691,9 @@ sweep_kernel(const SweepArgs<T> a1, const SweepBatch<T> bt)
                         const T Inew = acc * rinv;
                         IW = Inew;
                         Iprev = Inew;
-                        if (DELTA)
-                            B::put(Ic + tt * dc, (wb[SM::W_IOLD * SM::WIN + tt] + wb[SM::W_SHIFT * SM::WIN + tt]) + Inew);
-                        else
-                            B::put(Ic + tt * dc, Inew);
+                        const T out = DELTA ? (wb[SM::W_IOLD * SM::WIN + tt] + wb[SM::W_SHIFT * SM::WIN + tt]) + Inew : Inew;
+                        if constexpr (STAGE) wb[SM::W_SRC * SM::WIN + tt] = out;   // the slot just read
+                        else B::put(Ic + tt * dc, out);
                         if (put_edge) B::store(ec + tt, Inew);
                     }
                 } else {
@@ -722,15 +726,31 @@ sweep_kernel(const SweepArgs<T> a1, const SweepBatch<T> bt)
                             acc = fma(bj, Isouth, acc);
                             Inew = acc * rinv;
                             IW = Inew;
-                            if (DELTA)
-                                B::put(Is + base0 + lane * dr + c * dc,
-                                       (wb[SM::W_IOLD * SM::WIN + tt] + wb[SM::W_SHIFT * SM::WIN + tt]) + Inew);
-                            else
-                                B::put(Is + base0 + lane * dr + c * dc, Inew);
+                            const T out =
+                                DELTA ? (wb[SM::W_IOLD * SM::WIN + tt] + wb[SM::W_SHIFT * SM::WIN + tt]) + Inew : Inew;
+                            if constexpr (STAGE) wb[SM::W_SRC * SM::WIN + tt] = out;
+                            else B::put(Is + base0 + lane * dr + c * dc, out);
                             if (put_edge) B::store(eo + c, Inew);
                         }
                         Iprev = Inew;
                     }
+                }
+                if constexpr (STAGE) {
+                    // write the chunk's results out row by row: RPI rows of SEG
+                    // consecutive cells per store instruction instead of one
+                    // cell of each of 32 rows
+                    __syncwarp();
+                    constexpr int RPI = 32 / SEG;
+                    const int kk = lane % SEG;
+                    const T* stage = reinterpret_cast<const T*>(bp);
+#pragma unroll 4
+                    for (int r0 = 0; r0 < 32; r0 += RPI) {
+                        const int r = r0 + lane / SEG;
+                        const int c = t0 + kk - r;
+                        if (band * 32 + r < ny && c >= 0 && c < nx)
+                            B::put(Is + base0 + r * dr + c * dc, stage[r * RS + kk]);
+                    }
+                    __syncwarp();
                 }
                 mbar_arrive(empty + b);
             }
