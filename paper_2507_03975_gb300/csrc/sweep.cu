@@ -665,15 +665,14 @@ sweep_kernel(const SweepArgs<T> a1, const SweepBatch<T> bt)
                     // interior chunk: every lane updates a cell at every step
                     T* Ic = Is + base0 + lane * dr + (t0 - lane) * dc;
                     T* ec = eo + (t0 - 31);
-#pragma unroll
-                    for (int tt = 0; tt < SEG; ++tt) {
-                        // lane l gets lane l-1's previous result; lane 0 the south value
-                        const T e = ein[tt];
-                        const T Isouth = __shfl_sync(kFull, lane == 31 ? e : Iprev, (lane + 31) & 31);
-                        T sv = wb[SM::W_SRC * SM::WIN + tt];
+                    // the step's source, column coefficient and 1/d depend only on
+                    // the chunk's data: they are formed one step ahead, so that
+                    // only the two upwind FMAs and the 1/d multiply wait on the
+                    // previous step
+                    auto operands = [&](int tt, T& sv, T& ai, T& rinv) {
+                        sv = wb[SM::W_SRC * SM::WIN + tt];
                         if (ADJ) sv = fma(cm, wb[SM::W_SHIFT * SM::WIN + tt], fma(ce, wb[SM::W_IOLD * SM::WIN + tt], cw * sv));
-                        const T ai = ab[tt];
-                        T rinv;
+                        ai = ab[tt];
                         if (PRE) {
                             if (PT) sv = fma(wb[SM::W_SHIFT * SM::WIN + tt], wb[SM::W_IOLD * SM::WIN + tt], sv);
                             rinv = (T)rb[tt * 32];
@@ -686,6 +685,16 @@ sweep_kernel(const SweepArgs<T> a1, const SweepBatch<T> bt)
                             }
                             rinv = rcp_t(d);
                         }
+                    };
+                    T sv_n, ai_n, rinv_n;
+                    operands(0, sv_n, ai_n, rinv_n);
+#pragma unroll
+                    for (int tt = 0; tt < SEG; ++tt) {
+                        const T sv = sv_n, ai = ai_n, rinv = rinv_n;
+                        if (tt + 1 < SEG) operands(tt + 1, sv_n, ai_n, rinv_n);
+                        // lane l gets lane l-1's previous result; lane 0 the south value
+                        const T e = ein[tt];
+                        const T Isouth = __shfl_sync(kFull, lane == 31 ? e : Iprev, (lane + 31) & 31);
                         T acc = fma(ai, IW, sv);
                         acc = fma(bj, Isouth, acc);
                         const T Inew = acc * rinv;
