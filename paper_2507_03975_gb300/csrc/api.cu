@@ -541,7 +541,7 @@ int gsis_solve(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis_op
             } else {
                 TIMED(GSIS_KCLASS_SWEEP, 1, launch_sweep(P, st));
             }
-            TIMED(GSIS_KCLASS_MOMENTS, 2,
+            TIMED(GSIS_KCLASS_MOMENTS, P.order == 2 ? 2 : 1,
                   launch_moments_to(P, gsis, false, P.rho_h, nullptr, nullptr, false, P.fb, false, st));
             if (gsis) {
                 TIMED(GSIS_KCLASS_HOT_RHS, 2, launch_hot_rhs(P, P.rho_h, P.Fx, P.Fy, P.fb, P.rho_m, st));
@@ -564,7 +564,7 @@ int gsis_solve(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis_op
         }
     }
     // outputs: rho^{m+1}; F and P of I^{m+1} from the intensities of the last sweep
-    TIMED(GSIS_KCLASS_MOMENTS, 2, launch_moments_to(P, true, P_out != nullptr, P.rho_h, F, P_out, gsis, P.fb, true, st));
+    TIMED(GSIS_KCLASS_MOMENTS, P.order == 2 ? 2 : 1, launch_moments_to(P, true, P_out != nullptr, P.rho_h, F, P_out, gsis, P.fb, true, st));
     CK(cudaMemcpyAsync(rho, P.rho_m, (size_t)P.N * sizeof(double), cudaMemcpyDeviceToDevice, st));
     if ((rc = read_status(S, P, st))) return rc;
     if (history && S.iter > 0)
@@ -603,7 +603,7 @@ int gsis_transport_sweep(const gsis_mesh* mesh, const gsis_quadrature* quad, con
     if ((rc = prepare(P, mesh, quad, &o, sigma_a, sigma_s, q, inflow, st))) return rc;
     TIMED(GSIS_KCLASS_SETUP, 1, launch_source_from(P, rho_in, st));
     TIMED(GSIS_KCLASS_SWEEP, 1, launch_sweep(P, st));
-    TIMED(GSIS_KCLASS_MOMENTS, 2, launch_moments_to(P, true, P_half != nullptr, rho_half, F_half, P_half, false,
+    TIMED(GSIS_KCLASS_MOMENTS, P.order == 2 ? 2 : 1, launch_moments_to(P, true, P_half != nullptr, rho_half, F_half, P_half, false,
                                                     bflux ? bflux : P.fb, true, st));
     return GSIS_OK;
 }
@@ -688,7 +688,7 @@ int gsis_adjoint(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis_
     CK(cudaMemcpyAsync(P.rho_m, rho_star, (size_t)P.N * sizeof(double), cudaMemcpyDeviceToDevice, st));
     TIMED(GSIS_KCLASS_SETUP, 1, launch_source_from(P, P.rho_m, st));
     TIMED(GSIS_KCLASS_SWEEP, 1, launch_sweep(P, st));
-    TIMED(GSIS_KCLASS_MOMENTS, 2, launch_moments_to(P, true, false, P.rho_h, nullptr, nullptr, false, P.fb, false, st));
+    TIMED(GSIS_KCLASS_MOMENTS, P.order == 2 ? 2 : 1, launch_moments_to(P, true, false, P.rho_h, nullptr, nullptr, false, P.fb, false, st));
     // lam = g (also the first right-hand side), nu = 0
     CK(cudaMemcpyAsync(P.lam, dJ_drho, (size_t)P.N * sizeof(double), cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(P.b, dJ_drho, (size_t)P.N * sizeof(double), cudaMemcpyDeviceToDevice, st));

@@ -903,6 +903,15 @@ __global__ void __launch_bounds__(256) bflux_kernel(const BfArgs<T> a)
     bflux_body(a, blockIdx.x, gridDim.x);
 }
 
+// Moments and boundary fluxes of one problem in one launch: the first
+// mblocks blocks take the cells, the rest the boundary faces.
+template <typename T, bool WITH_F, bool WITH_P>
+__global__ void __launch_bounds__(kRedBlock) moments_bflux_kernel(const MomArgs<T> m, const BfArgs<T> f, int mblocks)
+{
+    if ((int)blockIdx.x < mblocks) moments_body<T, WITH_F, WITH_P>(m, blockIdx.x, mblocks);
+    else bflux_body(f, blockIdx.x - mblocks, gridDim.x - mblocks);
+}
+
 // Batched moments and boundary fluxes: problem p owns blocks
 // [bstart[p], bstart[p + 1]); its first mblocks blocks take the cell moments,
 // the rest the boundary faces.
@@ -1055,6 +1064,15 @@ cudaError_t launch_moments_t(const Plan& P, bool with_F, bool with_P, double* rh
     a.done = force ? nullptr : &P.status->done;
     const size_t smem = moments_smem<T>(P.K);
     const int grid = grid_for(P.N, kRedBlock, P.num_sms * 8);
+    if (P.order != 2) {   // cells and boundary faces in one launch
+        static_assert(kRedBlock == 256, "the boundary-flux blocks take 256 threads");
+        const BfArgs<T> f = bflux_args<T>(P, fb_out, a.done);
+        const int fg = grid_for((long long)P.nbf * 32, 256, P.num_sms * 4);
+        if (with_P) moments_bflux_kernel<T, true, true><<<grid + fg, kRedBlock, smem, st>>>(a, f, grid);
+        else if (with_F) moments_bflux_kernel<T, true, false><<<grid + fg, kRedBlock, smem, st>>>(a, f, grid);
+        else moments_bflux_kernel<T, false, false><<<grid + fg, kRedBlock, smem, st>>>(a, f, grid);
+        return cudaGetLastError();
+    }
     if (with_P) moments_kernel<T, true, true><<<grid, kRedBlock, smem, st>>>(a);
     else if (with_F) moments_kernel<T, true, false><<<grid, kRedBlock, smem, st>>>(a);
     else moments_kernel<T, false, false><<<grid, kRedBlock, smem, st>>>(a);
@@ -1115,6 +1133,9 @@ cudaError_t prepare_t(int K)
     if ((e = raise_smem_limit((const void*)moments_kernel<T, true, false>, ms)) != cudaSuccess) return e;
     if ((e = raise_smem_limit((const void*)moments_kernel<T, false, false>, ms)) != cudaSuccess) return e;
     if ((e = raise_smem_limit((const void*)moments_batch_kernel<T, true, false>, ms)) != cudaSuccess) return e;
+    if ((e = raise_smem_limit((const void*)moments_bflux_kernel<T, true, true>, ms)) != cudaSuccess) return e;
+    if ((e = raise_smem_limit((const void*)moments_bflux_kernel<T, true, false>, ms)) != cudaSuccess) return e;
+    if ((e = raise_smem_limit((const void*)moments_bflux_kernel<T, false, false>, ms)) != cudaSuccess) return e;
     return raise_smem_limit((const void*)moments_batch_kernel<T, false, false>, ms);
 }
 

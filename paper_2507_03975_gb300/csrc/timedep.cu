@@ -275,7 +275,7 @@ int run_step(Plan& P, const gsis_time_params* tp, const gsis_options* opt, int g
         const int batch = std::min(opt->check_every, nmax - launched);
         for (int b = 0; b < batch; ++b) {
             TIMED(GSIS_KCLASS_SWEEP, 1, launch_sweep(P, st));
-            TIMED(GSIS_KCLASS_MOMENTS, 2,
+            TIMED(GSIS_KCLASS_MOMENTS, P.order == 2 ? 2 : 1,
                   launch_moments_to(P, gsis, false, P.rho_h, nullptr, nullptr, false, P.fb, false, st));
             if (gsis) {
                 TIMED(GSIS_KCLASS_HOT_RHS, 3, launch_td_coef_hot_rhs(P, a, g, st));
