@@ -131,7 +131,8 @@ def test_checkpoint_interval_does_not_change_the_gradient(gs):
 
 def test_full_size_directional_derivative(gs):
     """1024^2 S16 channel, cold start, two steps of dt = 1e-3, FP64 sweeps:
-    J = rho^2 summed over the channel cells next to the left wall."""
+    J = the sum of rho after the two steps over the channel cells next to
+    the left wall."""
     import torch
     p = W.config_timedep()
     td = W.TIMEDEP
@@ -162,3 +163,15 @@ def test_full_size_directional_derivative(gs):
     ad = float(ga @ delta)
     assert abs(fd - ad) <= 1e-4 * abs(ad), (fd, ad)
     del r
+
+
+def test_unconverged_forward_step_reports_maxiter(gs):
+    """A forward step that cannot reach the tolerance within max_iter stops
+    the call with GSIS_ERR_MAXITER (a status, not an exception)."""
+    name, make, tp, _ = CASES[0]
+    p = make()
+    rho0, T0, g_rho, g_T = _state(p, 9)
+    opt = gs.default_options(tol=1e-15, max_iter=2, check_every=1, synth_rtol=1e-14, synth_max_iter=3000,
+                             precision=gs.FP64)
+    r = _gpu(gs, p, tp, 2, rho0, T0, g_rho, g_T, opt, C=1)
+    assert r["status"] == gs.GSIS_ERR_MAXITER
