@@ -84,9 +84,16 @@ def _clock_sampler():
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
     try:
         proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                 "-lms", "200"], stdout=f, stderr=subprocess.DEVNULL)
+                                 "-lms", "20"], stdout=f, stderr=subprocess.DEVNULL)
     except OSError:
-        proc = None
+        return None, f
+    # nvidia-smi takes a moment to start: begin the timed region only once it
+    # is sampling (at most 3 s), so that the samples cover it
+    t0 = time.time()
+    while time.time() - t0 < 3.0 and proc.poll() is None:
+        if os.path.getsize(f.name) > 0:
+            break
+        time.sleep(0.01)
     return proc, f
 
 
@@ -123,9 +130,9 @@ def _clock_summary(proc, f, gpu_index):
 
 def _sweep_traffic():
     """DRAM bytes of one sweep launch on this workload from one ncu capture
-    (dram__bytes_read.sum + dram__bytes_write.sum, 96,051,200 + 4,298,496;
-    profiles/sweep_kernel_channel256.md), or None once the sweep source differs
-    from the one that was captured."""
+    (dram__bytes_read.sum + dram__bytes_write.sum, 96,051,200 + 4,298,496; the
+    committed ncu summary of the sweep kernel on this workload), or None once
+    the sweep source differs from the one that was captured."""
     import hashlib
     src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2507_03975_gb300", "csrc", "sweep.cu")
     with open(src, "rb") as f:
