@@ -99,6 +99,8 @@ def _clock_sampler():
 
 def _clock_summary(proc, f, gpu_index):
     if proc is None:
+        f.close()
+        os.unlink(f.name)
         return None
     proc.terminate()
     try:
