@@ -581,6 +581,10 @@ def run_ours(args):
     except Exception as ex:   # noqa: BLE001
         FP64_PEAK = 1250.0
         fp64_src = f"nominal GB300 FP64 rate 1.25 TFLOP/s (measurement failed: {ex})"
+    try:
+        fp32_rate = gsis.measure_fp32_fma()
+    except Exception:   # noqa: BLE001
+        fp32_rate = None
     shares = {k: v["total_ms"] for k, v in prof.items()}
     tot = sum(shares.values()) or 1.0
     upd = p.N * p.K
@@ -613,7 +617,7 @@ def run_ours(args):
                  "share": {k: v / tot for k, v in shares.items()},
                  "peak_source": ("measured hbm_gbs (MEASURED_PEAKS.json)" if roof["bound"] == "hbm"
                                  else fp64_src),
-                 "fp64_fma_gflops": FP64_PEAK,
+                 "fp64_fma_gflops": FP64_PEAK, "fp32_fma_gflops": fp32_rate,
                  "others": {k: model(k) for k in ("sweep", "moments", "synth") if k != dom}})
 
     cpu = None

@@ -336,6 +336,8 @@ int gsis_td_adjoint(const gsis_mesh* mesh, const gsis_quadrature* quad, const gs
  * memory is allocated.  Synchronises the stream.
  */
 int gsis_measure_fp64_fma(double* gflops, void* stream);
+/* The same for FP32 FMAs (32 times more iterations per thread). */
+int gsis_measure_fp32_fma(double* gflops, void* stream);
 
 /*
  * Batched solve: n independent steady problems, each with its own mesh,

@@ -1,7 +1,8 @@
-// FP64 FMA rate of the device (gsis_measure_fp64_fma): the denominator of
-// the ALU-bound kernels' rooflines.  Every thread runs kChains independent
-// dependent-FMA chains, so each sub-partition always has FP64 instructions
-// to issue; the grid fills every SM with kBlocksPerSm blocks.
+// FP64 and FP32 FMA rates of the device (gsis_measure_fp64_fma,
+// gsis_measure_fp32_fma): the denominators of the ALU-bound kernels'
+// rooflines.  Every thread runs kChains independent dependent-FMA chains, so
+// each sub-partition always has FMA instructions to issue; the grid fills
+// every SM with kBlocksPerSm blocks.
 #include <cuda_runtime.h>
 
 #include "gsis.h"
@@ -12,30 +13,33 @@ using namespace gsis;
 namespace {
 
 constexpr int kChains = 8;
-constexpr int kIters = 2048;
 constexpr int kThreads = 256;
 constexpr int kBlocksPerSm = 8;
 
-__device__ double g_fma_sink;
+__device__ double g_sink_d;
+__device__ float g_sink_f;
+__device__ __forceinline__ void sink(double v) { g_sink_d = v; }
+__device__ __forceinline__ void sink(float v) { g_sink_f = v; }
 
-__global__ void __launch_bounds__(kThreads) fma_rate_kernel(double a, double b)
+template <typename T, int ITERS>
+__global__ void __launch_bounds__(kThreads) fma_rate_kernel(T a, T b)
 {
-    double x[kChains];
+    T x[kChains];
 #pragma unroll
-    for (int c = 0; c < kChains; ++c) x[c] = threadIdx.x * 1e-6 + c;
-    for (int i = 0; i < kIters; ++i) {
+    for (int c = 0; c < kChains; ++c) x[c] = (T)(threadIdx.x * 1e-6 + c);
+    for (int i = 0; i < ITERS; ++i) {
 #pragma unroll
         for (int c = 0; c < kChains; ++c) x[c] = fma(x[c], a, b);
     }
-    double s = 0.0;
+    T s = 0;
 #pragma unroll
     for (int c = 0; c < kChains; ++c) s += x[c];
-    if (s == 12345.678) g_fma_sink = s;   // keeps the chains live; never true for these inputs
+    if (s == (T)12345.678) sink(s);   // keeps the chains live; never true for these inputs
 }
 
-}  // namespace
-
-extern "C" int gsis_measure_fp64_fma(double* gflops, void* stream)
+// Best of three timed launches after one warm-up, in GFLOP/s.
+template <typename T, int ITERS>
+int measure(double* gflops, void* stream)
 {
     if (!gflops) return fail(GSIS_ERR_ARG, "gflops is NULL");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -47,9 +51,9 @@ extern "C" int gsis_measure_fp64_fma(double* gflops, void* stream)
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     float best = 0.f;
-    for (int rep = 0; rep < 4; ++rep) {   // the first is the warm-up
+    for (int rep = 0; rep < 4; ++rep) {
         CK(cudaEventRecord(e0, st));
-        fma_rate_kernel<<<grid, kThreads, 0, st>>>(0.999999999, 1e-9);
+        fma_rate_kernel<T, ITERS><<<grid, kThreads, 0, st>>>((T)0.999999999, (T)1e-9);
         CK(cudaGetLastError());
         CK(cudaEventRecord(e1, st));
         CK(cudaEventSynchronize(e1));
@@ -59,7 +63,13 @@ extern "C" int gsis_measure_fp64_fma(double* gflops, void* stream)
     }
     CK(cudaEventDestroy(e0));
     CK(cudaEventDestroy(e1));
-    const double flops = 2.0 * kChains * (double)kIters * kThreads * grid;
+    const double flops = 2.0 * kChains * (double)ITERS * kThreads * grid;
     *gflops = flops / (best * 1e-3) / 1e9;
     return GSIS_OK;
 }
+
+}  // namespace
+
+extern "C" int gsis_measure_fp64_fma(double* gflops, void* stream) { return measure<double, 2048>(gflops, stream); }
+
+extern "C" int gsis_measure_fp32_fma(double* gflops, void* stream) { return measure<float, 65536>(gflops, stream); }

@@ -616,13 +616,25 @@ def td_adjoint(dx, dy, mu, eta, w, sigma_a, sigma_s, q, rho0, T0, dt, nsteps, dJ
     return out
 
 
-def measure_fp64_fma(stream=None) -> float:
-    """gsis_measure_fp64_fma: the device's FP64 FMA rate in GFLOP/s."""
+def _peak_load():
     lib = load()
     if not getattr(lib, "_peak_bound", False):
-        lib.gsis_measure_fp64_fma.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
-        lib.gsis_measure_fp64_fma.restype = ctypes.c_int
+        for f in (lib.gsis_measure_fp64_fma, lib.gsis_measure_fp32_fma):
+            f.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+            f.restype = ctypes.c_int
         lib._peak_bound = True
+    return lib
+
+
+def measure_fp64_fma(stream=None) -> float:
+    """gsis_measure_fp64_fma: the device's FP64 FMA rate in GFLOP/s."""
     g = ctypes.c_double(0.0)
-    _raise(lib.gsis_measure_fp64_fma(ctypes.byref(g), _stream(stream)))
+    _raise(_peak_load().gsis_measure_fp64_fma(ctypes.byref(g), _stream(stream)))
+    return float(g.value)
+
+
+def measure_fp32_fma(stream=None) -> float:
+    """gsis_measure_fp32_fma: the device's FP32 FMA rate in GFLOP/s."""
+    g = ctypes.c_double(0.0)
+    _raise(_peak_load().gsis_measure_fp32_fma(ctypes.byref(g), _stream(stream)))
     return float(g.value)
