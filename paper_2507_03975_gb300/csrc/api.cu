@@ -203,6 +203,7 @@ size_t layout(const Sizes& z, char* base, Plan* P)
             p.sigt_d = reinterpret_cast<float*>(take(N * sizeof(float)));
         }
     }
+    if (z.ordsrc) p.X = reinterpret_cast<double*>(take(K * N * sizeof(double)));
     if (z.td) {
         p.In = take(K * N * Ts);
         double** td[] = {&p.td.rho_n, &p.td.T_n, &p.td.T, &p.td.cn, &p.td.cnext, &p.td.qeff, &p.td.diag0};
@@ -376,6 +377,13 @@ Sizes sizes_of(const gsis_mesh* m, const gsis_quadrature* q, const gsis_options*
     return z;
 }
 
+Sizes solve_sizes(const gsis_mesh* m, const gsis_quadrature* q, const gsis_options* o)
+{
+    Sizes z = sizes_of(m, q, o);
+    z.ordsrc = (o->cfl_p > 0.0 || o->beta > 0.0) && o->precision == GSIS_FP64 && o->spatial_order == 1;
+    return z;
+}
+
 }  // namespace gsis
 
 void gsis::set_last_error(int code, const char* msg)
@@ -505,7 +513,7 @@ int gsis_workspace_bytes(const gsis_mesh* mesh, const gsis_quadrature* quad, con
     int rc;
     if ((rc = check_mesh(mesh)) || (quad && (rc = check_quad(quad))) || (rc = check_opt(opt))) return rc;
     if (!bytes) return fail(GSIS_ERR_ARG, "bytes is NULL");
-    *bytes = layout(sizes_of(mesh, quad, opt), nullptr, nullptr);
+    *bytes = layout(solve_sizes(mesh, quad, opt), nullptr, nullptr);
     return GSIS_OK;
 }
 
@@ -518,13 +526,14 @@ int gsis_solve(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis_op
     int rc;
     if ((rc = check_mesh(mesh)) || (rc = check_quad(quad)) || (rc = check_opt(opt))) return rc;
     if (!sigma_a || !sigma_s || !q || !rho || !F) return fail(GSIS_ERR_ARG, "a required device pointer is NULL");
-    const Sizes z = sizes_of(mesh, quad, opt);
+    const Sizes z = solve_sizes(mesh, quad, opt);
     if ((rc = check_ws(workspace, workspace_bytes, layout(z, nullptr, nullptr)))) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Plan P{};
     layout(z, static_cast<char*>(workspace), &P);
     if ((rc = prepare(P, mesh, quad, opt, sigma_a, sigma_s, q, inflow, st))) return rc;
     TIMED(GSIS_KCLASS_SETUP, P.pt ? 4 : 3, launch_init_state(P, st));
+    if (P.X) TIMED(GSIS_KCLASS_SETUP, 1, launch_ordinate_source(P, st));
     Status S{};
     if ((rc = read_status(S, P, st))) return rc;
 
@@ -550,6 +559,7 @@ int gsis_solve(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis_op
             } else {
                 TIMED(GSIS_KCLASS_UPDATE, 1, launch_update(P, P.rho_h, st));
             }
+            if (P.X) TIMED(GSIS_KCLASS_UPDATE, 1, launch_ordinate_source(P, st));
         }
         launched += batch;
         if ((rc = read_status(S, P, st))) return rc;

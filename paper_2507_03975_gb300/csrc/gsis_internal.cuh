@@ -102,6 +102,7 @@ struct Plan {
     double* sigt; float* sigt_f;
     double* shift; float* shift_f;
     double* src; float* src_f;      // source of the next sweep (with pseudo-time correction)
+    double* X;                      // [K][N] FP64 pseudo-time solve: src + shift I^m per ordinate (or null)
     double* rho_m;                  // rho^m
     double* rho_h;                  // rho^{m+1/2}
     double* Fx; double* Fy; double* fb;
@@ -165,6 +166,9 @@ cudaError_t plan_synthetic(Plan& P);   // before the first solve launch (no runt
 cudaError_t launch_synthetic_solve(const Plan& P, const double* guess, double* out, cudaStream_t st);
 int mg_cluster_size();
 cudaError_t launch_update(const Plan& P, const double* rho_new, cudaStream_t st);
+// X = src + shift I per ordinate from the current src and I (after every
+// update of the FP64 pseudo-time solve; skipped once the solve has stopped).
+cudaError_t launch_ordinate_source(const Plan& P, cudaStream_t st);
 // second-order upwind (csrc/uw2.cu, sweep in csrc/sweep.cu)
 cudaError_t launch_uw2_residual(const Plan& P, cudaStream_t st);     // R from I + corr and the source
 cudaError_t launch_delta_sweep(Plan& P, cudaStream_t st);           // I <- I + corr + dI

@@ -44,6 +44,7 @@ struct ProfScope {
 
 struct Sizes {
     int nx, ny, K, fp32, hist, adjoint, td, order;
+    int ordsrc;   // the per-ordinate source array of the FP64 pseudo-time solve
 };
 
 // Carves one problem's workspace (base may be null: size query only).
@@ -59,6 +60,9 @@ int prepare(Plan& P, const gsis_mesh* mesh, const gsis_quadrature* quad, const g
 // Copies the status block back (synchronising st) and maps device error bits.
 int read_status(Status& S, const Plan& P, cudaStream_t st);
 Sizes sizes_of(const gsis_mesh* m, const gsis_quadrature* q, const gsis_options* o);
+// The sizes of gsis_solve: with the FP64 pseudo-time form, also the
+// per-ordinate source of the sweep.
+Sizes solve_sizes(const gsis_mesh* m, const gsis_quadrature* q, const gsis_options* o);
 // All spacings equal (relative 1e-12).
 bool uniform_spacing(const double* h, int n);
 // Sorted index (quadrant-major, as in prepare) of the reflected direction

@@ -229,6 +229,7 @@ struct SweepArgs {
     const T* acoef; const T* bcoef;
     const double* rsw;
     const T* sigt; const T* shift; const T* src;
+    int src_stride;             // elements between ordinates' sources (0: one per-cell source for all)
     const T* iold;              // stored intensities of the delta form: I^m (pseudo-time) or I^n (time step)
     const T* ax; const T* ay;   // adjoint source: bx, by (src holds a)
     const double* qw;           // sorted weights (adjoint source)
@@ -515,7 +516,7 @@ sweep_kernel(const SweepArgs<T> a1, const SweepBatch<T> bt)
         if (copier) {
             // ---------------------------------------------------- copy warp
             const T* wsrc[NW];
-            wsrc[SM::W_SRC] = a.src;
+            wsrc[SM::W_SRC] = a.src + (size_t)s * a.src_stride;
             if (!PRE) wsrc[SM::W_SIGT] = a.sigt;
             if (PT) {
                 wsrc[SM::W_SHIFT] = a.shift;
@@ -1220,6 +1221,17 @@ cudaError_t launch_source_from(const Plan& P, const double* rho_in, cudaStream_t
 
 cudaError_t launch_sweep(Plan& P, cudaStream_t st)
 {
+    if (P.pt && P.X && !P.fp32) {
+        // FP64 pseudo-time form with its source already combined per ordinate
+        // (X = src + shift I^m, formed by the update kernel): the plain sweep
+        // over X takes one FP64 operation per update fewer, same bits
+        SweepArgs<double> a = sweep_args<double, kSrcPlain>(P);
+        a.src = P.X;
+        a.src_stride = P.N;
+        sweep_kernel<double, kSrcPlain, true, false>
+            <<<P.sweep_grid, kSweepPairs * 64, sweep_smem<double, kSrcPlain>(), st>>>(a, SweepBatch<double>{});
+        return cudaGetLastError();
+    }
     if (P.fp32) {
         return P.pt ? launch_sweep_t<float, kSrcPseudoTime, false>(P, st)
                     : launch_sweep_t<float, kSrcPlain, false>(P, st);

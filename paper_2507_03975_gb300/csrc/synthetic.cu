@@ -15,6 +15,8 @@
 //  * Err(rho) (Eq. (Err_W)), convergence decision, next angular source.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include <cstring>
 
 #include "gsis_internal.cuh"
@@ -179,6 +181,7 @@ __device__ __forceinline__ void update_body(const UpdArgs& a, int bid, int nblk)
         if (a.pt) s = fma(a.shift[c] * (nw - a.rho_h[c]), kInvFourPi, s);
         a.src[c] = s;
         if (a.src_f) a.src_f[c] = (float)s;
+
         if (a.corr) {   // I^{m+1} = I^{m+1/2} + (rho^{m+1} - rho^{m+1/2})/4pi, kept per cell
             const double cc = (nw - a.rho_h[c]) * kInvFourPi;
             a.corr[c] = cc;
@@ -235,6 +238,7 @@ UpdArgs upd_args(const Plan& P, const double* rho_new)
     a.pt = P.pt && P.order == 1;   // second order: the correction is carried explicitly
     a.corr = P.order == 2 ? P.corr : nullptr;
     a.corr_f = P.order == 2 && P.fp32 ? P.corr_f : nullptr;
+
     a.tol = P.tol; a.fixed_iters = P.fixed_iters; a.max_iter = P.max_iter;
     a.partials = P.partials + (size_t)9 * kMaxCgBlocks;
     a.hist = P.hist;
@@ -252,6 +256,26 @@ cudaError_t launch_hot_rhs(const Plan& P, const double* rho_h, const double* Fx,
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     rhs_kernel<<<P.red_grid, kRedBlock, 0, st>>>(rhs_args(P, rho_h, fb, guess));
+    return cudaGetLastError();
+}
+
+// The FP64 pseudo-time sweep's source per ordinate, formed as that sweep
+// would form it: X[k][c] = fma(shift_c, I[k][c], src_c).
+__global__ void ordinate_source_kernel(int N, int K, const double* __restrict__ shift,
+                                       const double* __restrict__ I, const double* __restrict__ src, double* X,
+                                       const int* done)
+{
+    if (ld_volatile_int(done)) return;
+    const size_t row = (size_t)blockIdx.y * N;   // ordinate blockIdx.y
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x)
+        X[row + c] = fma(shift[c], I[row + c], src[c]);
+}
+
+cudaError_t launch_ordinate_source(const Plan& P, cudaStream_t st)
+{
+    const dim3 grid(grid_for(P.N, 256, std::max(1, P.num_sms * 16 / P.K)), P.K);
+    ordinate_source_kernel<<<grid, 256, 0, st>>>(
+        P.N, P.K, P.shift, static_cast<const double*>(P.I), P.src, P.X, &P.status->done);
     return cudaGetLastError();
 }
 
