@@ -50,7 +50,7 @@ def _workload(args=None):
                    synthetic=f"FP64 iterative refinement, FP32 multigrid-CG inner iterations capped at {cap} "
                              "per GSIS iteration (warm-started; same fixed point)" if cap > 0 else
                              "solved to relative residual 1e-12",
-                   l2="flushed before each step (512 MiB write); per-solve working set ~105 MB",
+                   l2="flushed before each step (512 MiB write); per-solve working set ~149 MB",
                    kernel_timing="a second pass of the same solves with CUDA events around every kernel "
                                  "class (roofline, shares); value and ms_per_step from the uninstrumented pass")
 
