@@ -274,8 +274,10 @@ __global__ void ordinate_source_kernel(int N, int K, const double* __restrict__ 
 cudaError_t launch_ordinate_source(const Plan& P, cudaStream_t st)
 {
     const dim3 grid(grid_for(P.N, 256, std::max(1, P.num_sms * 16 / P.K)), P.K);
-    ordinate_source_kernel<<<grid, 256, 0, st>>>(
-        P.N, P.K, P.shift, static_cast<const double*>(P.I), P.src, P.X, &P.status->done);
+    // the stored intensities the pseudo-time sweep reads: I^m in place, or a
+    // time step's I^n
+    const double* iold = static_cast<const double*>(P.In ? P.In : P.I);
+    ordinate_source_kernel<<<grid, 256, 0, st>>>(P.N, P.K, P.shift, iold, P.src, P.X, &P.status->done);
     return cudaGetLastError();
 }
 
