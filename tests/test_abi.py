@@ -154,3 +154,17 @@ def test_td_adjoint_binding_rejects_before_device_use(gs):
     rc = lib.gsis_td_adjoint(ctypes.byref(a.mesh), ctypes.byref(a.quad), ctypes.byref(gs.default_options()),
                              ctypes.byref(tp), 2, *([dummy] * 14), its, None, ctypes.c_size_t(0), None)
     assert rc == gs.GSIS_ERR_WORKSPACE
+
+
+def test_mesh_size_limits(gs):
+    """Sides above 2^20 - 1 cells and meshes above 2^30 cells are rejected on
+    the host (GSIS_ERR_ARG) before anything is sized or launched; the largest
+    side is accepted."""
+    mu, eta, w = gs.quadrature_level_symmetric(4)
+    big = (1 << 20) - 1
+    ok = gs.workspace_bytes(np.full(big, 1.0 / big), np.full(1, 1.0), mu, eta, w)
+    assert ok > 0
+    for nx, ny in ((big + 1, 1), ((1 << 15) + 1, (1 << 15) + 1)):
+        with pytest.raises(gs.GsisError) as e:
+            gs.workspace_bytes(np.full(nx, 1.0 / nx), np.full(ny, 1.0 / ny), mu, eta, w)
+        assert e.value.status == gs.GSIS_ERR_ARG
