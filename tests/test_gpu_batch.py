@@ -52,8 +52,8 @@ def rel(a, b):
 
 def _mixed():
     # uneven sizes and orders; ragged bands; problems too small for the strip
-    # solver (their synthetic solve is launched on its own); one cell; inflow
-    # on some, vacuum on others
+    # solver (their synthetic solve is launched on its own); one cell, one row,
+    # one column; inflow on some, vacuum on others
     return [
         W.random_problem(16, 12, order=4, seed=1),
         W.random_problem(40, 33, order=6, seed=2, with_inflow=False),
@@ -61,6 +61,8 @@ def _mixed():
         W.random_problem(70, 45, order=8, seed=4),
         W.random_problem(33, 97, order=6, seed=5, nonuniform=False),
         W.random_problem(1, 1, order=4, seed=6),
+        W.random_problem(37, 1, order=6, seed=7),     # one row
+        W.random_problem(1, 45, order=4, seed=8),     # one column
         W.channel_problem(64, 8, 2, width=2, sigma_bulk=200.0),
     ]
 
