@@ -275,9 +275,10 @@ def timedep_measure(gsis, torch, stream, hbm):
     run("si_fp32", gsis.SCHEME_SI, gsis.FP32_SWEEP, 1e-6)
     ws = None   # the FP64 layout is larger
     run("gsis_fp64", gsis.SCHEME_GSIS, gsis.FP64, 1e-8)
-    # roofline of the time-step sweep (FP32 delta form): read I^n and write I
-    # (4 + 4 B per update) plus src, sigma_t, shift (FP32) once per cell
-    algo = 8.0 * upd + 12.0 * p.N
+    # roofline of the time-step sweep (FP32): read its per-ordinate source
+    # X = src + I^n/(c dt) and write I (4 + 4 B per update) plus its diagonal
+    # sigma_t + 1/(c dt) (FP32) once per cell
+    algo = 8.0 * upd + 4.0 * p.N
     ach = algo / (prof["sweep_ms_avg"] * 1e-3) / 1e9
     out["sweep_roofline"] = {"bound": "hbm", "kernel": "sweep (fp32, time step)", "achieved": ach, "peak": hbm,
                              "unit": "GB/s", "frac": ach / hbm, "traffic": None, "algorithmic_bytes": algo,

@@ -203,7 +203,14 @@ size_t layout(const Sizes& z, char* base, Plan* P)
             p.sigt_d = reinterpret_cast<float*>(take(N * sizeof(float)));
         }
     }
-    if (z.ordsrc) p.X = reinterpret_cast<double*>(take(K * N * sizeof(double)));
+    if (z.ordsrc) {   // the sweep's source per ordinate (FP32: with its diagonal sigma_t + shift)
+        if (z.fp32) {
+            p.X_f = reinterpret_cast<float*>(take(K * N * sizeof(float)));
+            if (!p.sigt_d) p.sigt_d = reinterpret_cast<float*>(take(N * sizeof(float)));
+        } else {
+            p.X = reinterpret_cast<double*>(take(K * N * sizeof(double)));
+        }
+    }
     if (z.td) {
         p.In = take(K * N * Ts);
         double** td[] = {&p.td.rho_n, &p.td.T_n, &p.td.T, &p.td.cn, &p.td.cnext, &p.td.qeff, &p.td.diag0};

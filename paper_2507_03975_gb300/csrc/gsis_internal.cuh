@@ -103,6 +103,7 @@ struct Plan {
     double* shift; float* shift_f;
     double* src; float* src_f;      // source of the next sweep (with pseudo-time correction)
     double* X;                      // [K][N] FP64 pseudo-time solve: src + shift I^m per ordinate (or null)
+    float* X_f;                     // [K][N] FP32 time step: src + I^n/(c dt) per ordinate (or null)
     double* rho_m;                  // rho^m
     double* rho_h;                  // rho^{m+1/2}
     double* Fx; double* Fy; double* fb;

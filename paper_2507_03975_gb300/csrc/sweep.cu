@@ -1232,6 +1232,18 @@ cudaError_t launch_sweep(Plan& P, cudaStream_t st)
             <<<P.sweep_grid, kSweepPairs * 64, sweep_smem<double, kSrcPlain>(), st>>>(a, SweepBatch<double>{});
         return cudaGetLastError();
     }
+    if (P.fp32 && P.pt && P.X_f) {
+        // FP32 time step with its source combined per ordinate (X = src +
+        // I^n/(c dt)) and its diagonal sigma_t + 1/(c dt): the plain sweep
+        // over X reads two cell windows instead of four
+        SweepArgs<float> a = sweep_args<float, kSrcPlain>(P);
+        a.src = P.X_f;
+        a.src_stride = P.N;
+        a.sigt = P.sigt_d;
+        sweep_kernel<float, kSrcPlain, false, false>
+            <<<P.sweep_grid, kSweepPairs * 64, sweep_smem<float, kSrcPlain>(), st>>>(a, SweepBatch<float>{});
+        return cudaGetLastError();
+    }
     if (P.fp32) {
         return P.pt ? launch_sweep_t<float, kSrcPseudoTime, false>(P, st)
                     : launch_sweep_t<float, kSrcPlain, false>(P, st);

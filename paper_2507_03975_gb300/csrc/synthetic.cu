@@ -259,11 +259,11 @@ cudaError_t launch_hot_rhs(const Plan& P, const double* rho_h, const double* Fx,
     return cudaGetLastError();
 }
 
-// The FP64 pseudo-time sweep's source per ordinate, formed as that sweep
-// would form it: X[k][c] = fma(shift_c, I[k][c], src_c).
-__global__ void ordinate_source_kernel(int N, int K, const double* __restrict__ shift,
-                                       const double* __restrict__ I, const double* __restrict__ src, double* X,
-                                       const int* done)
+// The pseudo-time / time-step sweep's source per ordinate, formed as that
+// sweep would form it: X[k][c] = fma(shift_c, I[k][c], src_c) (FP64 or FP32).
+template <typename T>
+__global__ void ordinate_source_kernel(int N, const T* __restrict__ shift, const T* __restrict__ I,
+                                       const T* __restrict__ src, T* X, const int* done)
 {
     if (ld_volatile_int(done)) return;
     const size_t row = (size_t)blockIdx.y * N;   // ordinate blockIdx.y
@@ -276,8 +276,13 @@ cudaError_t launch_ordinate_source(const Plan& P, cudaStream_t st)
     const dim3 grid(grid_for(P.N, 256, std::max(1, P.num_sms * 16 / P.K)), P.K);
     // the stored intensities the pseudo-time sweep reads: I^m in place, or a
     // time step's I^n
-    const double* iold = static_cast<const double*>(P.In ? P.In : P.I);
-    ordinate_source_kernel<<<grid, 256, 0, st>>>(P.N, P.K, P.shift, iold, P.src, P.X, &P.status->done);
+    const void* iold = P.In ? P.In : P.I;
+    if (P.fp32)
+        ordinate_source_kernel<float><<<grid, 256, 0, st>>>(P.N, P.shift_f, static_cast<const float*>(iold),
+                                                            P.src_f, P.X_f, &P.status->done);
+    else
+        ordinate_source_kernel<double><<<grid, 256, 0, st>>>(P.N, P.shift, static_cast<const double*>(iold),
+                                                             P.src, P.X, &P.status->done);
     return cudaGetLastError();
 }
 

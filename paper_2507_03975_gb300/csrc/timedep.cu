@@ -236,7 +236,7 @@ Sizes td_sizes(const gsis_mesh* m, const gsis_quadrature* q, const gsis_options*
 {
     Sizes z = sizes_of(m, q, o);
     z.td = 1;
-    z.ordsrc = o->precision == GSIS_FP64;   // FP64: the sweep's source src + I^n/(c dt) per ordinate
+    z.ordsrc = 1;   // the sweep's source src + I^n/(c dt) per ordinate
     return z;
 }
 
@@ -271,7 +271,7 @@ int run_step(Plan& P, const gsis_time_params* tp, const gsis_options* opt, int g
     }
     td_source_kernel<<<g, kRedBlock, 0, st>>>(a);
     CK(cudaGetLastError());
-    if (P.X) CK(launch_ordinate_source(P, st));
+    if (P.X || P.X_f) CK(launch_ordinate_source(P, st));
     int launched = 0;
     while (launched < nmax) {
         const int batch = std::min(opt->check_every, nmax - launched);
@@ -284,7 +284,7 @@ int run_step(Plan& P, const gsis_time_params* tp, const gsis_options* opt, int g
                 TIMED(GSIS_KCLASS_SYNTH, 1, launch_synthetic_solve(P, P.rho_m, P.x, st));
             }
             TIMED(GSIS_KCLASS_UPDATE, 1, launch_td_update(P, a, st));
-            if (P.X) TIMED(GSIS_KCLASS_UPDATE, 1, launch_ordinate_source(P, st));
+            if (P.X || P.X_f) TIMED(GSIS_KCLASS_UPDATE, 1, launch_ordinate_source(P, st));
         }
         launched += batch;
         if ((rc = read_status(S, P, st))) return rc;
