@@ -387,7 +387,7 @@ Sizes sizes_of(const gsis_mesh* m, const gsis_quadrature* q, const gsis_options*
 Sizes solve_sizes(const gsis_mesh* m, const gsis_quadrature* q, const gsis_options* o)
 {
     Sizes z = sizes_of(m, q, o);
-    z.ordsrc = (o->cfl_p > 0.0 || o->beta > 0.0) && o->precision == GSIS_FP64 && o->spatial_order == 1;
+    z.ordsrc = (o->cfl_p > 0.0 || o->beta > 0.0) && o->spatial_order == 1;
     return z;
 }
 
@@ -540,7 +540,7 @@ int gsis_solve(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis_op
     layout(z, static_cast<char*>(workspace), &P);
     if ((rc = prepare(P, mesh, quad, opt, sigma_a, sigma_s, q, inflow, st))) return rc;
     TIMED(GSIS_KCLASS_SETUP, P.pt ? 4 : 3, launch_init_state(P, st));
-    if (P.X) TIMED(GSIS_KCLASS_SETUP, 1, launch_ordinate_source(P, st));
+    if (P.X || P.X_f) TIMED(GSIS_KCLASS_SETUP, 1, launch_ordinate_source(P, st));
     Status S{};
     if ((rc = read_status(S, P, st))) return rc;
 
@@ -566,7 +566,7 @@ int gsis_solve(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis_op
             } else {
                 TIMED(GSIS_KCLASS_UPDATE, 1, launch_update(P, P.rho_h, st));
             }
-            if (P.X) TIMED(GSIS_KCLASS_UPDATE, 1, launch_ordinate_source(P, st));
+            if (P.X || P.X_f) TIMED(GSIS_KCLASS_UPDATE, 1, launch_ordinate_source(P, st));
         }
         launched += batch;
         if ((rc = read_status(S, P, st))) return rc;

@@ -45,7 +45,7 @@ size_t al(size_t b) { return (b + kAlign - 1) / kAlign * kAlign; }
 // problem's own gsis_solve workspace.
 struct Header {
     size_t bstatus, statuses, sweep, seg_start, seg_prob, seg_band, mom, mom_bs, hot, hot_bs, rhs, rhs_bs, upd,
-        upd_bs, strip, total;
+        upd_bs, ord, ord_bs, strip, total;
 };
 
 Header header_layout(int B, int nseg, int fp32)
@@ -72,6 +72,8 @@ Header header_layout(int B, int nseg, int fp32)
     h.rhs_bs = take(bs);
     h.upd = take((size_t)B * upd_batch_rec_bytes());
     h.upd_bs = take(bs);
+    h.ord = take((size_t)B * ord_batch_rec_bytes());
+    h.ord_bs = take(bs);
     h.strip = take((size_t)B * strip_batch_rec_bytes());
     h.total = off;
     return h;
@@ -84,7 +86,7 @@ struct Group {
 };
 
 struct Batch {
-    int B = 0, nseg = 0, fp32 = 0, pt = 0;
+    int B = 0, nseg = 0, fp32 = 0, pt = 0, ordsrc = 0;
     bool gsis = false;
     char* base = nullptr;
     Header h{};
@@ -122,10 +124,20 @@ int total_segments(const gsis_problem* probs, int n)
     return (int)s;
 }
 
+// A problem's arrays: gsis_solve's, except that FP64 pseudo-time sweeps keep
+// forming src + shift I^m inside the batched sweep (the same bits as the
+// single solve's per-ordinate source), so only FP32 plans get X.
+Sizes batch_sizes(const gsis_problem& q, const gsis_options* opt)
+{
+    Sizes z = solve_sizes(&q.mesh, &q.quad, opt);
+    if (!z.fp32) z.ordsrc = 0;
+    return z;
+}
+
 size_t batch_bytes(const gsis_problem* probs, int n, const gsis_options* opt)
 {
     size_t tot = header_layout(n, total_segments(probs, n), opt->precision == GSIS_FP32_SWEEP).total;
-    for (int p = 0; p < n; ++p) tot += al(layout(sizes_of(&probs[p].mesh, &probs[p].quad, opt), nullptr, nullptr));
+    for (int p = 0; p < n; ++p) tot += al(layout(batch_sizes(probs[p], opt), nullptr, nullptr));
     return tot;
 }
 
@@ -147,7 +159,7 @@ int batch_setup(Batch& b, const gsis_problem* probs, int n, const gsis_options* 
     size_t off = b.h.total;
     for (int p = 0; p < n; ++p) {
         const gsis_problem& q = probs[p];
-        const Sizes z = sizes_of(&q.mesh, &q.quad, opt);
+        const Sizes z = batch_sizes(q, opt);
         layout(z, b.base + off, &b.P[p]);
         off += al(layout(z, nullptr, nullptr));
         b.P[p].status = b.statuses + p;   // all status blocks side by side: one read per check
@@ -156,8 +168,10 @@ int batch_setup(Batch& b, const gsis_problem* probs, int n, const gsis_options* 
         // synthetic solves run on concurrent branches: no grid-wide (every-SM) solver here
         b.P[p].synth_grid = 0;
         CK(launch_init_state(b.P[p], st));
+        if (b.P[p].X_f) CK(launch_ordinate_source(b.P[p], st));
     }
     b.pt = b.P[0].pt;
+    b.ordsrc = b.P[0].X_f != nullptr;   // FP32 pseudo-time sweeps over per-ordinate sources
     CK(cudaMemsetAsync(b.bstatus, 0, sizeof(Status), st));
     return GSIS_OK;
 }
@@ -167,7 +181,10 @@ int batch_restart(Batch& b, cudaStream_t st)
 {
     CK(cudaMemsetAsync(b.statuses, 0, (size_t)b.B * sizeof(Status), st));
     CK(cudaMemsetAsync(b.bstatus, 0, sizeof(Status), st));
-    for (int p = 0; p < b.B; ++p) CK(launch_init_state(b.P[p], st));
+    for (int p = 0; p < b.B; ++p) {
+        CK(launch_init_state(b.P[p], st));
+        if (b.P[p].X_f) CK(launch_ordinate_source(b.P[p], st));
+    }
     return GSIS_OK;
 }
 
@@ -255,6 +272,10 @@ int batch_tables(Batch& b, const gsis_batch_tuning& t, cudaStream_t st)
                                   [&](const Plan& P, void* o) { return rhs_batch_rec(P, o); });
     const int upd_blocks = blocks(h.upd, upd_batch_rec_bytes(), h.upd_bs,
                                   [&](const Plan& P, void* o) { return upd_batch_rec(P, gsis, o); });
+    // FP32 pseudo-time: the next sweeps' per-ordinate sources after every update
+    const int ord_blocks = b.ordsrc ? blocks(h.ord, ord_batch_rec_bytes(), h.ord_bs,
+                                             [&](const Plan& P, void* o) { return ord_batch_rec(P, o); })
+                                    : 0;
 
     // synthetic: problems grouped by cluster size, one table run per group
     b.groups.clear();
@@ -317,6 +338,9 @@ int batch_tables(Batch& b, const gsis_batch_tuning& t, cudaStream_t st)
     bt.upd = b.base + h.upd;
     bt.upd_bstart = reinterpret_cast<const int*>(b.base + h.upd_bs);
     bt.upd_blocks = upd_blocks;
+    bt.ord = b.base + h.ord;
+    bt.ord_bstart = reinterpret_cast<const int*>(b.base + h.ord_bs);
+    bt.ord_blocks = ord_blocks;
     CK(cudaStreamSynchronize(st));   // the host image goes out of scope
     return GSIS_OK;
 }
@@ -401,6 +425,7 @@ cudaError_t enqueue_iteration(const Batch& b, cudaStream_t s, const Branches& br
     }
     if ((e = mark(4)) != cudaSuccess) return e;
     if ((e = launch_update_batch(b.bt, s)) != cudaSuccess) return e;
+    if (b.bt.ord_blocks > 0 && (e = launch_ordsrc_batch(b.bt, s)) != cudaSuccess) return e;
     return mark(5);
 }
 

@@ -44,7 +44,7 @@ struct ProfScope {
 
 struct Sizes {
     int nx, ny, K, fp32, hist, adjoint, td, order;
-    int ordsrc;   // the per-ordinate source array of the FP64 pseudo-time solve
+    int ordsrc;   // the per-ordinate source array of the pseudo-time sweeps (FP32: with its diagonal)
 };
 
 // Carves one problem's workspace (base may be null: size query only).

@@ -1301,7 +1301,13 @@ size_t sweep_batch_rec_bytes(int fp32)
 void sweep_batch_rec(const Plan& P, void* out)
 {
     if (P.fp32) {
-        const SweepArgs<float> a = P.pt ? sweep_args<float, kSrcPseudoTime>(P) : sweep_args<float, kSrcPlain>(P);
+        SweepArgs<float> a = P.pt ? sweep_args<float, kSrcPseudoTime>(P) : sweep_args<float, kSrcPlain>(P);
+        if (P.pt && P.X_f) {   // the plain sweep over the per-ordinate source, as launch_sweep does
+            a = sweep_args<float, kSrcPlain>(P);
+            a.src = P.X_f;
+            a.src_stride = P.N;
+            a.sigt = P.sigt_d;
+        }
         std::memcpy(out, &a, sizeof(a));
     } else {
         const SweepArgs<double> a = P.pt ? sweep_args<double, kSrcPseudoTime>(P) : sweep_args<double, kSrcPlain>(P);
@@ -1311,8 +1317,9 @@ void sweep_batch_rec(const Plan& P, void* out)
 
 cudaError_t launch_sweep_batch(const BatchTables& bt, cudaStream_t st)
 {
-    if (bt.fp32)
-        return bt.pt ? launch_sweep_batch_t<float, kSrcPseudoTime>(bt, st) : launch_sweep_batch_t<float, kSrcPlain>(bt, st);
+    if (bt.fp32)   // with per-ordinate sources (ord_blocks > 0) the records describe plain sweeps
+        return bt.pt && bt.ord_blocks == 0 ? launch_sweep_batch_t<float, kSrcPseudoTime>(bt, st)
+                                           : launch_sweep_batch_t<float, kSrcPlain>(bt, st);
     return bt.pt ? launch_sweep_batch_t<double, kSrcPseudoTime>(bt, st) : launch_sweep_batch_t<double, kSrcPlain>(bt, st);
 }
 

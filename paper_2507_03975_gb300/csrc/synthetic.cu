@@ -267,8 +267,10 @@ __global__ void ordinate_source_kernel(int N, const T* __restrict__ shift, const
 {
     if (ld_volatile_int(done)) return;
     const size_t row = (size_t)blockIdx.y * N;   // ordinate blockIdx.y
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x)
-        X[row + c] = fma(shift[c], I[row + c], src[c]);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+        if constexpr (sizeof(T) == 4) X[row + c] = fmaf(shift[c], I[row + c], src[c]);   // one FP32 rounding
+        else X[row + c] = fma(shift[c], I[row + c], src[c]);
+    }
 }
 
 cudaError_t launch_ordinate_source(const Plan& P, cudaStream_t st)
@@ -327,6 +329,61 @@ cudaError_t launch_hot_rhs_batch(const BatchTables& bt, cudaStream_t st)
     if (e != cudaSuccess) return e;
     batch_kernel<RhsArgs, rhs_body><<<bt.rhs_blocks, kRedBlock, 0, st>>>(
         static_cast<const RhsArgs*>(bt.rhs), bt.rhs_bstart, bt.B);
+    return cudaGetLastError();
+}
+
+// Batched FP32 per-ordinate source: X[k][c] = fma(shift_c, I[k][c], src_c),
+// the same operation as the single problem's ordinate_source_kernel.
+struct OrdArgs {
+    int N, K;
+    const float* shift; const float* I; const float* src;
+    float* X;
+    const int* done;
+};
+
+constexpr int kOrdSlab = 16;   // ordinates per thread: all their loads in flight before the stores
+
+__device__ __forceinline__ void ord_body(const OrdArgs& a, int bid, int nblk)
+{
+    if (ld_volatile_int(a.done)) return;
+    // tiles of (blockDim.x cells) x (kOrdSlab ordinates); coalesced rows, no per-element division
+    const int cb = (a.N + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int ntiles = cb * ((a.K + kOrdSlab - 1) / kOrdSlab);
+    for (int tile = bid; tile < ntiles; tile += nblk) {
+        const int slab = tile / cb;
+        const int c = (tile - slab * cb) * (int)blockDim.x + (int)threadIdx.x;
+        if (c >= a.N) continue;
+        const int k0 = slab * kOrdSlab;
+        const float sh = a.shift[c], sv = a.src[c];
+        const float* __restrict__ I = a.I + (size_t)k0 * a.N + c;
+        float* __restrict__ X = a.X + (size_t)k0 * a.N + c;
+        float v[kOrdSlab];
+#pragma unroll
+        for (int kk = 0; kk < kOrdSlab; ++kk) v[kk] = k0 + kk < a.K ? I[(size_t)kk * a.N] : 0.f;
+#pragma unroll
+        for (int kk = 0; kk < kOrdSlab; ++kk)
+            if (k0 + kk < a.K) X[(size_t)kk * a.N] = fmaf(sh, v[kk], sv);
+    }
+}
+
+size_t ord_batch_rec_bytes() { return sizeof(OrdArgs); }
+
+int ord_batch_rec(const Plan& P, void* out)
+{
+    OrdArgs a{};
+    a.N = P.N; a.K = P.K;
+    a.shift = P.shift_f; a.I = static_cast<const float*>(P.I); a.src = P.src_f;
+    a.X = P.X_f;
+    a.done = &P.status->done;
+    std::memcpy(out, &a, sizeof(a));
+    const long long tiles = (long long)((P.N + kRedBlock - 1) / kRedBlock) * ((P.K + kOrdSlab - 1) / kOrdSlab);
+    return (int)std::min<long long>(tiles, (long long)P.num_sms * 8);
+}
+
+cudaError_t launch_ordsrc_batch(const BatchTables& bt, cudaStream_t st)
+{
+    batch_kernel<OrdArgs, ord_body><<<bt.ord_blocks, kRedBlock, 0, st>>>(static_cast<const OrdArgs*>(bt.ord),
+                                                                           bt.ord_bstart, bt.B);
     return cudaGetLastError();
 }
 
