@@ -37,7 +37,7 @@ METRIC = "cell-direction updates/s and time-to-converge (GSIS vs SI) on 1 GB300;
 UNIT = "cell-direction updates/s"
 TOL = 1e-8
 BETA = 10.0   # local pseudo-time control (Sec. 4.3) the 2000/0.2 opacity jump needs
-SWEEP_CAPTURE_SHA256 = "09ad1fd7e75a2827"   # sweep.cu at the ncu capture behind _sweep_traffic()
+SWEEP_CAPTURE_SHA256 = "7bbbe3b4e539116b"   # sweep.cu at the ncu capture behind _sweep_traffic()
 SYNTH_CAP = 2  # inner iterations of the synthetic solve per GSIS iteration (capped sub-iterations, Sec. 4.2)
 TD_SYNTH_CAP = 4  # the same cap on the 1024^2 time-dependent workload (its measured optimum: 2 -> 19, 4 -> 8 iterations per step)
 
@@ -130,16 +130,19 @@ def _clock_summary(proc, f, gpu_index):
             "samples": len(sm)}
 
 
-def _sweep_traffic():
-    """DRAM bytes of one sweep launch on this workload from one ncu capture
-    (dram__bytes_read.sum + dram__bytes_write.sum, 94,921,984 + 14,725,888; the
-    committed ncu summary of the sweep kernel on this workload), or None once
+def _sweep_traffic(workload="channel"):
+    """DRAM bytes of one sweep launch from one ncu capture of each workload
+    (dram__bytes_read.sum + dram__bytes_write.sum; the committed ncu summaries
+    of the sweep kernel): the 256x256 S12 channel solve 94,940,416 +
+    14,861,056, the 64-problem batch 522,939,136 + 453,725,184.  None once
     the sweep source differs from the one that was captured."""
     import hashlib
     src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2507_03975_gb300", "csrc", "sweep.cu")
     with open(src, "rb") as f:
         digest = hashlib.sha256(f.read()).hexdigest()
-    return 109_647_872 if digest.startswith(SWEEP_CAPTURE_SHA256) else None
+    if not digest.startswith(SWEEP_CAPTURE_SHA256):
+        return None
+    return {"channel": 109_801_472, "batch": 976_664_320}[workload]
 
 
 def adjoint_measure(gsis, torch, stream):
@@ -202,9 +205,10 @@ def batch_measure(gsis, torch, stream, hbm, steps=3):
     updates = sum(it * p.N * p.K for it, p in zip(iters, ps))
     ms = statistics.median(times)
     sweep_ms = at["class_ms"]["sweep"]
-    # algorithmic bytes of one batched FP32 sweep in the pseudo-time delta form:
-    # read I^m and write I (4 + 4 B per update), cell data src, sigma_t, shift (FP32) once per cell
-    algo = 8.0 * per_sweep + 12.0 * sum(p.N for p in ps)
+    # algorithmic bytes of one batched FP32 pseudo-time sweep over its per-ordinate
+    # source X = src + shift I^m: read X and write I (4 + 4 B per update), the
+    # diagonal sigma_t + shift (FP32) once per cell
+    algo = 8.0 * per_sweep + 4.0 * sum(p.N for p in ps)
     ach = algo / (sweep_ms * 1e-3) / 1e9
     return {"workload": "batch_64_seed4 (sides 32-256, S8-S16, sigma_t 1e-2..1e4, ratio 0.5..0.9999)",
             "problems": len(ps), "updates_per_batch_sweep": per_sweep, "precision": "fp32 sweeps, fp64 synthetic",
@@ -216,7 +220,7 @@ def batch_measure(gsis, torch, stream, hbm, steps=3):
             "updates_per_s": updates / (ms * 1e-3),
             "sweep_updates_per_s": per_sweep / (sweep_ms * 1e-3),
             "sweep_roofline": {"bound": "hbm", "kernel": "batched sweep", "achieved": ach, "peak": hbm,
-                               "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+                               "unit": "GB/s", "frac": ach / hbm, "traffic": _sweep_traffic("batch"),
                                "algorithmic_bytes": algo}}
 
 
