@@ -31,7 +31,6 @@ this order; no step is blocked, fused or reordered.
 """
 from __future__ import annotations
 
-import ctypes
 import dataclasses
 import math
 
@@ -39,18 +38,8 @@ import numpy as np
 
 from . import gsis as G
 
-_lib_t = None
-
-
 def _clib():
-    global _lib_t
-    if _lib_t is None:
-        lib = G._clib()
-        P = ctypes.POINTER(ctypes.c_double)
-        lib.oracle_sweep_transposed.argtypes = [ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int, P, P, P, P, P]
-        lib.oracle_sweep_transposed.restype = ctypes.c_int
-        _lib_t = lib
-    return _lib_t
+    return G._clib()
 
 
 def transposed_sweep(prob, psi):

@@ -40,19 +40,39 @@ import scipy.sparse.linalg as spla
 
 from . import build as _build
 
-_lib = None
+_libs = {}
+_threaded = False
+
+
+def use_threads(on: bool) -> None:
+    """Selects, for later calls, the -fopenmp build of the C sweeps (the
+    ordinates on all host cores; every sum in the same order, so the same
+    results).  Only for timing the oracle; the default is the plain build."""
+    global _threaded
+    _threaded = bool(on)
+
+
+def threads() -> int:
+    """Host threads the selected C sweep library runs on."""
+    return int(_clib().oracle_threads())
 
 
 def _clib():
-    global _lib
-    if _lib is None:
-        lib = ctypes.CDLL(_build.build())
+    lib = _libs.get(_threaded)
+    if lib is None:
+        lib = ctypes.CDLL(_build.build(threads=_threaded))
         P = ctypes.POINTER(ctypes.c_double)
         lib.oracle_sweep.argtypes = [ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int, P, P, P,
                                      P, P, P, P, P, P, P, P, P, P, P, P, P]
         lib.oracle_sweep.restype = ctypes.c_int
-        _lib = lib
-    return _lib
+        lib.oracle_sweep_transposed.argtypes = [ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int, P, P, P, P, P]
+        lib.oracle_sweep_transposed.restype = ctypes.c_int
+        lib.oracle_sweep_delta.argtypes = [ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int, P, P, P, P, P, P]
+        lib.oracle_sweep_delta.restype = ctypes.c_int
+        lib.oracle_threads.argtypes = []
+        lib.oracle_threads.restype = ctypes.c_int
+        _libs[_threaded] = lib
+    return lib
 
 
 def _ptr(a):

@@ -23,11 +23,16 @@
  * triangular increment system with the shifted diagonal (Eqs. (RTE_d_mtx),
  * (elem_main_shifted)) solved in upwind order, and I^{m+1/2} = I^m + dI.
  *
- * Plain FP64, plain loops, no blocking.
+ * Plain FP64, plain loops, no blocking.  Built twice from this one file: plain
+ * (the oracle the tests use) and with -fopenmp (the same arithmetic in the
+ * same order, the ordinates on all host cores; only for timing the oracle).
  */
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* boundary face numbering: W j, E ny+j, S 2ny+i, N 2ny+nx+i */
 
@@ -60,6 +65,74 @@ static double upwind(const double* Ik, const double* inflow, int nx, int ny, int
     return inflow ? inflow[(size_t)bface(nx, ny, i, j, f) * K + k] : 0.0;
 }
 
+/* The intensities of ordinate k (I, [N]) by one exact upwind sweep, or in
+   the delta form when shift is given (dI: [N] scratch). */
+static void sweep_ordinate(int nx, int ny, const double* dx, const double* dy, int K, int k,
+                           double m, double e, const double* sigma_t, const double* S,
+                           const double* inflow, const double* shift, const double* I_prev,
+                           double* I, double* dI)
+{
+    const int N = nx * ny;
+    /* upwind visiting order: a cell is visited after the neighbours whose
+       shared face has Omega.n < 0 seen from this cell */
+    const int i0 = (m >= 0.0) ? 0 : nx - 1, di = (m >= 0.0) ? 1 : -1;
+    const int j0 = (e >= 0.0) ? 0 : ny - 1, dj = (e >= 0.0) ? 1 : -1;
+    for (int jj = 0; jj < ny; ++jj) {
+        const int j = j0 + dj * jj;
+        for (int ii = 0; ii < nx; ++ii) {
+            const int i = i0 + di * ii;
+            const int c = i + nx * j;
+            const double V = dx[i] * dy[j];
+            /* the four faces: outward normal and area */
+            const double An[4] = {dy[j], dy[j], dx[i], dx[i]};   /* W E S N */
+            const double on[4] = {-m, m, -e, e};                 /* Omega . n */
+            if (!shift) {
+                /* exact solve of the cell equation given the upwind values */
+                double diag = sigma_t[c];
+                double rhs = S[c];
+                for (int f = 0; f < 4; ++f) {
+                    const double oa = on[f] * An[f];   /* Omega . A_ij */
+                    if (on[f] >= 0.0) {
+                        diag += oa / V;                 /* outflow: I_ij = I_i */
+                    } else {
+                        rhs -= oa / V * upwind(I, inflow, nx, ny, K, k, i, j, f);
+                    }
+                }
+                I[c] = rhs / diag;
+            } else {
+                /* delta form with the pseudo-time shift (Eqs. (RTE_d_increment),
+                   (delta_Iij), (RTE_d_res), (RTE_d_mtx), (elem_main_shifted)):
+                   residual of the UW1 equation at I^m, then
+                   d_ii dI_i + sum_{inflow j} d_ij dI_j = r_i, I^{m+1/2} = I^m + dI */
+                const double* Im = I_prev + (size_t)k * N;
+                double r = S[c] - sigma_t[c] * Im[c];
+                double dii = shift[c] + sigma_t[c];
+                double lower = 0.0;
+                for (int f = 0; f < 4; ++f) {
+                    const double oa = on[f] * An[f];
+                    if (on[f] >= 0.0) {
+                        r -= oa / V * Im[c];
+                        dii += oa / V;
+                    } else {
+                        r -= oa / V * upwind(Im, inflow, nx, ny, K, k, i, j, f);
+                        /* d_ij dI_j with dI on an inflow boundary face = 0 */
+                        const int nb = neighbour(nx, ny, i, j, f);
+                        if (nb >= 0) lower += oa / V * dI[nb];
+                    }
+                }
+                dI[c] = (r - lower) / dii;
+                I[c] = Im[c] + dI[c];
+            }
+        }
+    }
+}
+
+/*
+ * The ordinates are independent: with -fopenmp they are swept in parallel
+ * (one ordinate per task), and every moment and boundary-flux sum then runs
+ * per cell / per face over the ordinates in index order, so the results do
+ * not depend on the thread count (and equal the single-threaded build's).
+ */
 int oracle_sweep(int nx, int ny, const double* dx, const double* dy, int K,
                  const double* mu, const double* eta, const double* w,
                  const double* sigma_t, const double* S, const double* inflow,
@@ -69,92 +142,70 @@ int oracle_sweep(int nx, int ny, const double* dx, const double* dy, int K,
 {
     const int N = nx * ny;
     const int nbf = 2 * (nx + ny);
-    double* I = (double*)malloc(sizeof(double) * (size_t)N);
-    double* dI = (double*)malloc(sizeof(double) * (size_t)N);
-    if (!I || !dI) { free(I); free(dI); return -1; }
-    for (int c = 0; c < N; ++c) {
-        rho[c] = 0.0; Fx[c] = 0.0; Fy[c] = 0.0;
-        Pxx[c] = 0.0; Pxy[c] = 0.0; Pyy[c] = 0.0;
-    }
-    for (int f = 0; f < nbf; ++f) fb[f] = 0.0;
-
+    /* every ordinate's intensities: the caller's I_out, else scratch */
+    double* Iall = I_out ? I_out : (double*)malloc(sizeof(double) * (size_t)K * (size_t)N);
+    if (!Iall) return -1;
+    int failed = 0;
+#pragma omp parallel for schedule(dynamic, 1)
     for (int k = 0; k < K; ++k) {
-        const double m = mu[k], e = eta[k];
-        /* upwind visiting order: a cell is visited after the neighbours whose
-           shared face has Omega.n < 0 seen from this cell */
-        const int i0 = (m >= 0.0) ? 0 : nx - 1, di = (m >= 0.0) ? 1 : -1;
-        const int j0 = (e >= 0.0) ? 0 : ny - 1, dj = (e >= 0.0) ? 1 : -1;
-        for (int jj = 0; jj < ny; ++jj) {
-            const int j = j0 + dj * jj;
-            for (int ii = 0; ii < nx; ++ii) {
-                const int i = i0 + di * ii;
-                const int c = i + nx * j;
-                const double V = dx[i] * dy[j];
-                /* the four faces: outward normal and area */
-                const double An[4] = {dy[j], dy[j], dx[i], dx[i]};   /* W E S N */
-                const double on[4] = {-m, m, -e, e};                 /* Omega . n */
-                if (!shift) {
-                    /* exact solve of the cell equation given the upwind values */
-                    double diag = sigma_t[c];
-                    double rhs = S[c];
-                    for (int f = 0; f < 4; ++f) {
-                        const double oa = on[f] * An[f];   /* Omega . A_ij */
-                        if (on[f] >= 0.0) {
-                            diag += oa / V;                 /* outflow: I_ij = I_i */
-                        } else {
-                            rhs -= oa / V * upwind(I, inflow, nx, ny, K, k, i, j, f);
-                        }
-                    }
-                    I[c] = rhs / diag;
-                } else {
-                    /* delta form with the pseudo-time shift (Eqs. (RTE_d_increment),
-                       (delta_Iij), (RTE_d_res), (RTE_d_mtx), (elem_main_shifted)):
-                       residual of the UW1 equation at I^m, then
-                       d_ii dI_i + sum_{inflow j} d_ij dI_j = r_i, I^{m+1/2} = I^m + dI */
-                    const double* Im = I_prev + (size_t)k * N;
-                    double r = S[c] - sigma_t[c] * Im[c];
-                    double dii = shift[c] + sigma_t[c];
-                    double lower = 0.0;
-                    for (int f = 0; f < 4; ++f) {
-                        const double oa = on[f] * An[f];
-                        if (on[f] >= 0.0) {
-                            r -= oa / V * Im[c];
-                            dii += oa / V;
-                        } else {
-                            r -= oa / V * upwind(Im, inflow, nx, ny, K, k, i, j, f);
-                            /* d_ij dI_j with dI on an inflow boundary face = 0 */
-                            const int nb = neighbour(nx, ny, i, j, f);
-                            if (nb >= 0) lower += oa / V * dI[nb];
-                        }
-                    }
-                    dI[c] = (r - lower) / dii;
-                    I[c] = Im[c] + dI[c];
-                }
-            }
+        double* dI = shift ? (double*)malloc(sizeof(double) * (size_t)N) : NULL;
+        if (shift && !dI) {
+#pragma omp atomic write
+            failed = 1;
+            continue;
         }
-        for (int c = 0; c < N; ++c) {
-            rho[c] += w[k] * I[c];
-            Fx[c] += w[k] * m * I[c];
-            Fy[c] += w[k] * e * I[c];
-            Pxx[c] += w[k] * m * m * I[c];
-            Pxy[c] += w[k] * m * e * I[c];
-            Pyy[c] += w[k] * e * e * I[c];
+        sweep_ordinate(nx, ny, dx, dy, K, k, mu[k], eta[k], sigma_t, S, inflow, shift, I_prev,
+                       Iall + (size_t)k * N, dI);
+        free(dI);
+    }
+    if (failed) {
+        if (!I_out) free(Iall);
+        return -1;
+    }
+#pragma omp parallel for
+    for (int c = 0; c < N; ++c) {
+        double r = 0.0, fx = 0.0, fy = 0.0, pxx = 0.0, pxy = 0.0, pyy = 0.0;
+        for (int k = 0; k < K; ++k) {
+            const double m = mu[k], e = eta[k], I = Iall[(size_t)k * N + c];
+            r += w[k] * I;
+            fx += w[k] * m * I;
+            fy += w[k] * e * I;
+            pxx += w[k] * m * m * I;
+            pxy += w[k] * m * e * I;
+            pyy += w[k] * e * e * I;
         }
-        /* boundary faces: outgoing uses the boundary cell, incoming the inflow */
-        for (int f = 0; f < nbf; ++f) {
+        rho[c] = r; Fx[c] = fx; Fy[c] = fy;
+        Pxx[c] = pxx; Pxy[c] = pxy; Pyy[c] = pyy;
+    }
+    /* boundary faces: outgoing uses the boundary cell, incoming the inflow */
+#pragma omp parallel for
+    for (int f = 0; f < nbf; ++f) {
+        double acc = 0.0;
+        for (int k = 0; k < K; ++k) {
+            const double m = mu[k], e = eta[k];
+            const double* I = Iall + (size_t)k * N;
             int c; double on;
             if (f < ny) { c = nx * f; on = -m; }
             else if (f < 2 * ny) { c = (nx - 1) + nx * (f - ny); on = m; }
             else if (f < 2 * ny + nx) { c = f - 2 * ny; on = -e; }
             else { c = (f - 2 * ny - nx) + nx * (ny - 1); on = e; }
             const double Iface = (on >= 0.0) ? I[c] : (inflow ? inflow[(size_t)f * K + k] : 0.0);
-            fb[f] += w[k] * on * Iface;
+            acc += w[k] * on * Iface;
         }
-        if (I_out) memcpy(I_out + (size_t)k * N, I, sizeof(double) * (size_t)N);
+        fb[f] = acc;
     }
-    free(I);
-    free(dI);
+    if (!I_out) free(Iall);
     return 0;
+}
+
+/* Threads the OpenMP build uses (1 without OpenMP). */
+int oracle_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 /*
@@ -176,6 +227,7 @@ int oracle_sweep_transposed(int nx, int ny, const double* dx, const double* dy, 
                             const double* psi, double* phi)
 {
     const int N = nx * ny;
+#pragma omp parallel for schedule(dynamic, 1)
     for (int k = 0; k < K; ++k) {
         const double m = mu[k], e = eta[k];
         const double* pk = psi + (size_t)k * N;
@@ -225,6 +277,7 @@ int oracle_sweep_delta(int nx, int ny, const double* dx, const double* dy, int K
                        const double* shift, const double* R, double* dI)
 {
     const int N = nx * ny;
+#pragma omp parallel for schedule(dynamic, 1)
     for (int k = 0; k < K; ++k) {
         const double m = mu[k], e = eta[k];
         const double* Rk = R + (size_t)k * N;

@@ -42,21 +42,10 @@ import math
 
 import numpy as np
 
-from . import build as _build
 from . import gsis as G
 
-_lib = None
-
-
 def _clib():
-    global _lib
-    if _lib is None:
-        lib = ctypes.CDLL(_build.build())
-        P = ctypes.POINTER(ctypes.c_double)
-        lib.oracle_sweep_delta.argtypes = [ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int, P, P, P, P, P, P]
-        lib.oracle_sweep_delta.restype = ctypes.c_int
-        _lib = lib
-    return _lib
+    return G._clib()
 
 
 def _ptr(a):
