@@ -673,6 +673,68 @@ def run_ours(args):
     return 0
 
 
+def run_oracle_times(args):
+    """The FP64 oracle's own timings on the host cores, single thread and with
+    its C sweeps on every core: time per sweep (64^2 S8 uniform, 256^2 S12
+    channel); time to Err < 1e-8 by SI and GSIS on the 64^2 problem and by
+    GSIS on the channel (beta = 10, as the GPU solve); channel SI and the
+    1024^2 S16 time-dependent run from bounded samples, extrapolated with
+    the GPU runs' iteration counts (stated as extrapolations).  CPU only;
+    prints one JSON line."""
+    import platform
+
+    import numpy as np
+
+    import oracle
+    import workloads as W
+    from oracle import gsis as G
+    from oracle import timedep as TD
+
+    def timed(fn):
+        t0 = time.perf_counter()
+        r = fn()
+        return r, time.perf_counter() - t0
+
+    out = {"impl": "oracle_times", "host": platform.machine(), "nproc": os.cpu_count(), "arms": {}}
+    c1, c2 = W.config_small(), W.config_channel()
+    for threads in (False, True):
+        G.use_threads(threads)
+        try:
+            arm = {"threads": G.threads()}
+            for name, p in (("uniform_64x64_S8", c1), ("channel_256x256_S12", c2)):
+                rho = np.zeros(p.N)
+                G.transport_sweep(p, rho)
+                ts = [timed(lambda: G.transport_sweep(p, rho))[1] for _ in range(3)]
+                arm[f"sweep_s_{name}"] = min(ts)
+            for name, fn in (("si", oracle.si_solve), ("gsis", oracle.gsis_solve)):
+                r, dt = timed(lambda: fn(c1, tol=TOL))
+                arm[f"uniform_64x64_S8_{name}"] = {"s": dt, "iters": int(r["iters"])}
+            if threads:
+                r, dt = timed(lambda: oracle.gsis_solve(c2, tol=TOL, beta=BETA))
+                arm["channel_256x256_S12_gsis"] = {"s": dt, "iters": int(r["iters"])}
+                n = 20
+                _, dt = timed(lambda: oracle.si_solve(c2, fixed_iters=n))
+                arm["channel_256x256_S12_si_extrapolated"] = {
+                    "s": dt / n * 9081, "sample": f"{n} iterations in {dt:.1f} s, x 9081 (the GPU SI count)"}
+                p5 = W.config_timedep()
+                td = W.TIMEDEP
+                tp = TD.TimeParams(dt=td["dt"], c=td["c"], a=td["a"], cv=td["cv"])
+                T0 = np.full(p5.N, td["T0"])
+                rho0 = td["a"] * td["c"] * T0 ** 4
+                _, dt = timed(lambda: TD.gsis_time_step(p5, tp, rho0, T0, TD.isotropic(p5, rho0), fixed_iters=1))
+                per_step = 8.64   # GSIS iterations per step of the GPU FP64 run (100 steps, Err < 1e-8)
+                arm["channel_td_1024x1024_S16_gsis_extrapolated"] = {
+                    "s_2_steps": 2 * per_step * dt, "s_100_steps": 100 * per_step * dt,
+                    "sample": f"one GSIS iteration of the first step in {dt:.1f} s (sweep, gradient, sparse "
+                              f"direct solve of the 1,048,576-cell synthetic system), x {per_step} iterations "
+                              "per step (the GPU FP64 run's mean)"}
+            out["arms"]["all_cores" if threads else "one_core"] = arm
+        finally:
+            G.use_threads(False)
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -690,11 +752,15 @@ def main():
     ap.add_argument("--no-td-adjoint", action="store_true", help="skip the time-dependent adjoint measurement")
     ap.add_argument("--td-adjoint-only", action="store_true", help="run only the time-dependent adjoint measurement")
     ap.add_argument("--timedep-only", action="store_true", help="run only the time-dependent measurement")
+    ap.add_argument("--oracle-times", action="store_true",
+                    help="time the FP64 oracle itself on the host cores (CPU only) and exit")
     ap.add_argument("--synth-cap", type=int, default=SYNTH_CAP,
                     help="inner iterations of the synthetic solve per GSIS iteration (0: solve to 1e-12)")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.oracle_times:
+        return run_oracle_times(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
