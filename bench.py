@@ -145,6 +145,37 @@ def _sweep_traffic(workload="channel"):
     return {"channel": 109_801_472, "batch": 976_664_320}[workload]
 
 
+def small_measure(gsis, torch, stream):
+    """Time to Err < 1e-8 of FP64 GSIS and SI on the 64x64 S8 uniform problem
+    (sigma_t = 10, ratio 0.99, q = 1, vacuum): the latency-bound size, where
+    a sweep is 164K updates.  Device time with CUDA events, inputs resident,
+    best of three after one warm-up solve."""
+    p = W.config_small()
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    sa, ss, q = t(p.sigma_a), t(p.sigma_s), t(p.q)
+    out = {"workload": "uniform_64x64_S8 (sigma_t 10, ratio 0.99, q 1, vacuum), FP64, Err < 1e-8"}
+    # GSIS with the synthetic system solved to its default tolerance each
+    # iteration, and with the multigrid-CG capped at SYNTH_CAP inner
+    # iterations (warm-started; the same fixed point), as in the channel solve
+    for name, scheme, cap in (("gsis", gsis.SCHEME_GSIS, 0), ("gsis_synth_cap", gsis.SCHEME_GSIS, SYNTH_CAP),
+                              ("si", gsis.SCHEME_SI, 0)):
+        kw = {"synth_max_iter": cap} if cap else {}
+        opt = gsis.default_options(scheme=scheme, precision=gsis.FP64, tol=TOL, max_iter=100000,
+                                   check_every=16 if scheme == gsis.SCHEME_GSIS else 64, **kw)
+        best, r = None, None
+        for i in range(4):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = gsis.solve(p.dx, p.dy, p.mu, p.eta, p.w, sa, ss, q, None, opt, want_P=False)
+            e1.record(stream)
+            e1.synchronize()
+            if i and (best is None or e0.elapsed_time(e1) < best):
+                best = e0.elapsed_time(e1)
+        out[name] = {"ms": best, "iters": r["iters"], "status": r["status"],
+                     "updates_per_s": r["iters"] * p.N * p.K / (best * 1e-3)}
+    return out
+
+
 def adjoint_measure(gsis, torch, stream):
     """Forward solve and adjoint gradient of J = sum of rho over 16 seed-3
     detector cells on the 64x64 S8 workload (sigma_t = 10, ratio 0.99, q = 1,
@@ -565,9 +596,10 @@ def run_ours(args):
         uw2 = uw2_measure(gsis, torch, stream, p, sa, ss, q, inflow, flush)
 
     # ---- adjoint (gradient of a detector functional, 64x64 S8 workload), once
-    adj = None
+    adj = small = None
     if not args.no_adjoint:
         adj = adjoint_measure(gsis, torch, stream)
+        small = small_measure(gsis, torch, stream)
 
     # ---- time-dependent radiation-material workload (1024^2 S16, 100 steps), once
     timedep = None
@@ -661,7 +693,7 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(sum(v["kernels"] for v in prof.values())),
             "kernel_ms": {k: v["total_ms"] for k, v in prof.items()},
-            "adjoint": adj,
+            "adjoint": adj, "uniform_64x64_S8": small,
             "batch": batch,
             "timedep": timedep,
             "td_adjoint": td_adj,

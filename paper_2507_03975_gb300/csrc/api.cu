@@ -566,7 +566,7 @@ int gsis_solve(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis_op
             } else {
                 TIMED(GSIS_KCLASS_UPDATE, 1, launch_update(P, P.rho_h, st));
             }
-            if (P.X || P.X_f) TIMED(GSIS_KCLASS_UPDATE, 1, launch_ordinate_source(P, st));
+            // (with pseudo-time the update also formed the next sweep's per-ordinate source)
         }
         launched += batch;
         if ((rc = read_status(S, P, st))) return rc;
