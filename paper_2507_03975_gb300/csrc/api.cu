@@ -566,7 +566,8 @@ int gsis_solve(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis_op
             } else {
                 TIMED(GSIS_KCLASS_UPDATE, 1, launch_update(P, P.rho_h, st));
             }
-            // (with pseudo-time the update also formed the next sweep's per-ordinate source)
+            // FP64 pseudo-time: the update also formed the next sweep's per-ordinate source
+            if (P.X_f) TIMED(GSIS_KCLASS_UPDATE, 1, launch_ordinate_source(P, st));
         }
         launched += batch;
         if ((rc = read_status(S, P, st))) return rc;

@@ -45,7 +45,7 @@ size_t al(size_t b) { return (b + kAlign - 1) / kAlign * kAlign; }
 // problem's own gsis_solve workspace.
 struct Header {
     size_t bstatus, statuses, sweep, seg_start, seg_prob, seg_band, mom, mom_bs, hot, hot_bs, rhs, rhs_bs, upd,
-        upd_bs, strip, total;
+        upd_bs, ord, ord_bs, strip, total;
 };
 
 Header header_layout(int B, int nseg, int fp32)
@@ -72,6 +72,8 @@ Header header_layout(int B, int nseg, int fp32)
     h.rhs_bs = take(bs);
     h.upd = take((size_t)B * upd_batch_rec_bytes());
     h.upd_bs = take(bs);
+    h.ord = take((size_t)B * ord_batch_rec_bytes());
+    h.ord_bs = take(bs);
     h.strip = take((size_t)B * strip_batch_rec_bytes());
     h.total = off;
     return h;
@@ -169,7 +171,7 @@ int batch_setup(Batch& b, const gsis_problem* probs, int n, const gsis_options* 
         if (b.P[p].X_f) CK(launch_ordinate_source(b.P[p], st));
     }
     b.pt = b.P[0].pt;
-    b.ordsrc = b.P[0].X_f != nullptr;   // FP32 pseudo-time sweeps over per-ordinate sources (the update forms them)
+    b.ordsrc = b.P[0].X_f != nullptr;   // FP32 pseudo-time sweeps over per-ordinate sources
     CK(cudaMemsetAsync(b.bstatus, 0, sizeof(Status), st));
     return GSIS_OK;
 }
@@ -270,6 +272,10 @@ int batch_tables(Batch& b, const gsis_batch_tuning& t, cudaStream_t st)
                                   [&](const Plan& P, void* o) { return rhs_batch_rec(P, o); });
     const int upd_blocks = blocks(h.upd, upd_batch_rec_bytes(), h.upd_bs,
                                   [&](const Plan& P, void* o) { return upd_batch_rec(P, gsis, o); });
+    // FP32 pseudo-time: the next sweeps' per-ordinate sources after every update
+    const int ord_blocks = b.ordsrc ? blocks(h.ord, ord_batch_rec_bytes(), h.ord_bs,
+                                             [&](const Plan& P, void* o) { return ord_batch_rec(P, o); })
+                                    : 0;
 
     // synthetic: problems grouped by cluster size, one table run per group
     b.groups.clear();
@@ -332,7 +338,9 @@ int batch_tables(Batch& b, const gsis_batch_tuning& t, cudaStream_t st)
     bt.upd = b.base + h.upd;
     bt.upd_bstart = reinterpret_cast<const int*>(b.base + h.upd_bs);
     bt.upd_blocks = upd_blocks;
-    bt.ordsrc = b.ordsrc;
+    bt.ord = b.base + h.ord;
+    bt.ord_bstart = reinterpret_cast<const int*>(b.base + h.ord_bs);
+    bt.ord_blocks = ord_blocks;
     CK(cudaStreamSynchronize(st));   // the host image goes out of scope
     return GSIS_OK;
 }
@@ -417,6 +425,7 @@ cudaError_t enqueue_iteration(const Batch& b, cudaStream_t s, const Branches& br
     }
     if ((e = mark(4)) != cudaSuccess) return e;
     if ((e = launch_update_batch(b.bt, s)) != cudaSuccess) return e;
+    if (b.bt.ord_blocks > 0 && (e = launch_ordsrc_batch(b.bt, s)) != cudaSuccess) return e;
     return mark(5);
 }
 

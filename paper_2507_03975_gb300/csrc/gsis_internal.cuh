@@ -220,7 +220,8 @@ struct BatchTables {
     const void* hot; const int* hot_bstart; int hot_blocks;
     const void* rhs; const int* rhs_bstart; int rhs_blocks;
     const void* upd; const int* upd_bstart; int upd_blocks;
-    int ordsrc;   // FP32 pseudo-time over per-ordinate sources (formed by the update): plain sweep records
+    // FP32 pseudo-time: the sweeps' per-ordinate sources (or ord_blocks = 0)
+    const void* ord; const int* ord_bstart; int ord_blocks;
 };
 
 size_t sweep_batch_rec_bytes(int fp32);
@@ -237,6 +238,9 @@ int rhs_batch_rec(const Plan& P, void* out);
 int upd_batch_rec(const Plan& P, bool gsis, void* out);
 cudaError_t launch_hot_rhs_batch(const BatchTables& bt, cudaStream_t st);
 cudaError_t launch_update_batch(const BatchTables& bt, cudaStream_t st);
+size_t ord_batch_rec_bytes();
+int ord_batch_rec(const Plan& P, void* out);
+cudaError_t launch_ordsrc_batch(const BatchTables& bt, cudaStream_t st);
 size_t strip_batch_rec_bytes();
 bool strip_batch_rec(const Plan& P, int cl, void* out, size_t* bytes);
 bool prepare_strip_batch(int cl, size_t bytes);

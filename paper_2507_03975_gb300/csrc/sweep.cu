@@ -1317,8 +1317,8 @@ void sweep_batch_rec(const Plan& P, void* out)
 
 cudaError_t launch_sweep_batch(const BatchTables& bt, cudaStream_t st)
 {
-    if (bt.fp32)   // with per-ordinate sources the records describe plain sweeps
-        return bt.pt && !bt.ordsrc ? launch_sweep_batch_t<float, kSrcPseudoTime>(bt, st)
+    if (bt.fp32)   // with per-ordinate sources (ord_blocks > 0) the records describe plain sweeps
+        return bt.pt && bt.ord_blocks == 0 ? launch_sweep_batch_t<float, kSrcPseudoTime>(bt, st)
                                            : launch_sweep_batch_t<float, kSrcPlain>(bt, st);
     return bt.pt ? launch_sweep_batch_t<double, kSrcPseudoTime>(bt, st) : launch_sweep_batch_t<double, kSrcPlain>(bt, st);
 }

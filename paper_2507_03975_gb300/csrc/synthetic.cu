@@ -149,11 +149,11 @@ struct UpdArgs {
     const double* rho_new; double* rho_m; const double* rho_h;
     double* src; float* src_f;
     double* corr; float* corr_f;   // second-order delta form: isotropic correction of I (or null)
-    // steady pseudo-time: the next sweep's per-ordinate source X[k][c] = src_c + shift_c I^m[k][c]
-    // (FP64 X from I, or FP32 X_f from I with shift_f; both null: not formed here)
+    // FP64 steady pseudo-time: the next sweep's per-ordinate source
+    // X[k][c] = src_c + shift_c I^m[k][c] (null: not formed here)
     int K;
-    const void* I;
-    double* X; float* X_f; const float* shift_f;
+    const double* I;
+    double* X;
     int pt;
     double tol;
     int fixed_iters, max_iter;
@@ -169,15 +169,14 @@ struct UpdArgs {
 // src = (sigma_s rho + q)/4pi + shift (rho - rho^{m+1/2})/4pi).
 // X[k][c] = fma(sh, I[k][c], s) for every ordinate of cell c; the loads of a
 // slab of ordinates are all issued before its stores.
-template <typename T>
-__device__ __forceinline__ void ordinate_row(int K, int N, int c, T sh, T s, const T* __restrict__ I,
-                                             T* __restrict__ X)
+__device__ __forceinline__ void ordinate_row(int K, int N, int c, double sh, double s,
+                                             const double* __restrict__ I, double* __restrict__ X)
 {
     constexpr int kSlab = 8;
     for (int k0 = 0; k0 < K; k0 += kSlab) {
-        T v[kSlab];
+        double v[kSlab];
 #pragma unroll
-        for (int kk = 0; kk < kSlab; ++kk) v[kk] = k0 + kk < K ? I[(size_t)(k0 + kk) * N + c] : T(0);
+        for (int kk = 0; kk < kSlab; ++kk) v[kk] = k0 + kk < K ? I[(size_t)(k0 + kk) * N + c] : 0.0;
 #pragma unroll
         for (int kk = 0; kk < kSlab; ++kk)
             if (k0 + kk < K) X[(size_t)(k0 + kk) * N + c] = fma(sh, v[kk], s);
@@ -204,9 +203,7 @@ __device__ __forceinline__ void update_body(const UpdArgs& a, int bid, int nblk)
         a.src[c] = s;
         if (a.src_f) a.src_f[c] = (float)s;
         // the same FMA as ordinate_source_kernel: the same bits
-        if (a.X) ordinate_row<double>(a.K, a.N, c, a.shift[c], s, static_cast<const double*>(a.I), a.X);
-        else if (a.X_f)
-            ordinate_row<float>(a.K, a.N, c, a.shift_f[c], (float)s, static_cast<const float*>(a.I), a.X_f);
+        if (a.X) ordinate_row(a.K, a.N, c, a.shift[c], s, a.I, a.X);
 
         if (a.corr) {   // I^{m+1} = I^{m+1/2} + (rho^{m+1} - rho^{m+1/2})/4pi, kept per cell
             const double cc = (nw - a.rho_h[c]) * kInvFourPi;
@@ -264,11 +261,10 @@ UpdArgs upd_args(const Plan& P, const double* rho_new)
     a.pt = P.pt && P.order == 1;   // second order: the correction is carried explicitly
     a.corr = P.order == 2 ? P.corr : nullptr;
     a.corr_f = P.order == 2 && P.fp32 ? P.corr_f : nullptr;
-    if (P.order == 1 && !P.In && (P.X || P.X_f)) {   // steady pseudo-time: the next sweeps' sources too
-        a.K = P.K; a.I = P.I;
-        a.X = P.fp32 ? nullptr : P.X;
-        a.X_f = P.fp32 ? P.X_f : nullptr;
-        a.shift_f = P.shift_f;
+    // FP64 steady pseudo-time: the next sweeps' sources too (FP32 ones come from
+    // ordinate_source_kernel / ord_body, faster there than inside this kernel)
+    if (P.order == 1 && !P.In && P.X && !P.fp32) {
+        a.K = P.K; a.I = static_cast<const double*>(P.I); a.X = P.X;
     }
 
     a.tol = P.tol; a.fixed_iters = P.fixed_iters; a.max_iter = P.max_iter;
@@ -361,6 +357,61 @@ cudaError_t launch_hot_rhs_batch(const BatchTables& bt, cudaStream_t st)
     if (e != cudaSuccess) return e;
     batch_kernel<RhsArgs, rhs_body><<<bt.rhs_blocks, kRedBlock, 0, st>>>(
         static_cast<const RhsArgs*>(bt.rhs), bt.rhs_bstart, bt.B);
+    return cudaGetLastError();
+}
+
+// Batched FP32 per-ordinate source: X[k][c] = fma(shift_c, I[k][c], src_c),
+// the same operation as the single problem's ordinate_source_kernel.
+struct OrdArgs {
+    int N, K;
+    const float* shift; const float* I; const float* src;
+    float* X;
+    const int* done;
+};
+
+constexpr int kOrdSlab = 16;   // ordinates per thread: all their loads in flight before the stores
+
+__device__ __forceinline__ void ord_body(const OrdArgs& a, int bid, int nblk)
+{
+    if (ld_volatile_int(a.done)) return;
+    // tiles of (blockDim.x cells) x (kOrdSlab ordinates); coalesced rows, no per-element division
+    const int cb = (a.N + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int ntiles = cb * ((a.K + kOrdSlab - 1) / kOrdSlab);
+    for (int tile = bid; tile < ntiles; tile += nblk) {
+        const int slab = tile / cb;
+        const int c = (tile - slab * cb) * (int)blockDim.x + (int)threadIdx.x;
+        if (c >= a.N) continue;
+        const int k0 = slab * kOrdSlab;
+        const float sh = a.shift[c], sv = a.src[c];
+        const float* __restrict__ I = a.I + (size_t)k0 * a.N + c;
+        float* __restrict__ X = a.X + (size_t)k0 * a.N + c;
+        float v[kOrdSlab];
+#pragma unroll
+        for (int kk = 0; kk < kOrdSlab; ++kk) v[kk] = k0 + kk < a.K ? I[(size_t)kk * a.N] : 0.f;
+#pragma unroll
+        for (int kk = 0; kk < kOrdSlab; ++kk)
+            if (k0 + kk < a.K) X[(size_t)kk * a.N] = fmaf(sh, v[kk], sv);
+    }
+}
+
+size_t ord_batch_rec_bytes() { return sizeof(OrdArgs); }
+
+int ord_batch_rec(const Plan& P, void* out)
+{
+    OrdArgs a{};
+    a.N = P.N; a.K = P.K;
+    a.shift = P.shift_f; a.I = static_cast<const float*>(P.I); a.src = P.src_f;
+    a.X = P.X_f;
+    a.done = &P.status->done;
+    std::memcpy(out, &a, sizeof(a));
+    const long long tiles = (long long)((P.N + kRedBlock - 1) / kRedBlock) * ((P.K + kOrdSlab - 1) / kOrdSlab);
+    return (int)std::min<long long>(tiles, (long long)P.num_sms * 8);
+}
+
+cudaError_t launch_ordsrc_batch(const BatchTables& bt, cudaStream_t st)
+{
+    batch_kernel<OrdArgs, ord_body><<<bt.ord_blocks, kRedBlock, 0, st>>>(static_cast<const OrdArgs*>(bt.ord),
+                                                                           bt.ord_bstart, bt.B);
     return cudaGetLastError();
 }
 
