@@ -170,6 +170,31 @@ def test_si_pseudo_time_parity(gs):
     assert rel(r["rho"].cpu().numpy(), o["rho"]) < TOL64
 
 
+def test_fp32_gsis_pseudo_time_parity(gs):
+    """FP32 sweeps over the per-ordinate source X = src + shift I^m with the
+    diagonal sigma_t + shift as one FP32 array (FP64 synthetic solve), on the
+    2000 / 0.2 opacity jump: eight iterations and the converged result
+    against the FP64 oracle within the FP32 sweep tolerance."""
+    p = W.channel_problem(64, 8, 2, width=2)
+    m = 8
+    o = oracle.gsis_solve(p, fixed_iters=m, beta=10.0)
+    r = _solve(gs, p, precision=gs.FP32_SWEEP, fixed_iters=m, max_iter=m, beta=10.0, synth_rtol=1e-14,
+               synth_max_iter=3000)
+    assert rel(r["rho"].cpu().numpy(), o["rho"]) < TOL32
+    oc = oracle.gsis_solve(p, tol=1e-10, beta=10.0)
+    rc = _solve(gs, p, precision=gs.FP32_SWEEP, tol=1e-7, beta=10.0, synth_rtol=1e-13, synth_max_iter=3000,
+                stall_window=8)
+    assert rel(rc["rho"].cpu().numpy(), oc["rho"]) < TOL32
+
+
+def test_fp32_si_pseudo_time_parity(gs):
+    p = W.random_problem(30, 20, order=4, seed=31)
+    o = oracle.si_solve(p, fixed_iters=5, cfl_p=0.5, beta=4.0)
+    r = _solve(gs, p, scheme=gs.SCHEME_SI, precision=gs.FP32_SWEEP, fixed_iters=5, max_iter=5, cfl_p=0.5,
+               beta=4.0)
+    assert rel(r["rho"].cpu().numpy(), o["rho"]) < TOL32
+
+
 @pytest.mark.parametrize("scheme", ["si", "gsis"])
 def test_uniform_square_converged_parity(gs, scheme):
     """The 64x64 S8 workload to Err < 1e-8: same iteration count as the
