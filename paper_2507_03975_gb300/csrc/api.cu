@@ -560,7 +560,7 @@ int gsis_solve(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis_op
             TIMED(GSIS_KCLASS_MOMENTS, P.order == 2 ? 2 : 1,
                   launch_moments_to(P, gsis, false, P.rho_h, nullptr, nullptr, false, P.fb, false, st));
             if (gsis) {
-                TIMED(GSIS_KCLASS_HOT_RHS, 2, launch_hot_rhs(P, P.rho_h, P.Fx, P.Fy, P.fb, P.rho_m, st));
+                TIMED(GSIS_KCLASS_HOT_RHS, 1, launch_hot_rhs(P, P.rho_h, P.Fx, P.Fy, P.fb, P.rho_m, st, true));
                 TIMED(GSIS_KCLASS_SYNTH, 1, launch_synthetic_solve(P, P.rho_m, P.x, st));
                 TIMED(GSIS_KCLASS_UPDATE, 1, launch_update(P, P.x, st));
             } else {

@@ -160,8 +160,11 @@ int sweep_max_active_blocks(int fp32, int pt);
 cudaError_t launch_source_from(const Plan& P, const double* rho_in, cudaStream_t st);
 // HoT, right-hand side b and the first residual b - D guess of the synthetic
 // solve (FP32 copy in mg.r0, norms at partials + 4 * kMaxCgBlocks).
+// fuse: one launch that forms HoT inside the right-hand side (hotx / hoty
+// are then not written); the two-launch form for the batched, time-dependent
+// and single-step paths (faster there, or hotx wanted)
 cudaError_t launch_hot_rhs(const Plan& P, const double* rho_h, const double* Fx, const double* Fy,
-                           const double* fb, const double* guess, cudaStream_t st);
+                           const double* fb, const double* guess, cudaStream_t st, bool fuse = false);
 cudaError_t launch_mg_setup(const Plan& P, cudaStream_t st);
 cudaError_t plan_synthetic(Plan& P);   // before the first solve launch (no runtime calls in the launch)
 cudaError_t launch_synthetic_solve(const Plan& P, const double* guess, double* out, cudaStream_t st);

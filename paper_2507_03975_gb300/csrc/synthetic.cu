@@ -43,22 +43,38 @@ struct HotArgs {
 };
 
 // HoT = F + G / (3 sigma_t) with the gradient weights of the cell set-up.
+// HoT of cell c = (i, j) (Eq. (GSIS_HoT)): F + the least-squares gradient of
+// rho with 1/(3 sigma_t) folded into the weights hw; one operation sequence
+// for every kernel that forms it, so stored and recomputed values agree bit
+// for bit.
+__device__ __forceinline__ double hot_x(const double* hw, const double* rho, const double* Fx, int N, int nx,
+                                        int c, int i)
+{
+    const double ri = rho[c];
+    double gx = 0.0;
+    if (i + 1 < nx) gx = fma(hw[c], rho[c + 1] - ri, gx);
+    if (i > 0) gx = fma(hw[N + c], rho[c - 1] - ri, gx);
+    return Fx[c] + gx;
+}
+
+__device__ __forceinline__ double hot_y(const double* hw, const double* rho, const double* Fy, int N, int nx,
+                                        int ny, int c, int j)
+{
+    const double ri = rho[c];
+    double gy = 0.0;
+    if (j + 1 < ny) gy = fma(hw[2 * N + c], rho[c + nx] - ri, gy);
+    if (j > 0) gy = fma(hw[3 * N + c], rho[c - nx] - ri, gy);
+    return Fy[c] + gy;
+}
+
 __device__ __forceinline__ void hot_body(const HotArgs& a, int bid, int nblk)
 {
     if (ld_volatile_int(a.done)) return;
     const int nx = a.nx, ny = a.ny, N = nx * ny;
-    const double* hw = a.hw; const double* rho = a.rho; const double* Fx = a.Fx; const double* Fy = a.Fy;
-    double* hotx = a.hotx; double* hoty = a.hoty;
     for (int c = bid * blockDim.x + threadIdx.x; c < N; c += nblk * blockDim.x) {
         const int j = c / nx, i = c - j * nx;
-        const double ri = rho[c];
-        double gx = 0.0, gy = 0.0;
-        if (i + 1 < nx) gx = fma(hw[c], rho[c + 1] - ri, gx);
-        if (i > 0) gx = fma(hw[N + c], rho[c - 1] - ri, gx);
-        if (j + 1 < ny) gy = fma(hw[2 * N + c], rho[c + nx] - ri, gy);
-        if (j > 0) gy = fma(hw[3 * N + c], rho[c - nx] - ri, gy);
-        hotx[c] = Fx[c] + gx;
-        hoty[c] = Fy[c] + gy;
+        a.hotx[c] = hot_x(a.hw, a.rho, a.Fx, N, nx, c, i);
+        a.hoty[c] = hot_y(a.hw, a.rho, a.Fy, N, nx, ny, c, j);
     }
 }
 
@@ -69,6 +85,7 @@ struct RhsArgs {
     const double* dx; const double* dy;
     const double* sigt; const double* q; const double* rho_h;
     const double* hotx; const double* hoty; const double* fb; const double* bface;
+    const double* hw; const double* Fx; const double* Fy;   // FUSE: HoT recomputed from rho_h, Fx, Fy
     double* b;
     // first residual of the synthetic solve, r0 = b - D guess
     const double* diag; const double* cx; const double* cy; const double* guess;
@@ -80,6 +97,9 @@ struct RhsArgs {
 
 // b, then r0 = b - D guess (five-point D) and the fixed-order sums r0.r0, b.b
 // (last-block ticket).  Block bid of the problem's nblk blocks.
+// FUSE: HoT formed here at the cell and its neighbours (the same operations
+// as hot_body, so the same b) instead of read from hotx / hoty.
+template <bool FUSE = false>
 __device__ __forceinline__ void rhs_body(const RhsArgs& a, int bid, int nblk)
 {
     __shared__ double sm[33];
@@ -94,11 +114,20 @@ __device__ __forceinline__ void rhs_body(const RhsArgs& a, int bid, int nblk)
         const double hx = dx[i], hy = dy[j];
         // explicit fma: the single-problem and batched kernels that inline
         // this body then round identically
+        auto HX = [&](int cc, int ii) {
+            if constexpr (FUSE) return hot_x(a.hw, a.rho_h, a.Fx, N, nx, cc, ii);
+            else return hotx[cc];
+        };
+        auto HY = [&](int cc, int jj) {
+            if constexpr (FUSE) return hot_y(a.hw, a.rho_h, a.Fy, N, nx, ny, cc, jj);
+            else return hoty[cc];
+        };
+        const double hxc = HX(c, i), hyc = HY(c, j);
         double v = hx * hy * a.q[c];
-        if (i + 1 < nx) v = fma(-0.5 * hy, hotx[c] + hotx[c + 1], v);
-        if (i > 0) v = fma(0.5 * hy, hotx[c] + hotx[c - 1], v);
-        if (j + 1 < ny) v = fma(-0.5 * hx, hoty[c] + hoty[c + nx], v);
-        if (j > 0) v = fma(0.5 * hx, hoty[c] + hoty[c - nx], v);
+        if (i + 1 < nx) v = fma(-0.5 * hy, hxc + HX(c + 1, i + 1), v);
+        if (i > 0) v = fma(0.5 * hy, hxc + HX(c - 1, i - 1), v);
+        if (j + 1 < ny) v = fma(-0.5 * hx, hyc + HY(c + nx, j + 1), v);
+        if (j > 0) v = fma(0.5 * hx, hyc + HY(c - nx, j - 1), v);
         const double rh = a.rho_h[c];
         const double* bf = a.bface;
         if (i == 0) v -= fma(hy, fb[j], -(bf[j] * rh));
@@ -140,7 +169,8 @@ __device__ __forceinline__ void rhs_body(const RhsArgs& a, int bid, int nblk)
     }
 }
 
-__global__ void __launch_bounds__(kRedBlock) rhs_kernel(const RhsArgs a) { rhs_body(a, blockIdx.x, gridDim.x); }
+template <bool FUSE>
+__global__ void __launch_bounds__(kRedBlock) rhs_kernel(const RhsArgs a) { rhs_body<FUSE>(a, blockIdx.x, gridDim.x); }
 
 struct UpdArgs {
     int nx, ny, N;
@@ -277,13 +307,19 @@ UpdArgs upd_args(const Plan& P, const double* rho_new)
 }  // namespace
 
 cudaError_t launch_hot_rhs(const Plan& P, const double* rho_h, const double* Fx, const double* Fy,
-                           const double* fb, const double* guess, cudaStream_t st)
+                           const double* fb, const double* guess, cudaStream_t st, bool fuse)
 {
+    if (fuse) {   // one launch, HoT formed where the right-hand side needs it; hotx / hoty not written
+        RhsArgs a = rhs_args(P, rho_h, fb, guess);
+        a.hw = P.hw; a.Fx = Fx; a.Fy = Fy;
+        rhs_kernel<true><<<P.red_grid, kRedBlock, 0, st>>>(a);
+        return cudaGetLastError();
+    }
     const int g = grid_for(P.N, 256, P.num_sms * 8);
     hot_kernel<<<g, 256, 0, st>>>(hot_args(P, rho_h, Fx, Fy));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    rhs_kernel<<<P.red_grid, kRedBlock, 0, st>>>(rhs_args(P, rho_h, fb, guess));
+    rhs_kernel<false><<<P.red_grid, kRedBlock, 0, st>>>(rhs_args(P, rho_h, fb, guess));
     return cudaGetLastError();
 }
 
@@ -355,7 +391,7 @@ cudaError_t launch_hot_rhs_batch(const BatchTables& bt, cudaStream_t st)
         static_cast<const HotArgs*>(bt.hot), bt.hot_bstart, bt.B);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    batch_kernel<RhsArgs, rhs_body><<<bt.rhs_blocks, kRedBlock, 0, st>>>(
+    batch_kernel<RhsArgs, rhs_body<false>><<<bt.rhs_blocks, kRedBlock, 0, st>>>(
         static_cast<const RhsArgs*>(bt.rhs), bt.rhs_bstart, bt.B);
     return cudaGetLastError();
 }
