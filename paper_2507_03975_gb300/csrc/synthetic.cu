@@ -323,32 +323,68 @@ cudaError_t launch_hot_rhs(const Plan& P, const double* rho_h, const double* Fx,
     return cudaGetLastError();
 }
 
+// Ordinates per thread in the per-ordinate source kernels: all their loads
+// are in flight before the stores.
+template <typename T>
+__host__ __device__ constexpr int ord_slab() { return sizeof(T) == 4 ? 16 : 8; }
+
+// X[k][c] = fma(shift_c, I[k][c], src_c) over tiles of (blockDim.x cells) x
+// (ord_slab ordinates), tile t = bid, bid + nblk, ...: coalesced rows, no
+// per-element division.
+template <typename T>
+__device__ __forceinline__ void ord_tiles(int N, int K, const T* __restrict__ shift, const T* __restrict__ I,
+                                          const T* __restrict__ src, T* __restrict__ X, int bid, int nblk)
+{
+    constexpr int S = ord_slab<T>();
+    const int cb = (N + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int ntiles = cb * ((K + S - 1) / S);
+    for (int tile = bid; tile < ntiles; tile += nblk) {
+        const int slab = tile / cb;
+        const int c = (tile - slab * cb) * (int)blockDim.x + (int)threadIdx.x;
+        if (c >= N) continue;
+        const int k0 = slab * S;
+        const T sh = shift[c], sv = src[c];
+        const T* Ik = I + (size_t)k0 * N + c;
+        T* Xk = X + (size_t)k0 * N + c;
+        T v[S];
+#pragma unroll
+        for (int kk = 0; kk < S; ++kk) v[kk] = k0 + kk < K ? Ik[(size_t)kk * N] : T(0);
+#pragma unroll
+        for (int kk = 0; kk < S; ++kk)
+            if (k0 + kk < K) Xk[(size_t)kk * N] = fma(sh, v[kk], sv);   // float: the FP32 overload
+    }
+}
+
+int ord_tile_count(int N, int K, int fp32)
+{
+    const int S = fp32 ? ord_slab<float>() : ord_slab<double>();
+    return ((N + kRedBlock - 1) / kRedBlock) * ((K + S - 1) / S);
+}
+
 // The pseudo-time / time-step sweep's source per ordinate, formed as that
 // sweep would form it: X[k][c] = fma(shift_c, I[k][c], src_c) (FP64 or FP32).
 template <typename T>
-__global__ void ordinate_source_kernel(int N, const T* __restrict__ shift, const T* __restrict__ I,
-                                       const T* __restrict__ src, T* X, const int* done)
+__global__ void __launch_bounds__(kRedBlock) ordinate_source_kernel(int N, int K, const T* __restrict__ shift,
+                                                                    const T* __restrict__ I,
+                                                                    const T* __restrict__ src, T* X,
+                                                                    const int* done)
 {
     if (ld_volatile_int(done)) return;
-    const size_t row = (size_t)blockIdx.y * N;   // ordinate blockIdx.y
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
-        if constexpr (sizeof(T) == 4) X[row + c] = fmaf(shift[c], I[row + c], src[c]);   // one FP32 rounding
-        else X[row + c] = fma(shift[c], I[row + c], src[c]);
-    }
+    ord_tiles<T>(N, K, shift, I, src, X, blockIdx.x, gridDim.x);
 }
 
 cudaError_t launch_ordinate_source(const Plan& P, cudaStream_t st)
 {
-    const dim3 grid(grid_for(P.N, 256, std::max(1, P.num_sms * 16 / P.K)), P.K);
+    const int grid = std::max(1, std::min(ord_tile_count(P.N, P.K, P.fp32), P.num_sms * 8));
     // the stored intensities the pseudo-time sweep reads: I^m in place, or a
     // time step's I^n
     const void* iold = P.In ? P.In : P.I;
     if (P.fp32)
-        ordinate_source_kernel<float><<<grid, 256, 0, st>>>(P.N, P.shift_f, static_cast<const float*>(iold),
-                                                            P.src_f, P.X_f, &P.status->done);
+        ordinate_source_kernel<float><<<grid, kRedBlock, 0, st>>>(
+            P.N, P.K, P.shift_f, static_cast<const float*>(iold), P.src_f, P.X_f, &P.status->done);
     else
-        ordinate_source_kernel<double><<<grid, 256, 0, st>>>(P.N, P.shift, static_cast<const double*>(iold),
-                                                             P.src, P.X, &P.status->done);
+        ordinate_source_kernel<double><<<grid, kRedBlock, 0, st>>>(
+            P.N, P.K, P.shift, static_cast<const double*>(iold), P.src, P.X, &P.status->done);
     return cudaGetLastError();
 }
 
@@ -405,29 +441,10 @@ struct OrdArgs {
     const int* done;
 };
 
-constexpr int kOrdSlab = 16;   // ordinates per thread: all their loads in flight before the stores
-
 __device__ __forceinline__ void ord_body(const OrdArgs& a, int bid, int nblk)
 {
     if (ld_volatile_int(a.done)) return;
-    // tiles of (blockDim.x cells) x (kOrdSlab ordinates); coalesced rows, no per-element division
-    const int cb = (a.N + (int)blockDim.x - 1) / (int)blockDim.x;
-    const int ntiles = cb * ((a.K + kOrdSlab - 1) / kOrdSlab);
-    for (int tile = bid; tile < ntiles; tile += nblk) {
-        const int slab = tile / cb;
-        const int c = (tile - slab * cb) * (int)blockDim.x + (int)threadIdx.x;
-        if (c >= a.N) continue;
-        const int k0 = slab * kOrdSlab;
-        const float sh = a.shift[c], sv = a.src[c];
-        const float* __restrict__ I = a.I + (size_t)k0 * a.N + c;
-        float* __restrict__ X = a.X + (size_t)k0 * a.N + c;
-        float v[kOrdSlab];
-#pragma unroll
-        for (int kk = 0; kk < kOrdSlab; ++kk) v[kk] = k0 + kk < a.K ? I[(size_t)kk * a.N] : 0.f;
-#pragma unroll
-        for (int kk = 0; kk < kOrdSlab; ++kk)
-            if (k0 + kk < a.K) X[(size_t)kk * a.N] = fmaf(sh, v[kk], sv);
-    }
+    ord_tiles<float>(a.N, a.K, a.shift, a.I, a.src, a.X, bid, nblk);
 }
 
 size_t ord_batch_rec_bytes() { return sizeof(OrdArgs); }
@@ -440,8 +457,7 @@ int ord_batch_rec(const Plan& P, void* out)
     a.X = P.X_f;
     a.done = &P.status->done;
     std::memcpy(out, &a, sizeof(a));
-    const long long tiles = (long long)((P.N + kRedBlock - 1) / kRedBlock) * ((P.K + kOrdSlab - 1) / kOrdSlab);
-    return (int)std::min<long long>(tiles, (long long)P.num_sms * 8);
+    return std::min(ord_tile_count(P.N, P.K, 1), P.num_sms * 8);
 }
 
 cudaError_t launch_ordsrc_batch(const BatchTables& bt, cudaStream_t st)
