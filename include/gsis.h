@@ -270,11 +270,17 @@ int gsis_td_workspace_bytes(const gsis_mesh* mesh, const gsis_quadrature* quad, 
  * last sweep) or NULL.  step_iters, step_err: HOST [nsteps] out or NULL,
  * inner iterations and final Err of every step.
  * opt: scheme, precision, tol / max_iter / fixed_iters per step, synthetic
- * controls, check_every, wait_limit_s; pseudo-time must be off (cfl_p, beta
- * <= 0, else GSIS_ERR_ARG).  Synchronises the stream.
- * Returns GSIS_OK when every step converged; GSIS_ERR_MAXITER or
- * GSIS_ERR_DIVERGED when a step did not (the solve stops there and rho, T
- * hold that step's last iterate); argument, CUDA, timeout, workspace errors.
+ * controls, check_every, stall_window, wait_limit_s; pseudo-time must be off
+ * (cfl_p, beta <= 0, else GSIS_ERR_ARG).  Synchronises the stream.
+ * stall_window > 0 (without fixed_iters): a step whose Err has reached no new
+ *   minimum for stall_window checks (of check_every iterations) ends there,
+ *   at its floor, and the run goes on with the next step; step_err holds the
+ *   floor reached.  FP32 sweeps stop near Err = 1e-8 on some steps.
+ * Returns GSIS_OK when every step converged; GSIS_ERR_STALLED when every
+ * step converged or stalled and at least one stalled (all nsteps were run;
+ * rho, T hold the final state); GSIS_ERR_MAXITER or GSIS_ERR_DIVERGED when a
+ * step did neither (the solve stops there and rho, T hold that step's last
+ * iterate); argument, CUDA, timeout, workspace errors.
  */
 int gsis_td_solve(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis_options* opt,
                   const gsis_time_params* tp, const double* sigma_a, const double* sigma_s, const double* q,
@@ -445,8 +451,11 @@ int gsis_batch_autotune(gsis_problem* probs, int n, const gsis_options* opt, int
  * (32 MiB) inside the library.  Every GPU on which the library's kernels are
  * loaded keeps that array reserved until the process exits.
  * Arguments, layouts and results are those of gsis_transport_sweep().
- * Problems whose gsis_workspace_bytes() exceeds the array are rejected with
- * GSIS_ERR_WORKSPACE before any device work.  The first call on a device
+ * Problems whose kinetic-step workspace exceeds the array are rejected with
+ * GSIS_ERR_WORKSPACE before any device work: the workspace that
+ * gsis_transport_sweep() needs, which runs first-order upwind without
+ * pseudo-time whatever opt asks (gsis_workspace_bytes() of the same options
+ * with spatial_order = 1 and cfl_p = beta = 0).  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress, once per
  * device): make that first call before any stream capture.  All calls share
  * the one array, which keeps the last call's contents (each call clears what

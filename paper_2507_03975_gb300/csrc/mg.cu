@@ -41,6 +41,9 @@ int grid_for(long long n, int block, int cap)
     return (int)g;
 }
 
+// Quiet NaN written into a synthetic solution whose residual is not finite.
+__device__ constexpr double kNaN = __builtin_nan("");
+
 // ------------------------------------------------------------ set-up
 __global__ void mg_copy_fine_kernel(int N, const double* __restrict__ d, const double* __restrict__ cx,
                                     const double* __restrict__ cy, double* d64, double* cx64, double* cy64,
@@ -618,6 +621,20 @@ __device__ __forceinline__ void mg_solve_body(const MgArgs& a, Ctx& cx)
             cx.sum2f(l0, l1, f2, slots_f, rotf);
         }
         float rz = f2[0];
+        if (!(rz > 0.f) || !(rz < INFINITY) || !isfinite(rr[0])) {
+            // No usable FP32 search direction, so the inner loop could not
+            // advance `total` and nothing else would end the refinement: a
+            // residual beyond the FP32 range or not finite (a diverging GSIS
+            // iteration), or one that vanished in FP32.  Leave; a non-finite
+            // one poisons x so that Err(rho) reports the divergence.  rz and
+            // rr are the same in every CTA, so all leave together.
+            const bool bad = !(rz == 0.f) || !isfinite(rr[0]);
+            if (bad) {
+                for (int c = G.start; c < N; c += stride) a.x[c] = kNaN;
+                relres = kNaN;
+            }
+            break;
+        }
         const float s00 = f2[1];
         const float istop = a.inner_rtol * a.inner_rtol * s00;
         while (total < a.max_iter && rz > 0.f) {
@@ -1196,6 +1213,16 @@ __device__ __forceinline__ void strip_body(const SArgs& a)
             cx.sum2<float>(l0, l1, f2, slots_f, rotf, wsm_f);
         }
         float rz = f2[0];
+        if (!(rz > 0.f) || !(rz < INFINITY) || !isfinite(rr)) {
+            // as in mg_solve_body: no usable FP32 search direction, leave the
+            // refinement (every CTA holds the same rz and rr); a non-finite
+            // residual poisons x, a vanished one keeps the current x
+            const bool bad = !(rz == 0.f) || !isfinite(rr);
+            const double* xo = outer == 0 ? a.guess : a.x;
+            for (int c = threadIdx.x; c < n0; c += blockDim.x) a.x[g00 + c] = bad ? kNaN : xo[g00 + c];
+            if (bad) relres = kNaN;
+            break;
+        }
         const float istop = a.inner_rtol * a.inner_rtol * f2[1];
         while (total < a.max_iter && rz > 0.f) {
             // the previous barrier published p and its halo rows

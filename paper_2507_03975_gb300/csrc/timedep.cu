@@ -210,6 +210,31 @@ cudaError_t launch_td_update(const Plan& P, const TdArgs& a, cudaStream_t st)
     return cudaGetLastError();
 }
 
+cudaError_t launch_td_begin(const TdArgs& a, int g, cudaStream_t st)
+{
+    td_begin_kernel<<<g, kRedBlock, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_td_step_operator(const Plan& P, const TdArgs& a, int g, cudaStream_t st)
+{
+    td_coef_kernel<<<g, kRedBlock, 0, st>>>(a);
+    const cudaError_t e = cudaGetLastError();
+    return e != cudaSuccess ? e : launch_mg_setup(P, st);
+}
+
+cudaError_t launch_td_source(const TdArgs& a, int g, cudaStream_t st)
+{
+    td_source_kernel<<<g, kRedBlock, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_td_end_si(const TdArgs& a, int g, cudaStream_t st)
+{
+    td_end_si_kernel<<<g, kRedBlock, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
 TdArgs td_args(const Plan& P, const gsis_time_params* tp, int gsis)
 {
     TdArgs a{};
@@ -254,24 +279,26 @@ int check_tp(const gsis_time_params* tp, const gsis_options* opt)
 
 // One backward-Euler step from the state held in the plan (rho_m, T, the
 // correction cnext and In: I^n = In + cn); leaves the step's last iterate
-// (I = I^{m+1/2}, rho_h, rho_m, T, cnext) and its status in S.
-int run_step(Plan& P, const gsis_time_params* tp, const gsis_options* opt, int gsis, Status& S, cudaStream_t st)
+// (I = I^{m+1/2}, rho_h, rho_m, T, cnext) and its status in S.  With
+// opt->stall_window > 0 (and no fixed iteration count) the step also ends
+// when Err has not reached a new minimum for that many checks; *stalled
+// says so (the FP32 kinetic step has a floor of Err near 1e-8).
+int run_step(Plan& P, const gsis_time_params* tp, const gsis_options* opt, int gsis, Status& S, cudaStream_t st,
+             bool* stalled = nullptr)
 {
     int rc;
     const int g = grid_for(P.N, kRedBlock, P.num_sms * 8);
     const int nmax = opt->fixed_iters > 0 ? opt->fixed_iters : opt->max_iter;
     const TdArgs a = td_args(P, tp, gsis);
     CK(cudaMemsetAsync(P.status, 0, sizeof(Status), st));
-    td_begin_kernel<<<g, kRedBlock, 0, st>>>(a);
-    CK(cudaGetLastError());
-    if (gsis) {   // multigrid hierarchy of the step's operator (coupling at T^n)
-        td_coef_kernel<<<g, kRedBlock, 0, st>>>(a);
-        CK(cudaGetLastError());
-        CK(launch_mg_setup(P, st));
-    }
-    td_source_kernel<<<g, kRedBlock, 0, st>>>(a);
-    CK(cudaGetLastError());
-    if (P.X || P.X_f) CK(launch_ordinate_source(P, st));
+    TIMED(GSIS_KCLASS_SETUP, 1, launch_td_begin(a, g, st));
+    if (gsis)   // multigrid hierarchy of the step's operator (coupling at T^n): 1 + nl kernels
+        TIMED(GSIS_KCLASS_SETUP, 1 + P.mg.nl, launch_td_step_operator(P, a, g, st));
+    TIMED(GSIS_KCLASS_SETUP, 1, launch_td_source(a, g, st));
+    if (P.X || P.X_f) TIMED(GSIS_KCLASS_SETUP, 1, launch_ordinate_source(P, st));
+    if (stalled) *stalled = false;
+    double best = INFINITY;
+    int since_best = 0;
     int launched = 0;
     while (launched < nmax) {
         const int batch = std::min(opt->check_every, nmax - launched);
@@ -289,11 +316,17 @@ int run_step(Plan& P, const gsis_time_params* tp, const gsis_options* opt, int g
         launched += batch;
         if ((rc = read_status(S, P, st))) return rc;
         if (S.done) break;
+        if (opt->stall_window > 0 && opt->fixed_iters <= 0) {
+            if (S.err < best) {
+                best = S.err;
+                since_best = 0;
+            } else if (++since_best >= opt->stall_window) {
+                if (stalled) *stalled = true;
+                break;
+            }
+        }
     }
-    if (!gsis) {
-        td_end_si_kernel<<<g, kRedBlock, 0, st>>>(a);
-        CK(cudaGetLastError());
-    }
+    if (!gsis) TIMED(GSIS_KCLASS_SETUP, 1, launch_td_end_si(a, g, st));
     return GSIS_OK;
 }
 
@@ -305,6 +338,19 @@ int step_result(const Status& S, int n)
     return GSIS_OK;
 }
 
+cudaError_t launch_td_init(const Plan& P, const TdArgs& a, int g, const double* rho0, const double* T0,
+                           cudaStream_t st)
+{
+    td_init_kernel<<<g, kRedBlock, 0, st>>>(a, rho0, T0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t n = (size_t)P.K * P.N;
+    const int gi = grid_for((long long)n, 256, P.num_sms * 16);
+    if (P.fp32) fill_iso_kernel<float><<<gi, 256, 0, st>>>(static_cast<float*>(P.In), P.K, P.N, rho0);
+    else fill_iso_kernel<double><<<gi, 256, 0, st>>>(static_cast<double*>(P.In), P.K, P.N, rho0);
+    return cudaGetLastError();
+}
+
 // Start of a run: the step-independent synthetic diagonal, rho^0, T^0 and
 // I^0 = rho^0/4pi in In.
 int td_start(Plan& P, const gsis_time_params* tp, int gsis, const double* rho0, const double* T0, cudaStream_t st)
@@ -312,13 +358,7 @@ int td_start(Plan& P, const gsis_time_params* tp, int gsis, const double* rho0, 
     const int g = grid_for(P.N, kRedBlock, P.num_sms * 8);
     const TdArgs a = td_args(P, tp, gsis);
     CK(cudaMemcpyAsync(P.td.diag0, P.diag, (size_t)P.N * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    td_init_kernel<<<g, kRedBlock, 0, st>>>(a, rho0, T0);
-    CK(cudaGetLastError());
-    const size_t n = (size_t)P.K * P.N;
-    const int gi = grid_for((long long)n, 256, P.num_sms * 16);
-    if (P.fp32) fill_iso_kernel<float><<<gi, 256, 0, st>>>(static_cast<float*>(P.In), P.K, P.N, rho0);
-    else fill_iso_kernel<double><<<gi, 256, 0, st>>>(static_cast<double*>(P.In), P.K, P.N, rho0);
-    CK(cudaGetLastError());
+    TIMED(GSIS_KCLASS_SETUP, 2, launch_td_init(P, a, g, rho0, T0, st));
     return GSIS_OK;
 }
 
@@ -443,13 +483,22 @@ int gsis_td_solve(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis
     if ((rc = read_status(S, P, st))) return rc;
 
     int result = GSIS_OK;
+    int n_stalled = 0, first_stalled = -1;
     for (int n = 0; n < tp->nsteps; ++n) {
         if (n > 0) std::swap(P.I, P.In);   // I^n = the last sweep's intensities (+ cn)
-        if ((rc = run_step(P, tp, opt, gsis, S, st))) return rc;
+        bool stalled = false;
+        if ((rc = run_step(P, tp, opt, gsis, S, st, &stalled))) return rc;
         if (step_iters) step_iters[n] = S.iter;
         if (step_err) step_err[n] = S.err;
+        if (stalled) {   // the step ends at its floor of Err; the run goes on
+            if (n_stalled++ == 0) first_stalled = n;
+            continue;
+        }
         if ((result = step_result(S, n)) != GSIS_OK) break;
     }
+    if (result == GSIS_OK && n_stalled > 0)
+        result = fail(GSIS_ERR_STALLED, "%d of %d steps ended on a stalled Err (first: step %d)", n_stalled,
+                      tp->nsteps, first_stalled);
     if (F) CK(launch_moments_to(P, true, false, P.rho_h, F, nullptr, false, P.fb, true, st));
     CK(cudaMemcpyAsync(rho, P.rho_m, (size_t)P.N * sizeof(double), cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(T, P.td.T, (size_t)P.N * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -522,8 +571,9 @@ int gsis_td_adjoint(const gsis_mesh* mesh, const gsis_quadrature* quad, const gs
             CK(cudaMemcpyAsync(A.ck_I[n / C], P.In, KN * Ts, cudaMemcpyDeviceToDevice, st));
             if ((rc = save_state(A.ck_v[n / C]))) return rc;
         }
-        if ((rc = run_step(P, tp, opt, 1, S, st))) return rc;
-        if ((rc = step_result(S, n))) return rc;
+        bool stalled = false;   // a stalled step ends at its floor, as in gsis_td_solve
+        if ((rc = run_step(P, tp, opt, 1, S, st, &stalled))) return rc;
+        if (!stalled && (rc = step_result(S, n))) return rc;
     }
     if (rho) CK(cudaMemcpyAsync(rho, P.rho_m, Nd, cudaMemcpyDeviceToDevice, st));
     if (T) CK(cudaMemcpyAsync(T, P.td.T, Nd, cudaMemcpyDeviceToDevice, st));
@@ -559,8 +609,9 @@ int gsis_td_adjoint(const gsis_mesh* mesh, const gsis_quadrature* quad, const gs
         for (int r = 0; r < n1 - n0; ++r) {
             P.In = r == 0 ? A.ck_I[sg] : A.rec_I[r - 1];
             P.I = A.rec_I[r];
-            if ((rc = run_step(P, tp, opt, 1, S, st))) return rc;
-            if ((rc = step_result(S, n0 + r))) return rc;
+            bool stalled = false;
+            if ((rc = run_step(P, tp, opt, 1, S, st, &stalled))) return rc;
+            if (!stalled && (rc = step_result(S, n0 + r))) return rc;
             double* rv = A.rec_v[r];
             CK(cudaMemcpyAsync(rv, P.rho_h, Nd, cudaMemcpyDeviceToDevice, st));
             CK(cudaMemcpyAsync(rv + N, P.rho_m, Nd, cudaMemcpyDeviceToDevice, st));
