@@ -384,6 +384,21 @@ Sizes sizes_of(const gsis_mesh* m, const gsis_quadrature* q, const gsis_options*
     return z;
 }
 
+gsis_options sweep_options(const gsis_options* o)
+{
+    gsis_options r = *o;
+    r.cfl_p = 0.0;
+    r.beta = 0.0;
+    r.spatial_order = 1;
+    return r;
+}
+
+Sizes sweep_sizes(const gsis_mesh* m, const gsis_quadrature* q, const gsis_options* o)
+{
+    const gsis_options r = sweep_options(o);
+    return sizes_of(m, q, &r);
+}
+
 Sizes solve_sizes(const gsis_mesh* m, const gsis_quadrature* q, const gsis_options* o)
 {
     Sizes z = sizes_of(m, q, o);
@@ -609,11 +624,8 @@ int gsis_transport_sweep(const gsis_mesh* mesh, const gsis_quadrature* quad, con
     if ((rc = check_mesh(mesh)) || (rc = check_quad(quad)) || (rc = check_opt(opt))) return rc;
     if (!sigma_a || !sigma_s || !q || !rho_in || !rho_half || !F_half)
         return fail(GSIS_ERR_ARG, "a required device pointer is NULL");
-    gsis_options o = *opt;
-    o.cfl_p = 0.0;
-    o.beta = 0.0;
-    o.spatial_order = 1;
-    const Sizes z = sizes_of(mesh, quad, &o);
+    const gsis_options o = sweep_options(opt);
+    const Sizes z = sweep_sizes(mesh, quad, opt);
     if ((rc = check_ws(workspace, workspace_bytes, layout(z, nullptr, nullptr)))) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Plan P{};

@@ -63,6 +63,10 @@ Sizes sizes_of(const gsis_mesh* m, const gsis_quadrature* q, const gsis_options*
 // The sizes of gsis_solve: with the FP64 pseudo-time form, also the
 // per-ordinate source of the sweep.
 Sizes solve_sizes(const gsis_mesh* m, const gsis_quadrature* q, const gsis_options* o);
+// The options gsis_transport_sweep runs with (first-order upwind, no
+// pseudo-time) and the sizes of its workspace.
+gsis_options sweep_options(const gsis_options* o);
+Sizes sweep_sizes(const gsis_mesh* m, const gsis_quadrature* q, const gsis_options* o);
 // All spacings equal (relative 1e-12).
 bool uniform_spacing(const double* h, int n);
 // Sorted index (quadrant-major, as in prepare) of the reflected direction

@@ -11,8 +11,11 @@
 //  * the array holds kStaticScratchBytes (GSIS_STATIC_SCRATCH_BYTES, 32 MiB);
 //    every GPU on which the library's kernels are loaded keeps it reserved
 //    until the process exits;
-//  * problems whose gsis_workspace_bytes() exceeds it are rejected with
-//    GSIS_ERR_WORKSPACE before any device work;
+//  * problems whose kinetic-step workspace exceeds it are rejected with
+//    GSIS_ERR_WORKSPACE before any device work; that is the workspace of
+//    gsis_transport_sweep() (first-order upwind, no pseudo-time, whatever
+//    the options ask), i.e. gsis_workspace_bytes() with spatial_order = 1,
+//    cfl_p = beta = 0;
 //  * the first call on a device looks the array's device address up with
 //    cudaGetSymbolAddress (once per device, that device current); make that
 //    first call before any stream capture;
@@ -27,6 +30,7 @@
 
 #include "gsis.h"
 #include "gsis_internal.cuh"
+#include "host.h"
 
 namespace {
 
@@ -75,9 +79,10 @@ extern "C" int gsis_transport_sweep_static(const gsis_mesh* mesh, const gsis_qua
                                            const double* rho_in, double* rho_half, double* F_half,
                                            double* P_half, double* bflux, void* stream)
 {
-    size_t need = 0;
-    int rc = gsis_workspace_bytes(mesh, quad, opt, &need);
-    if (rc != GSIS_OK) return rc;
+    int rc;
+    if ((rc = gsis::check_mesh(mesh)) || (rc = gsis::check_quad(quad)) || (rc = gsis::check_opt(opt))) return rc;
+    // the layout gsis_transport_sweep carves (its own option overrides)
+    const size_t need = gsis::layout(gsis::sweep_sizes(mesh, quad, opt), nullptr, nullptr);
     if (need > kStaticScratchBytes) {
         char msg[160];
         snprintf(msg, sizeof msg, "problem needs %zu bytes of scratch, the static array holds %zu", need,

@@ -58,3 +58,23 @@ def test_static_scratch_rejects_oversized_problem(gs):
         gs.transport_sweep_static(p.dx, p.dy, p.mu, p.eta, p.w, z, z, z, z, None, opt)
     assert ei.value.status == gs.GSIS_ERR_WORKSPACE
     assert "static array" in str(ei.value)
+
+
+def test_static_scratch_sizes_the_kinetic_step_not_the_solve(gs):
+    # gsis_transport_sweep runs first-order upwind without pseudo-time
+    # whatever the options ask, so options that enlarge only the full solve's
+    # workspace (second-order faces, pseudo-time) must not get a problem
+    # rejected: 128x128 S12 needs 29 MiB for the sweep, 40 MiB for the solve
+    p = W.random_problem(128, 128, order=12, seed=92)
+    opt = gs.default_options(spatial_order=2, beta=10.0)
+    plain = gs.default_options()
+    assert gs.workspace_bytes(p.dx, p.dy, p.mu, p.eta, p.w, opt) > 32 * 1024 * 1024
+    assert gs.workspace_bytes(p.dx, p.dy, p.mu, p.eta, p.w, plain) <= 32 * 1024 * 1024
+    args = (p.dx, p.dy, p.mu, p.eta, p.w, _t(p.sigma_a), _t(p.sigma_s), _t(p.q))
+    rho_in = _t(np.random.Generator(np.random.PCG64(5)).uniform(0.0, 2.0, p.N))
+    inflow = _t(p.inflow.reshape(-1))
+    for call in range(2):
+        ref = gs.transport_sweep(*args, rho_in, inflow, plain)
+        got = gs.transport_sweep_static(*args, rho_in, inflow, opt)
+        for key in ("rho", "F", "P", "bflux"):
+            assert _rel(got[key], ref[key]) < TOL64, (call, key)
