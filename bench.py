@@ -1,23 +1,36 @@
-"""Benchmark: time-to-converge and cell-direction update rate of GSIS on one
-GB300, the 256x256 S12 thick-medium / thin-channel workload, FP64.
+"""Benchmark: cell-direction update rate and time to converge of GSIS against
+plain source iteration on one GB300, with the roofline of the dominant kernel.
 
-One step = one complete GSIS solve (transport sweeps of every ordinate with
-fused-order angular moments, adaptive least-squares gradients, high-order
-terms, FP64 synthetic solve, Err) from rho = 0 to Err(rho) < 1e-8, inputs
-resident in HBM.  value = (iterations x cells x directions) / time, summed
-over steps and ranks.  L2 is flushed (512 MiB write) before every step.
+Headline workload: the time-dependent gray radiation-material problem
+(Sec. 2.1, Eqs. (RTE_g), (Tm_g); backward Euler, Sec. 4.1), 1024 x 1024
+cells on the unit square, S16 (144 directions), a thin bent channel
+(sigma_t 0.2, 32 cells wide) in a thick medium (sigma_t 2000), scattering
+ratio 0.999, unit isotropic intensity through the left wall, vacuum
+elsewhere, a = c = C_v = 1, cold start T = 0.1, 100 backward-Euler steps of
+dt = 1e-3; GSIS with FP64 sweeps, moments and synthetic solve, every step
+iterated to Err(rho) < 1e-8.
+
+One step of this benchmark = one complete gsis_td_solve call (all 100 time
+steps: every kinetic sweep with its moments, adaptive least-squares
+gradients, high-order terms, the rho-T synthetic solve, the material update)
+from the initial state, inputs resident in HBM.  value = (inner iterations x
+cells x directions) / time, summed over steps and ranks.  The two FP64
+intensity arrays of a time step (1.2 GB each) exceed L2, and L2 is also
+flushed (512 MiB write) before every run.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
---impl reference times the FP64 CPU oracle (the reference arm) on a
-bounded sample of the same workload on the host cores.  Under torchrun every
-rank runs an independent replica (no collective in the data path); rank 0
-prints one JSON line.
+--impl reference times the FP64 CPU oracle (the reference arm) on bounded
+samples of the same workload on the host cores.  Under torchrun every rank
+runs an independent replica (no collective in the data path); rank 0 prints
+one JSON line.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -36,25 +49,14 @@ import workloads as W  # noqa: E402
 METRIC = "cell-direction updates/s and time-to-converge (GSIS vs SI) on 1 GB300; HBM roofline %"
 UNIT = "cell-direction updates/s"
 TOL = 1e-8
-BETA = 10.0   # local pseudo-time control (Sec. 4.3) the 2000/0.2 opacity jump needs
-SWEEP_CAPTURE_SHA256 = "7bbbe3b4e539116b"   # sweep.cu at the ncu capture behind _sweep_traffic()
-SYNTH_CAP = 2  # inner iterations of the synthetic solve per GSIS iteration (capped sub-iterations, Sec. 4.2)
-TD_SYNTH_CAP = 4  # the same cap on the 1024^2 time-dependent workload (its measured optimum: 2 -> 19, 4 -> 8 iterations per step)
+BETA = 10.0        # local pseudo-time control (Sec. 4.3) the steady 2000/0.2 opacity jump needs
+SYNTH_CAP = 2      # inner iterations of the synthetic solve per GSIS iteration, steady channel (Sec. 4.2)
+TD_SYNTH_CAP = 4   # the same cap on the time-dependent workload (its measured optimum)
+TD_CHECK_EVERY = 4
+FP32_STALL = (2, 5)   # check_every, stall_window: an FP32 step ends after 10 iterations without a new minimum
 
 
-def _workload(args=None):
-    p = W.config_channel()
-    cap = getattr(args, "synth_cap", SYNTH_CAP) if args is not None else SYNTH_CAP
-    return p, dict(workload="channel_256x256_S12_seed2", nx=p.nx, ny=p.ny, K=p.K, scheme="gsis",
-                   beta=BETA, tol=TOL, precision="fp64",
-                   synthetic=f"FP64 iterative refinement, FP32 multigrid-CG inner iterations capped at {cap} "
-                             "per GSIS iteration (warm-started; same fixed point)" if cap > 0 else
-                             "solved to relative residual 1e-12",
-                   l2="flushed before each step (512 MiB write); per-solve working set ~149 MB",
-                   kernel_timing="a second pass of the same solves with CUDA events around every kernel "
-                                 "class (roofline, shares); value and ms_per_step from the uninstrumented pass")
-
-
+# ----------------------------------------------------------------- helpers
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -76,14 +78,16 @@ def replica_totals(dist, units, ms, device):
     return float(u.item()), float(t.item())
 
 
+CLOCK_FIELDS = ("uuid,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
 def _clock_sampler():
     """nvidia-smi clocks/throttle sampling during the timed region."""
     f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
-    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
     try:
-        proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+        proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={CLOCK_FIELDS}", "--format=csv,noheader,nounits",
                                  "-lms", "20"], stdout=f, stderr=subprocess.DEVNULL)
     except OSError:
         return None, f
@@ -97,7 +101,47 @@ def _clock_sampler():
     return proc, f
 
 
-def _clock_summary(proc, f, gpu_index):
+def device_uuid(torch, dev) -> str | None:
+    """The CUDA device's UUID as nvidia-smi prints it (without the GPU- prefix),
+    or None: nvidia-smi numbers GPUs physically, while CUDA_VISIBLE_DEVICES
+    renumbers them for the process, so the clock samples are matched by UUID."""
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:   # noqa: BLE001
+        return None
+    return u[4:] if u.startswith("GPU-") else u
+
+
+def parse_clock_samples(lines, uuid=None, index=None):
+    """Median SM clock, max clock and active throttle reasons of the samples
+    of one GPU (matched by UUID, else by nvidia-smi index)."""
+    sm, smax, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in lines:
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 10:
+            continue
+        u = parts[0][4:] if parts[0].startswith("GPU-") else parts[0]
+        if uuid is not None:
+            if u != uuid:
+                continue
+        elif index is not None and parts[1] != str(index):
+            continue
+        try:
+            sm.append(float(parts[2]))
+            smax = float(parts[3])
+        except ValueError:
+            continue
+        for n, v in zip(names, parts[6:10]):
+            if v.lower() == "active":
+                reasons.add(n)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm),
+            "matched_by": "uuid" if uuid is not None else "index"}
+
+
+def _clock_summary(proc, f, uuid, index):
     if proc is None:
         f.close()
         os.unlink(f.name)
@@ -109,42 +153,282 @@ def _clock_summary(proc, f, gpu_index):
         proc.kill()
     f.flush()
     f.seek(0)
-    sm, smax, reasons = [], None, set()
-    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-    for line in f.read().splitlines():
-        parts = [x.strip() for x in line.split(",")]
-        if len(parts) < 9 or parts[0] != str(gpu_index):
-            continue
-        try:
-            sm.append(float(parts[1]))
-            smax = float(parts[2])
-        except ValueError:
-            continue
-        for n, v in zip(names, parts[5:9]):
-            if v.lower() == "active":
-                reasons.add(n)
+    lines = f.read().splitlines()
     os.unlink(f.name)
-    if not sm:
+    return parse_clock_samples(lines, uuid=uuid, index=None if uuid else index)
+
+
+# DRAM bytes per launch from ncu captures (dram__bytes_read.sum +
+# dram__bytes_write.sum, one capture each, summarised in profiles/), valid
+# while the sources that define the sweep launch (kernel, arguments, grid,
+# workspace layout) are the captured ones.
+SWEEP_SOURCES = ("sweep.cu", "gsis_internal.cuh", "host.h", "api.cu", "timedep.cu", "batch.cu")
+SWEEP_TRAFFIC = {}   # {workload: (sources digest, bytes per launch)}
+
+
+def sweep_sources_digest() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2507_03975_gb300", "csrc")
+    for name in SWEEP_SOURCES:
+        with open(os.path.join(d, name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+def _sweep_traffic(workload):
+    """ncu DRAM bytes of one sweep launch of `workload`, or None once the
+    sweep-launch sources differ from the captured ones."""
+    ent = SWEEP_TRAFFIC.get(workload)
+    if ent is None or ent[0] != sweep_sources_digest():
         return None
-    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
-            "samples": len(sm)}
+    return ent[1]
 
 
-def _sweep_traffic(workload="channel"):
-    """DRAM bytes of one sweep launch from one ncu capture of each workload
-    (dram__bytes_read.sum + dram__bytes_write.sum; the committed ncu summaries
-    of the sweep kernel): the 256x256 S12 channel solve 94,940,416 +
-    14,861,056, the 64-problem batch 522,939,136 + 453,725,184.  None once
-    the sweep source differs from the one that was captured."""
-    import hashlib
-    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2507_03975_gb300", "csrc", "sweep.cu")
-    with open(src, "rb") as f:
-        digest = hashlib.sha256(f.read()).hexdigest()
-    if not digest.startswith(SWEEP_CAPTURE_SHA256):
-        return None
-    return {"channel": 109_801_472, "batch": 976_664_320}[workload]
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
 
 
+def _events(torch, n=2):
+    return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+
+
+def _rel(a, b):
+    a = a.double().cpu().numpy() if hasattr(a, "cpu") else np.asarray(a)
+    b = b.double().cpu().numpy() if hasattr(b, "cpu") else np.asarray(b)
+    s = np.abs(b).max()
+    return float(np.abs(a - b).max() / (s if s > 0 else 1.0))
+
+
+# ------------------------------------------------ headline: time-dependent
+class TdWorkload:
+    """Inputs of the time-dependent workload on the device (and pinned on the
+    host for the end-to-end pass)."""
+
+    def __init__(self, torch, dev):
+        self.p = p = W.config_timedep()
+        self.tp = tp = W.TIMEDEP
+        self.host = [np.ascontiguousarray(a, dtype=np.float64) for a in
+                     (p.sigma_a, p.sigma_s, p.q, p.inflow.reshape(-1), np.full(p.N, tp["T0"]),
+                      np.full(p.N, tp["a"] * tp["c"] * tp["T0"] ** 4))]
+        t = lambda a: torch.from_numpy(a).to(dev)
+        self.sa, self.ss, self.q, self.inflow, self.T0, self.rho0 = (t(a) for a in self.host)
+        self.upd = p.N * p.K
+
+    def run(self, gsis, opt, nsteps=None, workspace=None, stream=None, inputs=None):
+        p, tp = self.p, self.tp
+        sa, ss, q, inflow, T0, rho0 = inputs or (self.sa, self.ss, self.q, self.inflow, self.T0, self.rho0)
+        return gsis.td_solve(p.dx, p.dy, p.mu, p.eta, p.w, sa, ss, q, rho0, T0, tp["dt"],
+                             nsteps or tp["nsteps"], c=tp["c"], a=tp["a"], cv=tp["cv"], inflow=inflow,
+                             options=opt, workspace=workspace, stream=stream)
+
+
+def td_options(gsis, scheme=None, precision=None, tol=TOL, **kw):
+    base = dict(scheme=gsis.SCHEME_GSIS if scheme is None else scheme,
+                precision=gsis.FP64 if precision is None else precision, tol=tol, max_iter=2000,
+                check_every=TD_CHECK_EVERY, synth_rtol=1e-12, synth_max_iter=TD_SYNTH_CAP)
+    base.update(kw)
+    return gsis.default_options(**base)
+
+
+def _td_config(p, tp):
+    return dict(workload="channel_td_1024x1024_S16", nx=p.nx, ny=p.ny, K=p.K, nsteps=tp["nsteps"], dt=tp["dt"],
+                scheme="gsis", precision="fp64", tol=TOL, tol_applies_to="Err(rho) of every time step",
+                synthetic=f"rho-T system with T eliminated (Newton about T^m); FP64 iterative refinement, FP32 "
+                          f"multigrid-CG inner iterations capped at {TD_SYNTH_CAP} per GSIS iteration",
+                l2="inputs larger than L2 (two FP64 K x N intensity arrays of 1.2 GB per time step); L2 also "
+                   "flushed (512 MiB write) before every run",
+                step="one complete 100-time-step gsis_td_solve call from the cold start",
+                kernel_timing="a separate instrumented run with CUDA events around every kernel class on the "
+                              "launching stream (roofline, shares); value and ms_per_step from uninstrumented runs")
+
+
+def td_class_model(cls, prof, iters, upd, N, fp64_peak, hbm, fp64=True):
+    """Roofline entry of one kernel class of the time-dependent run, per
+    working launch (one launch group per inner iteration; launches after a
+    step converged inside a check_every batch return at once, their few
+    microseconds stay in the total, so this slightly overstates the time).
+    Algorithmic work (what the method must do, not what this implementation
+    adds):
+      sweep:   2 FMA + 1 MUL per update (5 FLOP; FP64 binds: 5 FLOP at
+               1.25 TFLOP/s take 3x longer than its HBM bytes at peak);
+               bytes: read I^n once per update (8 B FP64, 4 B FP32) plus
+               64 B per cell (sigma_t, source in, six moments out);
+      moments: 3 FMA per update (rho, F_x, F_y);
+      synth:   36 B per cell from HBM per call (level coefficients, r0,
+               guess, x) -- bound by barriers and latency;
+      hot_rhs / update: 15 / 10 doubles per cell."""
+    g = max(int(iters), 1)
+    avg_ms = prof[cls]["total_ms"] / g
+    ib = 8.0 if fp64 else 4.0
+    hbm_bytes = None
+    if cls == "sweep":
+        work, bound, peak, unit = 5.0 * upd, ("alu" if fp64 else "hbm"), (fp64_peak if fp64 else hbm), \
+            ("GFLOP/s" if fp64 else "GB/s")
+        hbm_bytes = ib * upd + 64.0 * N
+        if not fp64:
+            work = hbm_bytes
+    elif cls == "moments":
+        work, bound, peak, unit = 6.0 * upd, ("alu" if fp64 else "hbm"), (fp64_peak if fp64 else hbm), \
+            ("GFLOP/s" if fp64 else "GB/s")
+        if not fp64:
+            work = ib * upd + 48.0 * N
+    elif cls == "synth":
+        work, bound, peak, unit = 36.0 * N, "latency", hbm, "GB/s"
+    elif cls == "hot_rhs":
+        work, bound, peak, unit = 15 * 8.0 * N, "hbm", hbm, "GB/s"
+    else:
+        work, bound, peak, unit = 10 * 8.0 * N, "hbm", hbm, "GB/s"
+    ach = work / (avg_ms * 1e-3) / 1e9
+    out = {"bound": bound, "kernel": cls, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+           "avg_launch_ms": avg_ms, "launch_groups": g, "launches_timed": prof[cls]["timed"],
+           "algorithmic_work_per_launch": work}
+    if hbm_bytes is not None:
+        gbs = hbm_bytes / (avg_ms * 1e-3) / 1e9
+        out["hbm_view"] = {"algorithmic_bytes": hbm_bytes, "achieved_gbs": gbs, "peak_gbs": hbm,
+                           "frac": gbs / hbm}
+    return out
+
+
+def td_fp32_measure(gsis, torch, stream, wl, ref64, ws=None):
+    """The same 100 steps with FP32 sweeps (FP64 moments accumulate FP32
+    intensities; synthetic solve, material update and Err in FP64), each step
+    to Err < 1e-8 or to its floor (no new minimum of Err for 10 iterations),
+    and the error of the result against the FP64 run."""
+    ce, sw = FP32_STALL
+    opt = td_options(gsis, precision=gsis.FP32_SWEEP, check_every=ce, stall_window=sw)
+    wl.run(gsis, opt, workspace=ws, stream=stream)   # warm-up (workspace)
+    e0, e1 = _events(torch)
+    e0.record(stream)
+    r = wl.run(gsis, opt, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    s = e0.elapsed_time(e1) * 1e-3
+    its, err = r["step_iters"], r["step_err"]
+    return {"precision": "fp32 sweeps (fp32 intensities), fp64 moments / synthetic / material / Err",
+            "tol": TOL, "stall": f"a step ends after {ce * sw} iterations without a new minimum of Err",
+            "s": s, "status": r["status"], "iters_total": int(its.sum()),
+            "iters_per_step_mean": float(its.mean()), "updates_per_s": float(its.sum()) * wl.upd / s,
+            "steps_reaching_tol": int((err < TOL).sum()), "steps_at_floor": int((err >= TOL).sum()),
+            "step_err_median": float(np.median(err)), "step_err_max": float(err.max()),
+            "rel_err_vs_fp64": {"rho": _rel(r["rho"], ref64["rho"]), "T": _rel(r["T"], ref64["T"])}}
+
+
+def td_adjoint_measure(gsis, torch, stream, wl, nsteps=None):
+    """Gradient of J = sum of rho^N over the channel cells of the first 64
+    columns (a detector next to the source wall) after the full run, with
+    respect to sigma_a, sigma_s, rho^0 and T^0, by gsis_td_adjoint: FP64,
+    forward steps and adjoint iterations to Err < 1e-8, checkpoints every
+    ceil(sqrt(steps)) steps.  Device time with CUDA events around the forward
+    run alone and around the whole adjoint call (forward run with
+    checkpoints, one recomputation, the step adjoints), inputs resident; a
+    second, instrumented call gives the kernel classes."""
+    p, tp = wl.p, wl.tp
+    n = nsteps or tp["nsteps"]
+    cols = np.arange(p.N) % p.nx
+    g = torch.from_numpy((((p.sigma_a + p.sigma_s) < 1.0) & (cols < 64)).astype(np.float64)).to(wl.sa.device)
+    opt = td_options(gsis)
+    e0, e1 = _events(torch)
+
+    def timed(fn):
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return r, e0.elapsed_time(e1) * 1e-3
+
+    f, s_fwd = timed(lambda: wl.run(gsis, opt, nsteps=n, stream=stream))
+    adj = lambda ws=None: gsis.td_adjoint(p.dx, p.dy, p.mu, p.eta, p.w, wl.sa, wl.ss, wl.q, wl.rho0, wl.T0,
+                                          tp["dt"], n, dJ_drho=g, c=tp["c"], a=tp["a"], cv=tp["cv"],
+                                          inflow=wl.inflow, options=opt, workspace=ws, stream=stream)
+    r, s_adj = timed(adj)
+    gsis.profile_enable(True)
+    r2, _ = timed(lambda: adj(r["workspace"]))
+    prof = gsis.profile_read()
+    gsis.profile_enable(False)
+    out = {"workload": f"channel_td_1024x1024_S16, {n} steps of dt = 1e-3, J = sum of rho^N over the channel "
+                       "cells of the first 64 columns",
+           "nsteps": n, "precision": "fp64", "tol": TOL, "checkpoint_every": r["checkpoint_every"],
+           "status": r["status"], "forward_s": s_fwd, "forward_iters": int(f["step_iters"].sum()),
+           "adjoint_call_s": s_adj, "adjoint_over_forward": s_adj / s_fwd,
+           "adj_iters_per_step_mean": float(np.mean(r["adj_iters"])),
+           "workspace_gb": r["workspace"].numel() / 1e9,
+           "kernel_ms": {k: v["total_ms"] for k, v in prof.items()},
+           "repeat_bit_equal": bool(torch.equal(r["grad_sigma_a"], r2["grad_sigma_a"])),
+           "grad_sigma_a_max": float(r["grad_sigma_a"].abs().max())}
+    del r, r2
+    return out
+
+
+# ----------------------------------------- the steady 256^2 channel (extra)
+def channel_measure(gsis, torch, stream, flush, fp64_peak, steps=5, warmup=2, no_si=False, no_uw2=False):
+    """The steady multiscale workload: 256 x 256 cells, S12 (84 directions),
+    channel sigma_t 0.2 (8 cells wide) in a medium of sigma_t 2000, ratio
+    0.999, unit isotropic intensity through the left wall.  GSIS (FP64,
+    local pseudo-time beta = 10, synthetic solve capped at SYNTH_CAP inner
+    iterations) to Err < 1e-8 against SI to Err < 1e-8, the difference of the
+    two converged results, the sweep's ALU roofline, and the second-order
+    upwind form.  L2 flushed before every solve; device time with CUDA
+    events, inputs resident."""
+    p = W.config_channel()
+    dev = flush.device
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
+    sa, ss, q, inflow = t(p.sigma_a), t(p.sigma_s), t(p.q), t(p.inflow.reshape(-1))
+    opt = gsis.default_options(scheme=gsis.SCHEME_GSIS, precision=gsis.FP64, tol=TOL, beta=BETA, max_iter=5000,
+                               check_every=16, synth_max_iter=SYNTH_CAP)
+    ws = torch.empty(gsis.workspace_bytes(p.dx, p.dy, p.mu, p.eta, p.w, opt), dtype=torch.uint8, device=dev)
+    solve = lambda o=opt, w=ws: gsis.solve(p.dx, p.dy, p.mu, p.eta, p.w, sa, ss, q, inflow, o, workspace=w,
+                                           want_P=False)
+    for _ in range(warmup):
+        solve()
+    ms, r = [], None
+    for _ in range(steps):
+        flush.fill_(1.0)
+        e0, e1 = _events(torch)
+        e0.record(stream)
+        r = solve()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    gsis.profile_enable(True)
+    flush.fill_(1.0)
+    ri = solve()
+    prof = gsis.profile_read()
+    gsis.profile_enable(False)
+    upd = p.N * p.K
+    sweep_ms = prof["sweep"]["total_ms"] / max(1, ri["iters"])
+    ach = 5.0 * upd / (sweep_ms * 1e-3) / 1e9
+    out = {"workload": "channel_256x256_S12_seed2 (steady), GSIS FP64, beta = 10, Err < 1e-8",
+           "gsis": {"s": statistics.median(ms) * 1e-3, "iters": r["iters"], "status": r["status"],
+                    "synth_inner_iters": r["synth_inner_iters"],
+                    "updates_per_s": r["iters"] * upd / (statistics.median(ms) * 1e-3)},
+           "sweep_roofline": {"bound": "alu", "kernel": "sweep (fp64, pseudo-time, per-ordinate source)",
+                              "achieved": ach, "peak": fp64_peak, "unit": "GFLOP/s", "frac": ach / fp64_peak,
+                              "avg_launch_ms": sweep_ms, "traffic": _sweep_traffic("channel")},
+           "kernel_ms_per_iter": {k: v["total_ms"] / max(1, ri["iters"]) for k, v in prof.items() if k != "setup"}}
+    if not no_si:
+        opt_si = gsis.default_options(scheme=gsis.SCHEME_SI, precision=gsis.FP64, tol=TOL, max_iter=100000,
+                                      check_every=256)
+        flush.fill_(3.0)
+        e0, e1 = _events(torch)
+        e0.record(stream)
+        rs = gsis.solve(p.dx, p.dy, p.mu, p.eta, p.w, sa, ss, q, inflow, opt_si, want_P=False)
+        e1.record(stream)
+        e1.synchronize()
+        s = e0.elapsed_time(e1) * 1e-3
+        out["si"] = {"s": s, "iters": rs["iters"], "status": rs["status"], "updates_per_s": rs["iters"] * upd / s}
+        out["gsis_over_si_time"] = out["gsis"]["s"] / s
+        # the two schemes converge to different discrete solutions (GSIS
+        # corrects UW1 towards the diffusion limit)
+        out["rel_diff_rho_gsis_vs_si"] = _rel(r["rho"], rs["rho"])
+    if not no_uw2:
+        out["uw2"] = uw2_measure(gsis, torch, stream, p, sa, ss, q, inflow, flush)
+    return out
+
+
+# ------------------------------------------------ the other workloads
 def small_measure(gsis, torch, stream):
     """Time to Err < 1e-8 of FP64 GSIS and SI on the 64x64 S8 uniform problem
     (sigma_t = 10, ratio 0.99, q = 1, vacuum): the latency-bound size, where
@@ -255,127 +539,6 @@ def batch_measure(gsis, torch, stream, hbm, steps=3):
                                "algorithmic_bytes": algo}}
 
 
-def timedep_measure(gsis, torch, stream, hbm):
-    """The time-dependent radiation-material workload: 1024x1024 cells, S16
-    (144 directions), the channel geometry scaled x4 (32-cell channel,
-    sigma_t 2000 / 0.2, ratio 0.999, unit intensity through the left wall),
-    emission sigma_a a c T^4 with a = c = C_v = 1, cold start T = 0.1,
-    100 backward-Euler steps of dt = 1e-3.  GSIS (Newton-eliminated rho-T
-    synthetic system, capped at TD_SYNTH_CAP inner iterations) and SI with the
-    Fleck-Cummings linearisation, FP32 sweeps (Err < 1e-6 per step: the FP32
-    floor) and GSIS with FP64 sweeps (Err < 1e-8).  Device time with CUDA
-    events around each whole solve, inputs resident."""
-    p = W.config_timedep()
-    tpd = W.TIMEDEP
-    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
-    sa, ss, q, inflow = t(p.sigma_a), t(p.sigma_s), t(p.q), t(p.inflow.reshape(-1))
-    T0 = t(np.full(p.N, tpd["T0"]))
-    rho0 = t(np.full(p.N, tpd["a"] * tpd["c"] * tpd["T0"] ** 4))
-    upd = p.N * p.K
-    out = {"workload": "channel_td_1024x1024_S16 (channel x4, 32 cells wide), 100 steps of dt = 1e-3",
-           "updates_per_sweep": upd}
-    ws = None
-
-    def run(name, scheme, prec, tol, profile=False):
-        nonlocal ws
-        opt = gsis.default_options(scheme=scheme, precision=prec, tol=tol, max_iter=2000, check_every=4,
-                                   synth_rtol=1e-12, synth_max_iter=TD_SYNTH_CAP)
-        gsis.profile_enable(profile)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        r = gsis.td_solve(p.dx, p.dy, p.mu, p.eta, p.w, sa, ss, q, rho0, T0, tpd["dt"], tpd["nsteps"],
-                          c=tpd["c"], a=tpd["a"], cv=tpd["cv"], inflow=inflow, options=opt, workspace=ws)
-        e1.record(stream)
-        e1.synchronize()
-        ws = r["workspace"]
-        s = e0.elapsed_time(e1) * 1e-3
-        its = r["step_iters"]
-        res = {"s": s, "status": r["status"], "tol": tol, "iters_total": int(its.sum()),
-               "iters_per_step_mean": float(its.mean()), "iters_per_step_max": int(its.max()),
-               "updates_per_s": float(its.sum()) * upd / s,
-               "T_max": float(r["T"].max()), "rho_max": float(r["rho"].max())}
-        if profile:
-            prof = gsis.profile_read()
-            res["kernel_ms"] = {k: v["total_ms"] for k, v in prof.items()}
-            sw = prof["sweep"]
-            # per working launch: one sweep per inner iteration (the launches
-            # after a step converged, up to check_every - 1, return at once)
-            res["sweep_ms_avg"] = sw["total_ms"] / max(1, int(its.sum()))
-        gsis.profile_enable(False)
-        out[name] = res
-        return res
-
-    run("gsis_fp32", gsis.SCHEME_GSIS, gsis.FP32_SWEEP, 1e-6)
-    prof = run("gsis_fp32_instrumented", gsis.SCHEME_GSIS, gsis.FP32_SWEEP, 1e-6, profile=True)
-    run("si_fp32", gsis.SCHEME_SI, gsis.FP32_SWEEP, 1e-6)
-    ws = None   # the FP64 layout is larger
-    run("gsis_fp64", gsis.SCHEME_GSIS, gsis.FP64, 1e-8)
-    # roofline of the time-step sweep (FP32): read its per-ordinate source
-    # X = src + I^n/(c dt) and write I (4 + 4 B per update) plus its diagonal
-    # sigma_t + 1/(c dt) (FP32) once per cell
-    algo = 8.0 * upd + 4.0 * p.N
-    ach = algo / (prof["sweep_ms_avg"] * 1e-3) / 1e9
-    out["sweep_roofline"] = {"bound": "hbm", "kernel": "sweep (fp32, time step)", "achieved": ach, "peak": hbm,
-                             "unit": "GB/s", "frac": ach / hbm, "traffic": None, "algorithmic_bytes": algo,
-                             "avg_launch_ms": prof["sweep_ms_avg"]}
-    return out
-
-
-TD_ADJ_STEPS = 10
-
-
-def td_adjoint_measure(gsis, torch, stream):
-    """Gradient of J = sum of rho^N over the channel cells next to the left
-    wall after TD_ADJ_STEPS steps of the time-dependent workload (1024^2 S16,
-    dt = 1e-3, cold start), with respect to sigma_a, sigma_s, rho^0 and T^0:
-    FP32 sweeps, forward steps and adjoint iterations to Err < 1e-6,
-    checkpoints every ceil(sqrt(steps)) steps.  Device time with CUDA events
-    around the forward run alone and around the whole adjoint call (forward
-    run with checkpoints, one recomputation, the step adjoints), inputs
-    resident; a second instrumented call gives the kernel classes."""
-    p = W.config_timedep()
-    tpd = W.TIMEDEP
-    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
-    sa, ss, q, inflow = t(p.sigma_a), t(p.sigma_s), t(p.q), t(p.inflow.reshape(-1))
-    T0 = t(np.full(p.N, tpd["T0"]))
-    rho0 = t(np.full(p.N, tpd["a"] * tpd["c"] * tpd["T0"] ** 4))
-    cols = np.arange(p.N) % p.nx
-    g = t((((p.sigma_a + p.sigma_s) < 1.0) & (cols < 64)).astype(np.float64))
-    n = TD_ADJ_STEPS
-    opt = gsis.default_options(scheme=gsis.SCHEME_GSIS, precision=gsis.FP32_SWEEP, tol=1e-6, max_iter=2000,
-                               check_every=4, synth_rtol=1e-12, synth_max_iter=TD_SYNTH_CAP)
-    kw = dict(c=tpd["c"], a=tpd["a"], cv=tpd["cv"], inflow=inflow, options=opt)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-
-    def timed(fn):
-        e0.record(stream)
-        r = fn()
-        e1.record(stream)
-        e1.synchronize()
-        return r, e0.elapsed_time(e1) * 1e-3
-
-    f, s_fwd = timed(lambda: gsis.td_solve(p.dx, p.dy, p.mu, p.eta, p.w, sa, ss, q, rho0, T0, tpd["dt"], n, **kw))
-    adj = lambda ws=None: gsis.td_adjoint(p.dx, p.dy, p.mu, p.eta, p.w, sa, ss, q, rho0, T0, tpd["dt"], n,
-                                          dJ_drho=g, workspace=ws, **kw)
-    r, s_adj = timed(adj)
-    gsis.profile_enable(True)
-    r2, _ = timed(lambda: adj(r["workspace"]))
-    prof = gsis.profile_read()
-    gsis.profile_enable(False)
-    same = bool(torch.equal(r["grad_sigma_a"], r2["grad_sigma_a"]))
-    return {"workload": f"channel_td_1024x1024_S16, {n} steps of dt = 1e-3, J = sum of rho^N over the channel "
-                        "cells of the first 64 columns",
-            "precision": "fp32 sweeps, fp64 synthetic solve / material / gradient terms", "tol": 1e-6,
-            "checkpoint_every": r["checkpoint_every"], "status": r["status"],
-            "forward_s": s_fwd, "forward_iters": int(f["step_iters"].sum()),
-            "adjoint_call_s": s_adj, "adjoint_over_forward": s_adj / s_fwd,
-            "adj_iters_per_step_mean": float(np.mean(r["adj_iters"])),
-            "workspace_gb": r["workspace"].numel() / 1e9,
-            "kernel_ms": {k: v["total_ms"] for k, v in prof.items()},
-            "repeat_bit_equal": same,
-            "grad_sigma_a_max": float(r["grad_sigma_a"].abs().max())}
-
-
 def uw2_measure(gsis, torch, stream, p, sa, ss, q, inflow, flush):
     """The channel workload with second-order upwind face values (the paper's
     transport scheme): GSIS, FP64, beta = 10, Err < 1e-8, synthetic solve
@@ -412,61 +575,94 @@ def uw2_measure(gsis, torch, stream, p, sa, ss, q, inflow, flush):
     return out
 
 
-def _peaks():
-    try:
-        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        return {}
+# ------------------------------------------------------- the oracle on CPU
+def _td_oracle_inputs():
+    from oracle import timedep as TD
+    p = W.config_timedep()
+    td = W.TIMEDEP
+    tp = TD.TimeParams(dt=td["dt"], c=td["c"], a=td["a"], cv=td["cv"])
+    T0 = np.full(p.N, td["T0"])
+    rho0 = td["a"] * td["c"] * T0 ** 4
+    return TD, p, tp, rho0, T0
 
 
-def cpu_baseline_sample(p, iters=2, threads=False):
-    """The FP64 oracle as it stands on a bounded sample: `iters` GSIS
-    iterations of the same workload (the first includes the oracle's one-off
-    sparse LU of the synthetic operator).  threads: the -fopenmp build of its
-    C sweeps (ordinates on all host cores, same results) instead of one
-    thread.  Returns (updates/s, seconds, threads used)."""
-    import oracle
+def cpu_baseline_sample(threads=False):
+    """The FP64 oracle as it stands on a bounded sample of the headline
+    workload: one GSIS iteration of its first time step from the cold start
+    (the kinetic step over all 144 ordinates and 1,048,576 cells, the
+    adaptive gradients, the synthetic operator and its sparse LU solve, the
+    material update).  threads: the -fopenmp build of the oracle's C sweeps
+    (ordinates on all host cores, the same results) instead of one thread.
+    Returns (updates/s, seconds, threads used)."""
     from oracle import gsis as G
+    TD, p, tp, rho0, T0 = _td_oracle_inputs()
+    I0 = TD.isotropic(p, rho0)
     G.use_threads(threads)
     try:
         cores = G.threads()
         t0 = time.perf_counter()
-        oracle.gsis_solve(p, fixed_iters=iters, beta=BETA)
+        TD.gsis_time_step(p, tp, rho0, T0, I0, fixed_iters=1)
         dt = time.perf_counter() - t0
     finally:
         G.use_threads(False)
-    return iters * p.N * p.K / dt, dt, cores
+    return p.N * p.K / dt, dt, cores
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores, on the headline
+    workload.  One of its GSIS iterations takes ~20 s (its sparse LU of the
+    1,048,576-cell synthetic system alone ~15 s), so each step is a bounded
+    sample: the oracle's kinetic step of the first time step (the UW1 sweep
+    of all 144 ordinates with the shift 1/(c dt) and I^n, moments and
+    boundary fluxes; C sweeps on every host core).  The synthetic solve is
+    outside the sample, so this rate bounds the oracle's whole-iteration rate
+    from above; one whole iteration is timed once after the steps and
+    reported beside it."""
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
-    p, cfg = _workload()
-    import oracle  # noqa: F401  (builds the C sweep on first use)
-    # the oracle's C sweeps on every host core (-fopenmp build, same results)
-    for _ in range(args.warmup):
-        cpu_baseline_sample(p, 1, threads=True)
-    vals, secs = [], []
-    cores = 1
-    for _ in range(args.steps):
-        v, dt, cores = cpu_baseline_sample(p, 1, threads=True)
-        vals.append(v)
-        secs.append(dt)
+    from oracle import gsis as G
+    TD, p, tp, rho0, T0 = _td_oracle_inputs()
+    cfg = _td_config(p, W.TIMEDEP)
+    I0 = TD.isotropic(p, rho0)
+    src = p.sigma_a * TD.emission(T0, tp) + p.q
+    G.use_threads(True)
+    try:
+        cores = G.threads()
+        for _ in range(args.warmup):
+            TD.kinetic_step(p, tp, rho0, src, I0)
+        secs = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            TD.kinetic_step(p, tp, rho0, src, I0)
+            secs.append(time.perf_counter() - t0)
+        full = None
+        if not args.no_cpu_baseline:
+            t0 = time.perf_counter()
+            TD.gsis_time_step(p, tp, rho0, T0, I0, fixed_iters=1)
+            dt = time.perf_counter() - t0
+            full = {"value": p.N * p.K / dt, "unit": UNIT, "s": dt, "cores": cores,
+                    "sample": "one whole oracle GSIS iteration of the first time step (kinetic step, gradients, "
+                              "synthetic operator and its sparse LU solve, material update)"}
+    finally:
+        G.use_threads(False)
     value = args.steps * p.N * p.K / sum(secs)
+    sample = ("one oracle kinetic step of the first time step per bench step: UW1 sweep of all 144 ordinates over "
+              "the 1,048,576 cells (diagonal shift 1/(c dt), I^n on the right), moments and boundary fluxes, C "
+              "sweeps on every host core; the oracle's synthetic solve is outside the sample (an upper bound of "
+              "its whole-iteration rate)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": cfg,
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "one oracle GSIS iteration of the 256x256 S12 channel workload per step "
-                                       "(sparse LU of the synthetic operator included; C sweeps over the "
-                                       "ordinates on every host core)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "oracle_full_iteration": full,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
+# ------------------------------------------------------------ our arm
 def run_ours(args):
     import torch
 
@@ -481,151 +677,122 @@ def run_ours(args):
         dist = None
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
-    if args.batch_only:   # the batched-solve measurement alone (profiling runs)
-        print(json.dumps({"batch": batch_measure(gsis, torch, torch.cuda.current_stream(),
-                                                 _peaks().get("hbm_gbs", 6800.0))}))
-        return 0
-    if args.timedep_only:   # the time-dependent measurement alone (profiling runs)
-        print(json.dumps({"timedep": timedep_measure(gsis, torch, torch.cuda.current_stream(),
-                                                     _peaks().get("hbm_gbs", 6800.0))}))
-        return 0
-    if args.td_adjoint_only:   # the time-dependent adjoint measurement alone
-        print(json.dumps({"td_adjoint": td_adjoint_measure(gsis, torch, torch.cuda.current_stream())}))
-        return 0
-    p, cfg = _workload(args)
-    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
-    sa, ss, q, inflow = t(p.sigma_a), t(p.sigma_s), t(p.q), t(p.inflow.reshape(-1))
-    cap = args.synth_cap
-    opt = gsis.default_options(scheme=gsis.SCHEME_GSIS, precision=gsis.FP64, tol=TOL, beta=BETA,
-                               max_iter=5000, check_every=16,
-                               synth_max_iter=cap if cap > 0 else 20000)
     stream = torch.cuda.current_stream()
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    if args.batch_only:   # the batched-solve measurement alone (profiling runs)
+        print(json.dumps({"batch": batch_measure(gsis, torch, stream, hbm)}))
+        return 0
+    if args.channel_only:   # the steady channel measurement alone (profiling runs)
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device=dev)
+        print(json.dumps({"channel_256": channel_measure(gsis, torch, stream, flush, gsis.measure_fp64_fma(),
+                                                         no_si=True, no_uw2=True)}))
+        return 0
+
+    wl = TdWorkload(torch, dev)
+    p, tpd = wl.p, wl.tp
+    cfg = _td_config(p, tpd)
+    opt = td_options(gsis)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device=dev)   # 512 MiB > L2
-    nbytes = gsis.workspace_bytes(p.dx, p.dy, p.mu, p.eta, p.w, opt)
-    workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    workspace = torch.empty(gsis.td_workspace_bytes(p.dx, p.dy, p.mu, p.eta, p.w, opt), dtype=torch.uint8,
+                            device=dev)
+    gsis.profile_enable(False)
     for _ in range(args.warmup):
-        gsis.solve(p.dx, p.dy, p.mu, p.eta, p.w, sa, ss, q, inflow, opt, workspace=workspace)
+        wl.run(gsis, opt, workspace=workspace, stream=stream)
     torch.cuda.synchronize()
 
-    # ---- timed: K complete solves, inputs resident in HBM (no instrumentation)
-    gsis.profile_enable(False)
+    # ---- timed: K complete runs, inputs resident in HBM (no instrumentation)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     proc, cf = _clock_sampler() if rank == 0 else (None, None)
-    step_ms, iters, inner = [], [], []
+    step_ms, iters, res = [], [], None
     for _ in range(args.steps):
         flush.fill_(1.0)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
+        e0, e1 = _events(torch)
         e0.record(stream)
-        r = gsis.solve(p.dx, p.dy, p.mu, p.eta, p.w, sa, ss, q, inflow, opt, workspace=workspace)
+        res = wl.run(gsis, opt, workspace=workspace, stream=stream)
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
-        iters.append(r["iters"])
-        inner.append(r["synth_inner_iters"])
-        if r["status"] != gsis.GSIS_OK:
-            raise RuntimeError(f"solve did not converge: status {r['status']}, Err {r['err']}")
+        iters.append(int(res["step_iters"].sum()))
+        if res["status"] != gsis.GSIS_OK:
+            raise RuntimeError(f"time-dependent run did not converge: status {res['status']}")
     torch.cuda.synchronize()
-    clocks = _clock_summary(proc, cf, torch.cuda.current_device()) if rank == 0 else None
+    clocks = _clock_summary(proc, cf, device_uuid(torch, dev), torch.cuda.current_device()) if rank == 0 else None
     if dist:
         dist.barrier()
-    # ---- the same K solves again with CUDA events around every kernel class on
-    # the launching stream: per-launch durations and shares for the roofline
-    gsis.profile_enable(True)
-    prof_iters = 0
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        prof_iters += gsis.solve(p.dx, p.dy, p.mu, p.eta, p.w, sa, ss, q, inflow, opt, workspace=workspace)["iters"]
-    torch.cuda.synchronize()
-    prof = gsis.profile_read()
-    gsis.profile_enable(False)
-    units, total_ms = replica_totals(dist, sum(iters) * p.N * p.K, sum(step_ms), dev)
+    units, total_ms = replica_totals(dist, sum(iters) * wl.upd, sum(step_ms), dev)
     if dist:
         dist.barrier()
     value = units / (total_ms * 1e-3)
+    ref64 = {"rho": res["rho"].clone(), "T": res["T"].clone()}
+    step_iters = res["step_iters"]
+
+    # ---- one instrumented run: CUDA events around every kernel class
+    gsis.profile_enable(True)
+    flush.fill_(1.0)
+    ri = wl.run(gsis, opt, workspace=workspace, stream=stream)
+    torch.cuda.synchronize()
+    prof = gsis.profile_read()
+    gsis.profile_enable(False)
+    prof_iters = int(ri["step_iters"].sum())
+    launches_per_run = int(sum(v["kernels"] for v in prof.values()))
 
     # ---- end to end through the C ABI: pinned host inputs in, result out
-    h_in = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).pin_memory()
-            for a in (p.sigma_a, p.sigma_s, p.q, p.inflow.reshape(-1))]
+    h_in = [torch.from_numpy(a).pin_memory() for a in wl.host]
     h_rho = torch.empty(p.N, dtype=torch.float64).pin_memory()
-    h_F = torch.empty(2 * p.N, dtype=torch.float64).pin_memory()
+    h_T = torch.empty(p.N, dtype=torch.float64).pin_memory()
     e2e_ms, e2e_iters = [], []
-    for _ in range(0 if args.no_e2e else max(1, min(args.steps, 3))):
+    for _ in range(0 if args.no_e2e else max(1, min(args.steps, 2))):
         flush.fill_(2.0)
         torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
+        e0, e1 = _events(torch)
         e0.record(stream)
         d_in = [h.to(dev, non_blocking=True) for h in h_in]
-        r = gsis.solve(p.dx, p.dy, p.mu, p.eta, p.w, *d_in, opt, workspace=workspace, want_P=False)
+        r = wl.run(gsis, opt, workspace=workspace, stream=stream, inputs=d_in)
         h_rho.copy_(r["rho"], non_blocking=True)
-        h_F.copy_(r["F"], non_blocking=True)
+        h_T.copy_(r["T"], non_blocking=True)
         e1.record(stream)
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
-        e2e_iters.append(r["iters"])
+        e2e_iters.append(int(r["step_iters"].sum()))
     h2d = sum(h.numel() * 8 for h in h_in)
-    d2h = (h_rho.numel() + h_F.numel()) * 8
+    d2h = (h_rho.numel() + h_T.numel()) * 8
     e2e_value = None
     if e2e_ms:
-        e2e_units, e2e_total = replica_totals(dist, sum(e2e_iters) * p.N * p.K, sum(e2e_ms), dev)
+        e2e_units, e2e_total = replica_totals(dist, sum(e2e_iters) * wl.upd, sum(e2e_ms), dev)
         e2e_value = e2e_units / (e2e_total * 1e-3)
 
-    # ---- time-to-converge of plain source iteration on the same problem (once)
+    # ---- time to converge: Fleck-Cummings source iteration on the same run, once
     si = None
     if not args.no_si:
-        opt_si = gsis.default_options(scheme=gsis.SCHEME_SI, precision=gsis.FP64, tol=TOL, max_iter=100000,
-                                      check_every=256)
-        gsis.profile_enable(False)
+        opt_si = td_options(gsis, scheme=gsis.SCHEME_SI, max_iter=20000, check_every=16)
         flush.fill_(3.0)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
+        e0, e1 = _events(torch)
         e0.record(stream)
-        rs = gsis.solve(p.dx, p.dy, p.mu, p.eta, p.w, sa, ss, q, inflow, opt_si, workspace=None)
+        rs = wl.run(gsis, opt_si, stream=stream)
         e1.record(stream)
         e1.synchronize()
-        si = {"s": e0.elapsed_time(e1) * 1e-3, "iters": rs["iters"], "status": rs["status"],
-              "updates_per_s": rs["iters"] * p.N * p.K / (e0.elapsed_time(e1) * 1e-3)}
+        s = e0.elapsed_time(e1) * 1e-3
+        its = rs["step_iters"]
+        si = {"s": s, "status": rs["status"], "iters_total": int(its.sum()),
+              "iters_per_step_mean": float(its.mean()), "updates_per_s": float(its.sum()) * wl.upd / s,
+              # GSIS and SI converge to different discrete solutions
+              "rel_diff_gsis_vs_si": {"rho": _rel(ref64["rho"], rs["rho"]), "T": _rel(ref64["T"], rs["T"])}}
+        del rs
 
-    # ---- the same workload with second-order upwind face values, once
-    uw2 = None
-    if not args.no_uw2:
-        uw2 = uw2_measure(gsis, torch, stream, p, sa, ss, q, inflow, flush)
+    fp32 = None
+    if not args.no_fp32:
+        fp32 = td_fp32_measure(gsis, torch, stream, wl, ref64)
 
-    # ---- adjoint (gradient of a detector functional, 64x64 S8 workload), once
-    adj = small = None
-    if not args.no_adjoint:
-        adj = adjoint_measure(gsis, torch, stream)
-        small = small_measure(gsis, torch, stream)
-
-    # ---- time-dependent radiation-material workload (1024^2 S16, 100 steps), once
-    timedep = None
-    if not args.no_timedep:
-        timedep = timedep_measure(gsis, torch, stream, _peaks().get("hbm_gbs", 6800.0))
-
-    # ---- adjoint of the time-dependent run (10 steps, checkpointed), once
     td_adj = None
     if not args.no_td_adjoint:
-        td_adj = td_adjoint_measure(gsis, torch, stream)
-
-    # ---- batched solve of 64 independent problems (autotuned), once
-    batch = None
-    if not args.no_batch:
-        batch = batch_measure(gsis, torch, stream, _peaks().get("hbm_gbs", 6800.0))
-
-    if rank != 0:
-        if dist:
-            dist.destroy_process_group()
-        return 0
+        td_adj = td_adjoint_measure(gsis, torch, stream, wl)
+    del workspace
+    torch.cuda.empty_cache()
 
     # ---- roofline of the dominant kernel class (algorithmic work per launch)
-    peaks = _peaks()
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    # GFLOP/s: the FP64 FMA rate measured in this run (independent FMA chains
-    # filling every SM, gsis_measure_fp64_fma); nominal 1250 if it fails
     try:
         FP64_PEAK = gsis.measure_fp64_fma()
         fp64_src = "measured in this run: FP64 FMA kernel (gsis_measure_fp64_fma)"
@@ -638,67 +805,58 @@ def run_ours(args):
         fp32_rate = None
     shares = {k: v["total_ms"] for k, v in prof.items()}
     tot = sum(shares.values()) or 1.0
-    upd = p.N * p.K
-    inner_per_call = sum(inner) / max(1, sum(iters))
-
-    def model(cls):
-        # per working launch: one launch group of the class per iteration (the
-        # launches after convergence, up to check_every - 1 per solve, return at
-        # once; their time stays in the total, so this slightly overstates it)
-        g = max(prof_iters, 1)
-        avg_ms = prof[cls]["total_ms"] / g
-        if cls == "sweep":
-            # 2 FMA + 1 MUL per update: with the FP64 pseudo-time form the
-            # per-ordinate source src + shift I^m is formed after the update
-            # step (its FMA is counted there, not here)
-            work, bound, peak, unit = 5.0 * upd, "alu", FP64_PEAK, "GFLOP/s"
-        elif cls == "moments":   # rho, Fx, Fy: 3 FMA per update
-            work, bound, peak, unit = 6.0 * upd, "alu", FP64_PEAK, "GFLOP/s"
-        elif cls == "synth":     # one cluster, every level in shared memory: barrier/latency bound;
-            # HBM bytes per call = level coefficients (12 B/cell x 4/3) + r0 (4) + guess (8) + x (8)
-            work, bound, peak, unit = 36.0 * p.N, "latency", hbm, "GB/s"
-        elif cls == "hot_rhs":
-            work, bound, peak, unit = 15 * 8.0 * p.N, "hbm", hbm, "GB/s"
-        else:
-            work, bound, peak, unit = 6 * 8.0 * p.N, "hbm", hbm, "GB/s"
-        ach = work / (avg_ms * 1e-3) / 1e9
-        return {"bound": bound, "kernel": cls, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
-                "avg_launch_ms": avg_ms, "launch_groups": g, "launches_timed": prof[cls]["timed"]}
-
-    dom = max(("sweep", "moments", "synth"), key=lambda k: shares[k])
+    model = lambda c: td_class_model(c, prof, prof_iters, wl.upd, p.N, FP64_PEAK, hbm)
+    dom = max(("sweep", "moments", "synth", "update", "hot_rhs"), key=lambda k: shares[k])
     roof = model(dom)
-    roof.update({"traffic": _sweep_traffic() if dom == "sweep" else None,
+    roof.update({"traffic": _sweep_traffic("timedep_fp64") if dom == "sweep" else None,
                  "share": {k: v / tot for k, v in shares.items()},
-                 "peak_source": ("measured hbm_gbs (MEASURED_PEAKS.json)" if roof["bound"] == "hbm"
+                 "peak_source": ("measured hbm_gbs (MEASURED_PEAKS.json)" if roof["bound"] != "alu"
                                  else fp64_src),
                  "fp64_fma_gflops": FP64_PEAK, "fp32_fma_gflops": fp32_rate,
-                 "others": {k: model(k) for k in ("sweep", "moments", "synth") if k != dom}})
+                 "others": {k: model(k) for k in ("sweep", "moments", "synth", "update", "hot_rhs") if k != dom}})
 
-    cpu = cpu_all = None
+    # ---- the other workloads, once each
+    extra = {}
+    if not args.no_channel:
+        extra["channel_256"] = channel_measure(gsis, torch, stream, flush, FP64_PEAK, no_si=args.no_si,
+                                               no_uw2=args.no_uw2)
+    if not args.no_adjoint:
+        extra["adjoint"] = adjoint_measure(gsis, torch, stream)
+        extra["uniform_64x64_S8"] = small_measure(gsis, torch, stream)
+    if not args.no_batch:
+        extra["batch"] = batch_measure(gsis, torch, stream, hbm)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    cpu = None
     if not args.no_cpu_baseline:
-        v, dt, _ = cpu_baseline_sample(p, 2)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"2 oracle GSIS iterations of the same workload ({dt:.1f} s, includes the oracle's "
-                         "one-off sparse LU)"}
-        v, dt, cores = cpu_baseline_sample(p, 2, threads=True)
-        cpu_all = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle (C sweeps on every host core)",
-                   "sample": f"the same 2 iterations ({dt:.1f} s)"}
+        v, dt, cores = cpu_baseline_sample(threads=False)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"one oracle GSIS iteration of the first time step of the same workload ({dt:.1f} s: "
+                         "kinetic step of 144 ordinates x 1,048,576 cells, adaptive gradients, synthetic "
+                         "operator with its sparse LU solve, material update), one thread"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": max(ws, 1), "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
-            "time_to_converge": {"gsis": {"s": total_ms / args.steps * 1e-3, "iters": iters[0],
-                                          "synth_inner_iters": inner[0]}, "si": si},
-            "roofline": roof, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all,
+            "time_to_converge": {"gsis": {"s": total_ms / args.steps * 1e-3, "iters_total": iters[0],
+                                          "iters_per_step_mean": float(np.mean(step_iters)),
+                                          "iters_per_step_max": int(step_iters.max()),
+                                          "step_err_max": float(res["step_err"].max())},
+                                 "si": si,
+                                 "note": "both schemes, 100 backward-Euler steps, Err(rho) < 1e-8 in every step"},
+            "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": int(sum(v["kernels"] for v in prof.values())),
+            "gpu_launches": launches_per_run * args.steps,
+            "gpu_launches_note": "library kernel launches per run (its launch counters) x timed runs",
             "kernel_ms": {k: v["total_ms"] for k, v in prof.items()},
-            "adjoint": adj, "uniform_64x64_S8": small,
-            "batch": batch,
-            "timedep": timedep,
+            "fp32_intensities": fp32,
             "td_adjoint": td_adj,
-            "uw2": uw2,
             "clocks": clocks}
+    line.update(extra)
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
@@ -706,21 +864,16 @@ def run_ours(args):
 
 
 def run_oracle_times(args):
-    """The FP64 oracle's own timings on the host cores, single thread and with
-    its C sweeps on every core: time per sweep (64^2 S8 uniform, 256^2 S12
-    channel); time to Err < 1e-8 by SI and GSIS on the 64^2 problem and by
-    GSIS on the channel (beta = 10, as the GPU solve); channel SI and the
-    1024^2 S16 time-dependent run from bounded samples, extrapolated with
-    the GPU runs' iteration counts (stated as extrapolations).  CPU only;
-    prints one JSON line."""
+    """The FP64 oracle's own timings on the host cores (CPU only; prints one
+    JSON line): time per sweep (64^2 S8 uniform, 256^2 S12 channel); time to
+    Err < 1e-8 by SI and GSIS on the 64^2 problem and by GSIS on the channel
+    (beta = 10); the headline time-dependent workload for real: its first
+    --oracle-td-steps time steps by GSIS to Err < 1e-8 on every core, and one
+    GSIS iteration on one core."""
     import platform
 
-    import numpy as np
-
     import oracle
-    import workloads as W
     from oracle import gsis as G
-    from oracle import timedep as TD
 
     def timed(fn):
         t0 = time.perf_counter()
@@ -744,23 +897,21 @@ def run_oracle_times(args):
             if threads:
                 r, dt = timed(lambda: oracle.gsis_solve(c2, tol=TOL, beta=BETA))
                 arm["channel_256x256_S12_gsis"] = {"s": dt, "iters": int(r["iters"])}
-                n = 20
-                _, dt = timed(lambda: oracle.si_solve(c2, fixed_iters=n))
-                arm["channel_256x256_S12_si_extrapolated"] = {
-                    "s": dt / n * 9081, "sample": f"{n} iterations in {dt:.1f} s, x 9081 (the GPU SI count)"}
-                p5 = W.config_timedep()
-                td = W.TIMEDEP
-                tp = TD.TimeParams(dt=td["dt"], c=td["c"], a=td["a"], cv=td["cv"])
-                T0 = np.full(p5.N, td["T0"])
-                rho0 = td["a"] * td["c"] * T0 ** 4
-                _, dt = timed(lambda: TD.gsis_time_step(p5, tp, rho0, T0, TD.isotropic(p5, rho0), fixed_iters=1))
-                per_step = 8.64   # GSIS iterations per step of the GPU FP64 run (100 steps, Err < 1e-8)
-                arm["channel_td_1024x1024_S16_gsis_extrapolated"] = {
-                    "s_2_steps": 2 * per_step * dt, "s_100_steps": 100 * per_step * dt,
-                    "sample": f"one GSIS iteration of the first step in {dt:.1f} s (sweep, gradient, sparse "
-                              f"direct solve of the 1,048,576-cell synthetic system), x {per_step} iterations "
-                              "per step (the GPU FP64 run's mean)"}
             out["arms"]["all_cores" if threads else "one_core"] = arm
+        finally:
+            G.use_threads(False)
+    if args.oracle_td_steps > 0:
+        TD, p5, tp, rho0, T0 = _td_oracle_inputs()
+        v, dt, cores = cpu_baseline_sample(threads=False)
+        out["arms"]["one_core"]["channel_td_1024x1024_S16_one_gsis_iteration"] = {"s": dt, "updates_per_s": v}
+        G.use_threads(True)
+        try:
+            n = args.oracle_td_steps
+            r, dt = timed(lambda: TD.run(p5, tp, n, rho0, T0, scheme="gsis", tol=TOL))
+            out["arms"]["all_cores"][f"channel_td_1024x1024_S16_gsis_{n}_steps"] = {
+                "s": dt, "iters": r["iters"].tolist(), "updates_per_s": float(r["iters"].sum()) * p5.N * p5.K / dt,
+                "note": f"the first {n} of the 100 time steps, every step to Err < 1e-8 (sparse LU of the "
+                        "synthetic system in every iteration)"}
         finally:
             G.use_threads(False)
     print(json.dumps(out))
@@ -776,18 +927,18 @@ def main():
     ap.add_argument("--no-si", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-gradient measurement")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-intensity form of the headline")
+    ap.add_argument("--no-channel", action="store_true", help="skip the steady 256^2 channel measurement")
+    ap.add_argument("--channel-only", action="store_true", help="run only the steady channel GSIS measurement")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the steady adjoint-gradient measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve measurement")
     ap.add_argument("--batch-only", action="store_true", help="run only the batched-solve measurement")
-    ap.add_argument("--no-timedep", action="store_true", help="skip the time-dependent measurement")
     ap.add_argument("--no-uw2", action="store_true", help="skip the second-order upwind measurement")
     ap.add_argument("--no-td-adjoint", action="store_true", help="skip the time-dependent adjoint measurement")
-    ap.add_argument("--td-adjoint-only", action="store_true", help="run only the time-dependent adjoint measurement")
-    ap.add_argument("--timedep-only", action="store_true", help="run only the time-dependent measurement")
     ap.add_argument("--oracle-times", action="store_true",
                     help="time the FP64 oracle itself on the host cores (CPU only) and exit")
-    ap.add_argument("--synth-cap", type=int, default=SYNTH_CAP,
-                    help="inner iterations of the synthetic solve per GSIS iteration (0: solve to 1e-12)")
+    ap.add_argument("--oracle-td-steps", type=int, default=0,
+                    help="with --oracle-times: time this many real oracle steps of the headline workload")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
