@@ -80,6 +80,7 @@ struct Plan {
     int limiter;                    // order 2: 0 Barth-Jespersen, 1 none
     int synth_cl;                   // synthetic solver: strip-solver cluster size, 0 = global-memory solver
     int synth_grid;                 // global-memory solver over a cooperative grid of this many CTAs (0: one cluster)
+    int synth_tiled;                // that grid solver in its tiled form (levels in per-CTA blocks)
     double* mg_gslots_d; float* mg_gslots_f;   // its reduction slots [3][2][kMaxCgBlocks]
     size_t synth_bytes;             // its dynamic shared memory
 

@@ -713,6 +713,646 @@ __global__ void __launch_bounds__(kMgBlock) mg_solve_grid_kernel(const MgArgs a)
     mg_solve_body(a, cx);
 }
 
+// ------------------------------------------------------------ tiled grid solver
+// The same iteration (FP64 refinement around FP32 MG-PCG, V-cycle with two
+// damped-Jacobi steps before and after, coarse correction x alpha) over a
+// cooperative grid, arranged so that each phase costs one grid barrier:
+//
+//  * CTAs 1..px*py own one rectangle of every distributed level (levels
+//    0..local_from-1): the level-0 rectangles of a px x py block grid, with
+//    boundaries at multiples of 2^(local_from-1), divided by 2^l on level l,
+//    so a rectangle's 2x2 restriction is the next level's rectangle.  CTA 0
+//    owns no rectangle; it runs the levels from local_from down in its
+//    shared memory.
+//  * Down phase of level l, per sub-tile of the rectangle (one sub-tile on
+//    the workloads' meshes): the sub-tile and a two-cell halo of r and of the
+//    level's coefficients go to shared memory, x1 = omega r / d and x2 = one
+//    Jacobi step are formed on all of it (a zero ring of ghost cells keeps
+//    the stencil branch-free; values near the halo's outer edge are wrong
+//    and never used), then on the own cells x2 is stored and the residual
+//    r - A x2 is restricted into the next level (on the last distributed
+//    level it is stored for CTA 0 to restrict).
+//  * Up phase: x2 + alpha P t_coarse and two Jacobi steps on the sub-tile
+//    with its halo; the own cells' result is the level's correction t.
+//  * CG: the level-0 down phase also performs the update s <- s - a q
+//    (pointwise, so halo cells repeat the owners' arithmetic bit for bit;
+//    s alternates between two buffers) and dl <- dl + a p; the new search
+//    direction uses A p = A z + beta (A p_old), so p, q and p.q take one
+//    phase.  A V-cycle costs 2 local_from + 1 barriers (old form: ~25).
+//  * Loads are issued several per thread before any is used (coefficients,
+//    read-only in the kernel, by asynchronous copies; values other CTAs
+//    wrote, from L2), so a phase waits on about one memory latency.
+constexpr int kTileMaxDim = 160;    // rectangles along one axis
+constexpr int kTileArrays = 6;      // shared arrays per sub-tile: r, 1/d, cx, cy, two iterates
+constexpr int kLocalArrays = 7;     // per coarse level in CTA 0: d, cx, cy, 1/d, x, t, r
+constexpr int kTileU = 2;           // cells per thread whose loads are in flight together
+constexpr int kTileBlock = 512;     // threads per CTA (128 registers each: no spills)
+constexpr int kTileLoadU = 4;       // the same in the sub-tile loads
+
+struct TileArgs {
+    MgArgs m;
+    int px, py;
+    int bx[kTileMaxDim + 1], by[kTileMaxDim + 1];   // level-0 rectangle boundaries (bx[px] = nx, by[py] = ny)
+    int tile_cells;                                 // padded cells of one sub-tile array
+};
+
+__device__ __forceinline__ void mg_cp_async4(void* smem, const void* gmem)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(smem)), "l"(gmem) : "memory");
+}
+
+// Cells k = tid, tid + nt, ... of a w-wide row-major block, as (i, j): one
+// division per thread, then steps with a carry.
+struct CellWalk {
+    int i, j, di, dj, w;
+    __device__ CellWalk(int w_) : w(w_)
+    {
+        i = (int)threadIdx.x % w;
+        j = (int)threadIdx.x / w;
+        di = (int)blockDim.x % w;
+        dj = (int)blockDim.x / w;
+    }
+    __device__ void next()
+    {
+        i += di;
+        j += dj;
+        if (i >= w) {
+            i -= w;
+            ++j;
+        }
+    }
+};
+
+// For the cells of rectangle [i0, i0 + w) x [j0, j0 + h) of a row-major
+// array with row length nx: v = f(c, i, j) for U cells first (their
+// loads in flight together), then g(c, v).
+template <class T, int U = kTileU, class F, class G>
+__device__ __forceinline__ void rect_cells(int i0, int j0, int w, int h, int nx, F f, G g)
+{
+    const int n = w * h;
+    if (n <= 0) return;
+    CellWalk cw(w);
+    for (int k0 = threadIdx.x; k0 < n; k0 += U * blockDim.x) {
+        T v[U];
+        int cc[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            cc[u] = -1;
+            if (k0 + u * (int)blockDim.x < n) {
+                const int gi = i0 + cw.i, gj = j0 + cw.j;
+                cc[u] = gj * nx + gi;
+                v[u] = f(cc[u], gi, gj);
+            }
+            cw.next();
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (cc[u] >= 0) g(cc[u], v[u]);
+    }
+}
+
+// One sub-tile region of level L in shared memory: cells [gi0, gi0 + rw) x
+// [gj0, gj0 + rh) of the level at local (li, lj), padded by a ghost ring.
+struct TileView {
+    int gi0, gj0, rw, rh, pw;
+    float *R, *ID, *CX, *CY, *XA, *XB;
+    __device__ int at(int li, int lj) const { return (lj + 1) * pw + li + 1; }
+};
+
+__device__ __forceinline__ float tile_nb(const TileView& v, const float* X, int p)
+{
+    return v.R[p] + v.CX[p] * X[p + 1] + v.CX[p - 1] * X[p - 1] + v.CY[p] * X[p + v.pw] +
+           v.CY[p - v.pw] * X[p - v.pw];
+}
+
+__device__ __forceinline__ float tile_jacobi(const TileView& v, const float* X, int p, float om, float id)
+{
+    return (1.f - om) * X[p] + om * tile_nb(v, X, p) * id;
+}
+
+// Rectangle of CTA b (1-based among the working CTAs) on level l.
+__device__ __forceinline__ void tile_rect(const TileArgs& a, int l, int b, int& i0, int& i1, int& j0, int& j1)
+{
+    const int bxi = (b - 1) % a.px, byi = (b - 1) / a.px;
+    i0 = a.bx[bxi] >> l;
+    i1 = bxi + 1 == a.px ? a.m.lv[l].nx : a.bx[bxi + 1] >> l;
+    j0 = a.by[byi] >> l;
+    j1 = byi + 1 == a.py ? a.m.lv[l].ny : a.by[byi + 1] >> l;
+}
+
+// Rows per sub-tile of a rectangle of width w (even, >= 2): what fits.
+__device__ __forceinline__ int tile_rows(const TileArgs& a, int w)
+{
+    int r = a.tile_cells / (w + 6) - 6;
+    r &= ~1;
+    return r < 2 ? 2 : r;
+}
+
+// Loads a sub-tile's region [si0-2, si1+2) x [sj0-2, sj1+2) (clipped to the
+// level) into v: d into ID (the first pass inverts it), the couplings (zero
+// across the level's edge), R = rin(c) and, if load_x, XA = xin(c, i, j);
+// zeroes the ghost ring of the iterates and couplings.
+template <class RF, class XF>
+__device__ __forceinline__ void tile_load(TileView& v, float* base, int cells, const MgLevelDev& L, int si0,
+                                          int si1, int sj0, int sj1, RF rin, bool load_x, XF xin)
+{
+    v.gi0 = max(si0 - 2, 0);
+    v.gj0 = max(sj0 - 2, 0);
+    v.rw = min(si1 + 2, L.nx) - v.gi0;
+    v.rh = min(sj1 + 2, L.ny) - v.gj0;
+    v.pw = v.rw + 2;
+    v.R = base;
+    v.ID = base + (size_t)cells;
+    v.CX = base + 2 * (size_t)cells;
+    v.CY = base + 3 * (size_t)cells;
+    v.XA = base + 4 * (size_t)cells;
+    v.XB = base + 5 * (size_t)cells;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int ph = v.rh + 2;
+    for (int k = tid; k < 2 * v.pw + 2 * ph; k += nt) {   // ghost ring: rows -1 and rh, columns -1 and rw
+        int p;
+        if (k < v.pw) p = k;
+        else if (k < 2 * v.pw) p = (ph - 1) * v.pw + (k - v.pw);
+        else if (k < 2 * v.pw + ph) p = (k - 2 * v.pw) * v.pw;
+        else p = (k - 2 * v.pw - ph) * v.pw + v.pw - 1;
+        v.XA[p] = 0.f;
+        v.XB[p] = 0.f;
+        v.CX[p] = 0.f;
+        v.CY[p] = 0.f;
+    }
+    const int n = v.rw * v.rh;
+    {   // coefficients: read-only in the kernel, so L1-cached asynchronous copies
+        CellWalk cw(v.rw);
+        for (int k = tid; k < n; k += nt, cw.next()) {
+            const int gi = v.gi0 + cw.i, gj = v.gj0 + cw.j, c = gj * L.nx + gi, p = v.at(cw.i, cw.j);
+            mg_cp_async4(v.ID + p, L.d + c);
+            if (gi + 1 < L.nx) mg_cp_async4(v.CX + p, L.cx + c);
+            else v.CX[p] = 0.f;
+            if (gj + 1 < L.ny) mg_cp_async4(v.CY + p, L.cy + c);
+            else v.CY[p] = 0.f;
+        }
+    }
+    {   // r (and x): values other CTAs wrote earlier in the kernel, from L2, kTileLoadU in flight per thread
+        CellWalk cw(v.rw);
+        for (int k0 = tid; k0 < n; k0 += kTileLoadU * nt) {
+            float rv[kTileLoadU], xv[kTileLoadU];
+            int pp[kTileLoadU];
+#pragma unroll
+            for (int u = 0; u < kTileLoadU; ++u) {
+                pp[u] = -1;
+                if (k0 + u * nt < n) {
+                    const int gi = v.gi0 + cw.i, gj = v.gj0 + cw.j, c = gj * L.nx + gi;
+                    pp[u] = v.at(cw.i, cw.j);
+                    rv[u] = rin(c);
+                    xv[u] = load_x ? xin(c, gi, gj) : 0.f;
+                }
+                cw.next();
+            }
+#pragma unroll
+            for (int u = 0; u < kTileLoadU; ++u)
+                if (pp[u] >= 0) {
+                    v.R[pp[u]] = rv[u];
+                    if (load_x) v.XA[pp[u]] = xv[u];
+                }
+        }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+}
+
+// V-cycle over the coarse levels [l0, nl) in CTA 0's shared memory: input
+// S[l0].r, output S[l0].x.  The same cycle as vcycle_local (x2 from r in one
+// pass, the residual, the 2x2 restriction; coarsest x = r / d; x2 + alpha P
+// x_coarse and two Jacobi steps), with 1/d precomputed and no division in a
+// loop; levels of at most 64 cells run in warp 0 alone.
+struct LocalLevel {
+    int nx, ny;
+    float *d, *cx, *cy, *id, *x, *t, *r;
+};
+
+template <bool WARP>
+__device__ __forceinline__ void local_down(const LocalLevel& L, const LocalLevel& C, float om)
+{
+    const int tid = WARP ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
+    const int nt = WARP ? 32 : (int)blockDim.x;
+    auto sync = [] { if (WARP) __syncwarp(); else __syncthreads(); };
+    const int nx = L.nx, ny = L.ny, n = nx * ny;
+    auto x1 = [&](int c) { return om * L.r[c] * L.id[c]; };
+    int i = tid % nx, j = tid / nx;
+    const int di = nt % nx, dj = nt / nx;
+    auto step = [&] { i += di; j += dj; if (i >= nx) { i -= nx; ++j; } };
+    for (int c = tid; c < n; c += nt, step()) {
+        float nb = L.r[c];
+        if (i + 1 < nx) nb += L.cx[c] * x1(c + 1);
+        if (i > 0) nb += L.cx[c - 1] * x1(c - 1);
+        if (j + 1 < ny) nb += L.cy[c] * x1(c + nx);
+        if (j > 0) nb += L.cy[c - nx] * x1(c - nx);
+        L.x[c] = (1.f - om) * x1(c) + om * nb * L.id[c];
+    }
+    sync();
+    i = tid % nx;
+    j = tid / nx;
+    for (int c = tid; c < n; c += nt, step()) {
+        float res = L.r[c] - L.d[c] * L.x[c];
+        if (i + 1 < nx) res += L.cx[c] * L.x[c + 1];
+        if (i > 0) res += L.cx[c - 1] * L.x[c - 1];
+        if (j + 1 < ny) res += L.cy[c] * L.x[c + nx];
+        if (j > 0) res += L.cy[c - nx] * L.x[c - nx];
+        L.t[c] = res;
+    }
+    sync();
+    const int cnx = C.nx, cn = cnx * C.ny;
+    int I = tid % cnx, J = tid / cnx;
+    const int dI = nt % cnx, dJ = nt / cnx;
+    for (int cc = tid; cc < cn; cc += nt) {
+        float sum = 0.f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int fi = 2 * I + (q & 1), fj = 2 * J + (q >> 1);
+            if (fi < nx && fj < ny) sum += L.t[fj * nx + fi];
+        }
+        C.r[cc] = sum;
+        I += dI;
+        J += dJ;
+        if (I >= cnx) { I -= cnx; ++J; }
+    }
+    sync();
+}
+
+template <bool WARP>
+__device__ __forceinline__ void local_up(const LocalLevel& L, const LocalLevel& C, float om, float alpha)
+{
+    const int tid = WARP ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
+    const int nt = WARP ? 32 : (int)blockDim.x;
+    auto sync = [] { if (WARP) __syncwarp(); else __syncthreads(); };
+    const int nx = L.nx, ny = L.ny, n = nx * ny, cnx = C.nx;
+    auto y0 = [&](int c, int i, int j) { return L.x[c] + alpha * C.x[(j >> 1) * cnx + (i >> 1)]; };
+    int i = tid % nx, j = tid / nx;
+    const int di = nt % nx, dj = nt / nx;
+    auto step = [&] { i += di; j += dj; if (i >= nx) { i -= nx; ++j; } };
+    for (int c = tid; c < n; c += nt, step()) {   // y1 = Jacobi(y0) into t
+        float nb = L.r[c];
+        if (i + 1 < nx) nb += L.cx[c] * y0(c + 1, i + 1, j);
+        if (i > 0) nb += L.cx[c - 1] * y0(c - 1, i - 1, j);
+        if (j + 1 < ny) nb += L.cy[c] * y0(c + nx, i, j + 1);
+        if (j > 0) nb += L.cy[c - nx] * y0(c - nx, i, j - 1);
+        L.t[c] = (1.f - om) * y0(c, i, j) + om * nb * L.id[c];
+    }
+    sync();
+    i = tid % nx;
+    j = tid / nx;
+    for (int c = tid; c < n; c += nt, step()) {   // y2 = Jacobi(y1) into x
+        float nb = L.r[c];
+        if (i + 1 < nx) nb += L.cx[c] * L.t[c + 1];
+        if (i > 0) nb += L.cx[c - 1] * L.t[c - 1];
+        if (j + 1 < ny) nb += L.cy[c] * L.t[c + nx];
+        if (j > 0) nb += L.cy[c - nx] * L.t[c - nx];
+        L.x[c] = (1.f - om) * L.t[c] + om * nb * L.id[c];
+    }
+    sync();
+}
+
+__device__ void vcycle_local_fast(const LocalLevel* S, int l0, int nl, float om, float alpha)
+{
+    int wl = l0;   // first level of at most 64 cells
+    while (wl < nl - 1 && S[wl].nx * S[wl].ny > 64) ++wl;
+    for (int l = l0; l < wl; ++l) local_down<false>(S[l], S[l + 1], om);
+    if (threadIdx.x < 32) {
+        for (int l = wl; l < nl - 1; ++l) local_down<true>(S[l], S[l + 1], om);
+        const LocalLevel& B = S[nl - 1];
+        for (int c = threadIdx.x; c < B.nx * B.ny; c += 32) B.x[c] = B.r[c] * B.id[c];
+        __syncwarp();
+        for (int l = nl - 2; l >= wl; --l) local_up<true>(S[l], S[l + 1], om, alpha);
+    }
+    __syncthreads();
+    for (int l = wl - 1; l >= l0; --l) local_up<false>(S[l], S[l + 1], om, alpha);
+}
+
+__global__ void __launch_bounds__(kTileBlock) mg_tile_grid_kernel(const TileArgs ta)
+{
+    const MgArgs& a = ta.m;
+    GridCtx cx(a);
+    __shared__ float slots_f[6];
+    __shared__ double slots_d[6];
+    __shared__ LocalLevel S[kMaxLevels];
+    extern __shared__ __align__(16) float mg_smem[];
+    if (ld_volatile_int(&a.status->done)) return;   // same value in every CTA (set by an earlier kernel)
+    const int nl = a.nl, lf = a.local_from;
+    const float om = a.omega, alpha = a.alpha;
+    const int b = blockIdx.x;                         // 0: coarse levels; 1..px*py: rectangles
+    const bool worker = b >= 1 && b <= ta.px * ta.py;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (b == 0) {   // the coarse levels in shared memory, with 1/d
+        if (tid == 0) {
+            size_t off = 0;
+            for (int l = lf; l < nl; ++l) {
+                const int n = a.lv[l].nx * a.lv[l].ny;
+                float* p = mg_smem + off;
+                S[l] = LocalLevel{a.lv[l].nx, a.lv[l].ny, p, p + n, p + 2 * n, p + 3 * n, p + 4 * n, p + 5 * n,
+                                  p + 6 * n};
+                off += ((size_t)kLocalArrays * n + 3) & ~(size_t)3;
+            }
+        }
+        __syncthreads();
+        for (int l = lf; l < nl; ++l) {
+            const int n = a.lv[l].nx * a.lv[l].ny;
+            for (int c = tid; c < n; c += nt) {
+                const float d = a.lv[l].d[c];
+                S[l].d[c] = d;
+                S[l].id[c] = 1.f / d;
+                S[l].cx[c] = a.lv[l].cx[c];
+                S[l].cy[c] = a.lv[l].cy[c];
+            }
+        }
+        __syncthreads();
+    }
+    int i0 = 0, i1 = 0, j0 = 0, j1 = 0;   // level-0 rectangle
+    if (worker) tile_rect(ta, 0, b, i0, i1, j0, j1);
+    const int nx = a.nx, ny = a.ny;
+    const int w0 = i1 - i0, h0 = j1 - j0;
+    const MgLevelDev& L0 = a.lv[0];
+    int sc = 0;   // the CG residual alternates between a.s (0) and level 0's r (1)
+    auto sbuf = [&](int k) { return k ? L0.r : a.s; };
+    float* const z = L0.t;
+    int rotf = 0, rotd = 0;
+
+    auto down_level = [&](int l, auto rin) {
+        const MgLevelDev& L = a.lv[l];
+        int si0, si1, sj0, sj1;
+        tile_rect(ta, l, b, si0, si1, sj0, sj1);
+        if (si1 <= si0 || sj1 <= sj0) return;
+        const int rows = tile_rows(ta, si1 - si0);
+        const bool last = l == lf - 1;
+        const MgLevelDev& C = a.lv[l + 1];
+        for (int t0 = sj0; t0 < sj1; t0 += rows) {
+            const int t1 = min(t0 + rows, sj1);
+            TileView v;
+            tile_load(v, mg_smem, ta.tile_cells, L, si0, si1, t0, t1, rin, false,
+                      [](int, int, int) { return 0.f; });
+            const int n = v.rw * v.rh;
+            {   // x1 = omega r / d (and 1/d in place)
+                CellWalk cw(v.rw);
+                for (int k = tid; k < n; k += nt, cw.next()) {
+                    const int p = v.at(cw.i, cw.j);
+                    const float id = 1.f / v.ID[p];
+                    v.ID[p] = id;
+                    v.XA[p] = om * v.R[p] * id;
+                }
+            }
+            __syncthreads();
+            {
+                CellWalk cw(v.rw);
+                for (int k = tid; k < n; k += nt, cw.next()) {
+                    const int p = v.at(cw.i, cw.j);
+                    v.XB[p] = tile_jacobi(v, v.XA, p, om, v.ID[p]);
+                }
+            }
+            __syncthreads();
+            // own cells: store x2; the residual r - A x2 into XA (its x1 is no longer read)
+            const int ow = si1 - si0, oh = t1 - t0;
+            {
+                CellWalk cw(ow);
+                for (int k = tid; k < ow * oh; k += nt, cw.next()) {
+                    const int gi = si0 + cw.i, gj = t0 + cw.j, c = gj * L.nx + gi;
+                    const int p = v.at(gi - v.gi0, gj - v.gj0);
+                    const float res = tile_nb(v, v.XB, p) - __frcp_rn(v.ID[p]) * v.XB[p];
+                    L.x[c] = v.XB[p];
+                    if (last) L.t[c] = res;   // restricted by CTA 0
+                    else v.XA[p] = res;
+                }
+            }
+            __syncthreads();
+            if (!last) {   // 2x2 restriction into the next level's rectangle
+                const int I0 = si0 >> 1, I1 = (si1 + 1) >> 1, J0 = t0 >> 1, J1 = (t1 + 1) >> 1;
+                const int cw_ = I1 - I0;
+                CellWalk cw(cw_);
+                for (int k = tid; k < cw_ * (J1 - J0); k += nt, cw.next()) {
+                    const int I = I0 + cw.i, J = J0 + cw.j;
+                    float sum = 0.f;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int gi = 2 * I + (q & 1), gj = 2 * J + (q >> 1);
+                        if (gi < si1 && gj < t1) sum += v.XA[v.at(gi - v.gi0, gj - v.gj0)];
+                    }
+                    C.r[J * C.nx + I] = sum;
+                }
+            }
+            __syncthreads();   // the next sub-tile reuses the arrays
+        }
+    };
+    auto up_level = [&](int l, auto rin, bool level0, float& lrz) {
+        const MgLevelDev& L = a.lv[l];
+        const MgLevelDev& C = a.lv[l + 1];
+        const float* ct = C.t;   // the coarse correction (CTA 0 copies its output there)
+        int si0, si1, sj0, sj1;
+        tile_rect(ta, l, b, si0, si1, sj0, sj1);
+        if (si1 <= si0 || sj1 <= sj0) return;
+        const int rows = tile_rows(ta, si1 - si0);
+        for (int t0 = sj0; t0 < sj1; t0 += rows) {
+            const int t1 = min(t0 + rows, sj1);
+            TileView v;
+            tile_load(v, mg_smem, ta.tile_cells, L, si0, si1, t0, t1, rin, true,
+                      [&](int c, int gi, int gj) {
+                          return __ldcg(L.x + c) + alpha * __ldcg(ct + (gj >> 1) * C.nx + (gi >> 1));
+                      });
+            const int n = v.rw * v.rh;
+            {
+                CellWalk cw(v.rw);
+                for (int k = tid; k < n; k += nt, cw.next()) {
+                    const int p = v.at(cw.i, cw.j);
+                    const float id = 1.f / v.ID[p];
+                    v.ID[p] = id;
+                    v.XB[p] = tile_jacobi(v, v.XA, p, om, id);
+                }
+            }
+            __syncthreads();
+            const int ow = si1 - si0, oh = t1 - t0;
+            {
+                CellWalk cw(ow);
+                for (int k = tid; k < ow * oh; k += nt, cw.next()) {
+                    const int gi = si0 + cw.i, gj = t0 + cw.j, c = gj * L.nx + gi;
+                    const int p = v.at(gi - v.gi0, gj - v.gj0);
+                    const float y = tile_jacobi(v, v.XB, p, om, v.ID[p]);
+                    L.t[c] = y;
+                    if (level0) lrz += v.R[p] * y;
+                }
+            }
+            __syncthreads();
+        }
+    };
+    // levels 1 .. lf-1 down, the coarse levels in CTA 0, back up to level 1;
+    // every phase ends on a grid barrier
+    auto inner_levels = [&]() {
+        for (int l = 1; l < lf; ++l) {
+            if (worker) {
+                const float* rl = a.lv[l].r;
+                down_level(l, [&](int c) { return __ldcg(rl + c); });
+            }
+            cx.sync();
+        }
+        if (b == 0) {   // restriction of level lf-1's residual, then the coarse V-cycle
+            const MgLevelDev& F = a.lv[lf - 1];
+            const LocalLevel& Lc = S[lf];
+            const int n = Lc.nx * Lc.ny;
+            for (int cc = tid; cc < n; cc += nt) {
+                const int J = cc / Lc.nx, I = cc - J * Lc.nx;
+                float sum = 0.f;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int gi = 2 * I + (q & 1), gj = 2 * J + (q >> 1);
+                    if (gi < F.nx && gj < F.ny) sum += __ldcg(F.t + gj * F.nx + gi);
+                }
+                Lc.r[cc] = sum;
+            }
+            __syncthreads();
+            vcycle_local_fast(S, lf, nl, om, alpha);
+            for (int c = tid; c < n; c += nt) a.lv[lf].t[c] = Lc.x[c];
+        }
+        cx.sync();
+        for (int l = lf - 1; l >= 1; --l) {
+            if (worker) {
+                const float* rl = a.lv[l].r;
+                float dummy = 0.f;
+                up_level(l, [&](int c) { return __ldcg(rl + c); }, false, dummy);
+            }
+            cx.sync();
+        }
+    };
+
+    // ---- FP64 refinement
+    int total = 0;
+    double relres = 0.0, bb = 0.0;
+    for (int outer = 0;; ++outer) {
+        if (outer > 0) cx.sync();   // every CTA's x update visible
+        const double* xs = outer == 0 ? a.guess : a.x;
+        double lrr = 0.0, lbb = 0.0;
+        float* s = sbuf(sc);
+        rect_cells<double2, 2>(i0, j0, w0, h0, nx,
+                            [&](int c, int i, int j) {
+                                double v = a.diag[c] * __ldcg(xs + c);
+                                if (i + 1 < nx) v -= a.cx[c] * __ldcg(xs + c + 1);
+                                if (i > 0) v -= a.cx[c - 1] * __ldcg(xs + c - 1);
+                                if (j + 1 < ny) v -= a.cy[c] * __ldcg(xs + c + nx);
+                                if (j > 0) v -= a.cy[c - nx] * __ldcg(xs + c - nx);
+                                const double bc = a.b[c];
+                                return make_double2(bc - v, bc);
+                            },
+                            [&](int c, double2 rb) {
+                                if (outer == 0) {
+                                    a.x[c] = xs[c];
+                                    lbb += rb.y * rb.y;
+                                }
+                                s[c] = (float)rb.x;
+                                a.dl[c] = 0.f;
+                                lrr += rb.x * rb.x;
+                            });
+        double v2[2];
+        cx.sum2d(lrr, lbb, v2, slots_d, rotd);
+        if (outer == 0) bb = v2[1];
+        const double rr = v2[0];
+        relres = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+        if (rr <= a.rtol * a.rtol * bb || total >= a.max_iter) break;
+        // z = M s: level 0 down, the inner levels, level 0 up
+        if (worker) {
+            const float* sr = s;
+            down_level(0, [&](int c) { return __ldcg(sr + c); });
+        }
+        cx.sync();
+        inner_levels();
+        float lrz = 0.f, lss = 0.f;
+        if (worker) {
+            const float* sr = s;
+            up_level(0, [&](int c) { return __ldcg(sr + c); }, true, lrz);
+            rect_cells<float>(i0, j0, w0, h0, nx, [&](int c, int, int) { return s[c]; },
+                              [&](int, float sv) { lss += sv * sv; });
+        }
+        float f2[2];
+        cx.sum2f(lrz, lss, f2, slots_f, rotf);
+        float rz = f2[0];
+        if (!(rz > 0.f) || !(rz < INFINITY) || !isfinite(rr)) {
+            // no usable FP32 search direction (as in mg_solve_body): leave;
+            // a non-finite residual poisons x so that Err(rho) reports it
+            const bool bad = !(rz == 0.f) || !isfinite(rr);
+            if (bad) {
+                rect_cells<int>(i0, j0, w0, h0, nx, [](int, int, int) { return 0; },
+                                [&](int c, int) { a.x[c] = kNaN; });
+                relres = kNaN;
+            }
+            break;
+        }
+        const float istop = a.inner_rtol * a.inner_rtol * f2[1];
+        float beta = 0.f;
+        bool first = true;
+        while (total < a.max_iter && rz > 0.f) {
+            // p = z + beta p, q = A p = A z + beta q, p.q (first: p = z, q = A z)
+            float lpq = 0.f;
+            rect_cells<float2, 2>(i0, j0, w0, h0, nx,
+                               [&](int c, int i, int j) {
+                                   const float zc = __ldcg(z + c);
+                                   float az = L0.d[c] * zc;
+                                   if (i + 1 < nx) az -= L0.cx[c] * __ldcg(z + c + 1);
+                                   if (i > 0) az -= L0.cx[c - 1] * __ldcg(z + c - 1);
+                                   if (j + 1 < ny) az -= L0.cy[c] * __ldcg(z + c + nx);
+                                   if (j > 0) az -= L0.cy[c - nx] * __ldcg(z + c - nx);
+                                   const float pv = first ? zc : __fmaf_rn(beta, a.p[c], zc);
+                                   const float qv = first ? az : __fmaf_rn(beta, a.q[c], az);
+                                   return make_float2(pv, qv);
+                               },
+                               [&](int c, float2 pq) {
+                                   a.p[c] = pq.x;
+                                   a.q[c] = pq.y;
+                                   lpq += pq.x * pq.y;
+                               });
+            cx.sum2f(lpq, 0.f, f2, slots_f, rotf);
+            first = false;
+            const float al = rz / f2[0];
+            ++total;
+            const bool more = total < a.max_iter;
+            // s <- s - al q, dl <- dl + al p; then level 0 down on the new s
+            const float* so = sbuf(sc);
+            float* sn = sbuf(sc ^ 1);
+            float lss2 = 0.f;
+            if (worker) {
+                rect_cells<float2>(i0, j0, w0, h0, nx,
+                                   [&](int c, int, int) {
+                                       return make_float2(__fmaf_rn(-al, __ldcg(a.q + c), __ldcg(so + c)),
+                                                          __fmaf_rn(al, a.p[c], a.dl[c]));
+                                   },
+                                   [&](int c, float2 sd) {
+                                       sn[c] = sd.x;
+                                       a.dl[c] = sd.y;
+                                       lss2 += sd.x * sd.x;
+                                   });
+                // the same arithmetic as the owners' update above: halo cells get the same bits
+                if (more) down_level(0, [&](int c) { return __fmaf_rn(-al, __ldcg(a.q + c), __ldcg(so + c)); });
+            }
+            sc ^= 1;
+            cx.sum2f(lss2, 0.f, f2, slots_f, rotf);
+            if (f2[0] <= istop || !more) break;
+            inner_levels();
+            float lrz2 = 0.f;
+            if (worker) {
+                const float* sr = sbuf(sc);
+                up_level(0, [&](int c) { return __ldcg(sr + c); }, true, lrz2);
+            }
+            cx.sum2f(lrz2, 0.f, f2, slots_f, rotf);
+            beta = f2[0] / rz;
+            rz = f2[0];
+        }
+        rect_cells<float>(i0, j0, w0, h0, nx, [&](int c, int, int) { return a.dl[c]; },
+                          [&](int c, float d) { a.x[c] += (double)d; });
+        if (total >= a.max_iter) {   // budget spent: no further residual evaluation
+            relres = -1.0;
+            break;
+        }
+    }
+    if (b == 0 && tid == 0) {
+        a.status->synth_iters = total;
+        a.status->synth_iters_total += total;
+        a.status->synth_relres = relres;
+    }
+}
+
 // ------------------------------------------------------------ strip solver
 // The same iteration (FP64 refinement around FP32 MG-PCG, identical cycle)
 // with every level resident in the cluster's shared memory.  Levels 0..ld
@@ -1409,6 +2049,65 @@ cudaError_t raise_limit(const void* fn, size_t bytes)
     return e;
 }
 
+size_t tile_smem_cap()
+{
+    static size_t cap = [] {
+        int dev = 0, c = 0;
+        cudaFuncAttributes fa{};
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&c, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+            cudaFuncGetAttributes(&fa, mg_tile_grid_kernel) != cudaSuccess) {
+            cudaGetLastError();
+            return (size_t)0;
+        }
+        return (size_t)c > fa.sharedSizeBytes ? (size_t)c - fa.sharedSizeBytes : (size_t)0;
+    }();
+    return cap;
+}
+
+// Rectangle grid of the tiled solver on G CTAs (CTA 0 runs the coarse
+// levels): px x py <= G - 1 rectangles whose level-0 boundaries are multiples
+// of 2^(local_from - 1), chosen to minimise the largest rectangle with its
+// halo; sub-tile arrays sized to the shared memory that is left.  False when
+// the mesh has fewer than two distributed levels or a sub-tile of the widest
+// rectangle would not fit.
+bool tile_plan(const Plan& P, int G, TileArgs& t, size_t& smem)
+{
+    const int lf = P.mg.local_from;
+    const size_t cap = tile_smem_cap();
+    size_t local_bytes = 0;   // CTA 0's coarse levels (kLocalArrays arrays each, 16-byte aligned)
+    for (int l = lf; l < P.mg.nl; ++l)
+        local_bytes += (((size_t)kLocalArrays * P.mg.nx[l] * P.mg.ny[l] + 3) & ~(size_t)3) * sizeof(float);
+    if (lf < 2 || G < 2 || cap < local_bytes) return false;
+    const int A = 1 << (lf - 1);
+    const int gx = (P.nx + A - 1) / A, gy = (P.ny + A - 1) / A;
+    long best = -1;
+    int bpx = 0, bpy = 0;
+    for (int px = 1; px <= std::min(gx, kTileMaxDim); ++px) {
+        const int py = std::min({(G - 1) / px, gy, kTileMaxDim});
+        if (py < 1) break;
+        const long w = (long)((gx + px - 1) / px) * A, h = (long)((gy + py - 1) / py) * A;
+        const long cost = (w + 4) * (h + 4);
+        if (best < 0 || cost < best) {
+            best = cost;
+            bpx = px;
+            bpy = py;
+        }
+    }
+    if (best < 0) return false;
+    t.px = bpx;
+    t.py = bpy;
+    int wmax = 0;
+    for (int k = 0; k <= bpx; ++k) t.bx[k] = k == bpx ? P.nx : (int)((long)k * gx / bpx) * A;
+    for (int k = 0; k <= bpy; ++k) t.by[k] = k == bpy ? P.ny : (int)((long)k * gy / bpy) * A;
+    for (int k = 0; k < bpx; ++k) wmax = std::max(wmax, t.bx[k + 1] - t.bx[k]);
+    const size_t cells = cap / ((size_t)kTileArrays * sizeof(float));
+    if ((size_t)(wmax + 6) * 8 > cells) return false;   // two rows of the widest rectangle
+    t.tile_cells = (int)std::min(cells, (size_t)1 << 20);
+    smem = std::max(local_bytes, (size_t)kTileArrays * t.tile_cells * sizeof(float));
+    return true;
+}
+
 void strip_fill(const Plan& P, const double* guess, double* out, SArgs& sa)
 {
     sa.nx = P.nx; sa.ny = P.ny; sa.N = P.N;
@@ -1494,6 +2193,21 @@ cudaError_t plan_synthetic(Plan& P)
             P.synth_grid = std::min(kMaxCgBlocks, per_sm * P.num_sms);
         }
         cudaGetLastError();
+        // its tiled form: one CTA per SM
+        TileArgs t{};
+        size_t tsm = 0;
+        P.synth_tiled = 0;
+        if (P.synth_grid > 0 && tile_plan(P, std::min(kMaxCgBlocks, P.num_sms), t, tsm) &&
+            raise_limit((const void*)mg_tile_grid_kernel, tsm) == cudaSuccess) {
+            per_sm = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mg_tile_grid_kernel, kTileBlock, tsm) ==
+                    cudaSuccess && per_sm >= 1) {
+                P.synth_tiled = 1;
+                P.synth_grid = std::min(kMaxCgBlocks, P.num_sms);
+                P.synth_bytes = tsm;
+            }
+        }
+        cudaGetLastError();
     }
     return cudaSuccess;
 }
@@ -1511,6 +2225,15 @@ cudaError_t launch_synthetic_solve(const Plan& P, const double* guess, double* o
     }
     size_t smem = 0;
     MgArgs a = fallback_args(P, guess, out, smem);
+    if (P.synth_grid > 0 && P.synth_tiled) {
+        TileArgs t{};
+        size_t tsm = 0;
+        if (!tile_plan(P, P.synth_grid, t, tsm)) return cudaErrorInvalidConfiguration;
+        t.m = a;
+        void* args[] = {&t};
+        return cudaLaunchCooperativeKernel((const void*)mg_tile_grid_kernel, dim3(P.synth_grid), dim3(kTileBlock),
+                                           args, tsm, st);
+    }
     if (P.synth_grid > 0) {
         void* args[] = {&a};
         return cudaLaunchCooperativeKernel((const void*)mg_solve_grid_kernel, dim3(P.synth_grid), dim3(kMgBlock),
