@@ -13,7 +13,8 @@ constexpr int kWarp = 32;
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxK = 4096;            // directions per quadrature (host-side check)
 constexpr int kMaxSide = (1 << 20) - 1; // cells per mesh side
-constexpr int kSweepPairs = 8;          // (compute, copy) warp pairs per sweep CTA
+constexpr int kSweepMaxPairs = 12;      // (compute, copy) warp pairs per sweep CTA, at most: as many as fit
+constexpr size_t kSweepSmemCap = 231424; // dynamic shared memory a sweep CTA may take (the 227 KB opt-in less 1 KB)
 constexpr int kRedBlock = 256;          // threads per reduction / stencil block
 constexpr int kMaxCgBlocks = 1024;      // partials capacity of the fixed-order grid reductions
 constexpr int kMaxLevels = 24;          // multigrid levels (2x2 aggregation down to one cell)

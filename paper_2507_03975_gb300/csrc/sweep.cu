@@ -324,7 +324,7 @@ template <> struct Bits<float> {
 // updates in the chunk (padded rows: conflict-free column access), the
 // column coefficients of the SEG + 31 columns the skewed lanes touch, the
 // 1/d table rows of the chunk (FP64) and the SEG south values of lane 0.
-template <typename T, bool PT, bool PRE>
+template <typename T, bool PT, bool PRE, bool WIDE = false>
 struct SweepSmem {
     static constexpr int SEG = 64 / (int)sizeof(T);
     static constexpr int NBUF = 3;
@@ -344,15 +344,24 @@ struct SweepSmem {
     static constexpr size_t buf_bytes = off_h + 16;
     static constexpr size_t bar_bytes = 64;                   // full[NBUF], empty[NBUF]
     static constexpr size_t pair_bytes = bar_bytes + NBUF * buf_bytes;
-    static constexpr size_t bytes = kSweepPairs * pair_bytes;
+    // pairs per CTA: 8 (two chains per SM sub-partition), or in the WIDE
+    // form (the batched sweep) as many as the shared memory holds up to
+    // kSweepMaxPairs: the batch's short units gain from more chains in
+    // flight (64 problems: 0.69 -> 0.55 ms), the long units of one large
+    // problem lose (1024^2 S16 FP64: 1.33 -> 1.50 ms)
+    static constexpr size_t kFit = kSweepSmemCap / pair_bytes;
+    static constexpr size_t kWant = WIDE ? (size_t)kSweepMaxPairs : (size_t)8;
+    static constexpr int PAIRS = (int)(kFit < kWant ? kFit : kWant);
+    static constexpr size_t bytes = PAIRS * pair_bytes;
+    static_assert(PAIRS >= 4, "a sweep CTA needs at least one pair per sub-partition");
     static_assert(2 * NBUF * 8 <= bar_bytes, "barrier space");
 };
 
-// One persistent CTA per SM runs kSweepPairs warp pairs; a pair's copy warp
+// One persistent CTA per SM runs PAIRS warp pairs; a pair's copy warp
 // chooses the units (direction s, band), u = band * K + s, and hands each to
 // its compute warp in the header of the unit's first chunk buffer.  When the
 // whole grid is resident (every CTA checks in within a few microseconds) the
-// units are placed statically: pair p of CTA c takes u = p G + c + i 8G, so
+// units are placed statically: pair p of CTA c takes u = p G + c + i PAIRS G, so
 // each SM's first units come from different bands and run at different
 // times; every unit is owned by a running pair and waits only on u - K.
 // Otherwise (part of the grid held back by other work on the GPU) the pairs
@@ -369,7 +378,7 @@ struct SweepSmem {
 // "empty".  Every wait is bounded; on time-out kErrTimeout is raised and the
 // warp leaves after its copies in flight have landed.
 template <typename T, int MODE, bool PRE, bool BATCH>
-__global__ void __launch_bounds__(kSweepPairs * 64, 1)
+__global__ void __launch_bounds__(SweepSmem<T, MODE != kSrcPlain, PRE, BATCH>::PAIRS * 64, 1)
 sweep_kernel(const SweepArgs<T> a1, const SweepBatch<T> bt)
 {
     constexpr bool PT = MODE == kSrcPseudoTime, ADJ = MODE == kSrcAdjoint, DELTA = MODE == kSrcDelta;
@@ -377,19 +386,19 @@ sweep_kernel(const SweepArgs<T> a1, const SweepBatch<T> bt)
     // coarser stores (fewer store instructions per step); FP64 writes each
     // result at once (there the write-out would sit on the band hand-off path)
     constexpr bool STAGE = sizeof(T) == 4;
-    using SM = SweepSmem<T, MODE != kSrcPlain, PRE>;
+    using SM = SweepSmem<T, MODE != kSrcPlain, PRE, BATCH>;
     using B = Bits<T>;
     constexpr int SEG = SM::SEG, NBUF = SM::NBUF, RS = SM::RS, NW = SM::NW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool copier = warp >= kSweepPairs;
-    const int pair = copier ? warp - kSweepPairs : warp;
+    const bool copier = warp >= SM::PAIRS;
+    const int pair = copier ? warp - SM::PAIRS : warp;
     unsigned char* pbase = smem_raw + (size_t)pair * SM::pair_bytes;
     unsigned long long* full = reinterpret_cast<unsigned long long*>(pbase);
     unsigned long long* empty = full + NBUF;
     auto buf = [&](int b) { return pbase + SM::bar_bytes + (size_t)b * SM::buf_bytes; };
 
-    if (threadIdx.x < kSweepPairs) {
+    if (threadIdx.x < SM::PAIRS) {
         unsigned long long* f = reinterpret_cast<unsigned long long*>(smem_raw + (size_t)threadIdx.x * SM::pair_bytes);
         for (int b = 0; b < NBUF; ++b) {
             mbar_init(f + b, 64);            // 32 cp.async arrivals + 32 lane arrivals
@@ -441,13 +450,13 @@ sweep_kernel(const SweepArgs<T> a1, const SweepBatch<T> bt)
                 for (;;) {
                     if (placed) {
                         t = next_static;
-                        next_static += kSweepPairs * G;
+                        next_static += SM::PAIRS * G;
                     } else {
-                        if (first && pair >= kSweepPairs / 2) {
+                        if (first && pair >= SM::PAIRS / 2) {
                             // the second half of the pairs shares sub-partitions with the
                             // first half: let the first half take the first units, so that
                             // concurrently running units start on distinct sub-partitions
-                            const unsigned want = min((unsigned)ntasks, (unsigned)(kSweepPairs / 2) * (unsigned)G);
+                            const unsigned want = min((unsigned)ntasks, (unsigned)(SM::PAIRS / 2) * (unsigned)G);
                             const long long t0 = clock64();
                             while (*reinterpret_cast<volatile unsigned*>(c_tasks) < want && clock64() - t0 < 20000)
                                 __nanosleep(64);
@@ -773,7 +782,7 @@ sweep_kernel(const SweepArgs<T> a1, const SweepBatch<T> bt)
     __syncwarp();
     if (lane == 0) {
         __threadfence();
-        if (atomicAdd(c_exits, 1u) == (unsigned)G * (unsigned)(2 * kSweepPairs) - 1u) {
+        if (atomicAdd(c_exits, 1u) == (unsigned)G * (unsigned)(2 * SM::PAIRS) - 1u) {
             *c_tasks = 0u;
             *c_arrived = 0u;
             *c_mode = 0;
@@ -947,8 +956,15 @@ int grid_for(long long n, int block, int cap)
     return (int)g;
 }
 
-template <typename T, int MODE>
+template <typename T, int MODE, bool BATCH = false>
 size_t sweep_smem();
+
+// Threads of one sweep CTA of this variant (its pairs x 64).
+template <typename T, int MODE, bool BATCH = false>
+constexpr int sweep_threads()
+{
+    return SweepSmem<T, MODE != kSrcPlain, sizeof(T) == 8, BATCH>::PAIRS * 64;
+}
 
 template <typename T, int MODE>
 SweepArgs<T> sweep_args(const Plan& P)
@@ -1000,7 +1016,7 @@ template <typename T, int MODE, bool PRE>
 cudaError_t launch_sweep_t(Plan& P, cudaStream_t st)
 {
     const SweepArgs<T> a = sweep_args<T, MODE>(P);
-    sweep_kernel<T, MODE, PRE, false><<<P.sweep_grid, kSweepPairs * 64, sweep_smem<T, MODE>(), st>>>(a, SweepBatch<T>{});
+    sweep_kernel<T, MODE, PRE, false><<<P.sweep_grid, sweep_threads<T, MODE>(), sweep_smem<T, MODE>(), st>>>(a, SweepBatch<T>{});
     return cudaGetLastError();
 }
 
@@ -1021,7 +1037,7 @@ cudaError_t launch_sweep_batch_t(const BatchTables& bt, cudaStream_t st)
     b.mode = &bt.status->sweep_mode;
     b.err = &bt.status->error;
     b.wait_cycles = bt.wait_cycles;
-    sweep_kernel<T, MODE, sizeof(T) == 8, true><<<bt.sweep_grid, kSweepPairs * 64, sweep_smem<T, MODE>(), st>>>(
+    sweep_kernel<T, MODE, sizeof(T) == 8, true><<<bt.sweep_grid, sweep_threads<T, MODE, true>(), sweep_smem<T, MODE, true>(), st>>>(
         SweepArgs<T>{}, b);
     return cudaGetLastError();
 }
@@ -1085,17 +1101,18 @@ cudaError_t launch_moments_t(const Plan& P, bool with_F, bool with_P, double* rh
     return cudaGetLastError();
 }
 
-template <typename T, int MODE>
+template <typename T, int MODE, bool BATCH>
 size_t sweep_smem()
 {
-    return SweepSmem<T, MODE != kSrcPlain, sizeof(T) == 8>::bytes;
+    return SweepSmem<T, MODE != kSrcPlain, sizeof(T) == 8, BATCH>::bytes;
 }
+
 
 template <typename T, int MODE, bool BATCH>
 cudaError_t sweep_attr()
 {
     return cudaFuncSetAttribute(sweep_kernel<T, MODE, sizeof(T) == 8, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sweep_smem<T, MODE>());
+                                (int)sweep_smem<T, MODE, BATCH>());
 }
 
 // Raises the dynamic shared-memory limit of fn to at least `bytes` (never
@@ -1145,7 +1162,7 @@ int sweep_occupancy()
 {
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<T, MODE, sizeof(T) == 8, BATCH>,
-                                                      kSweepPairs * 64, sweep_smem<T, MODE>()) != cudaSuccess)
+                                                      sweep_threads<T, MODE, BATCH>(), sweep_smem<T, MODE, BATCH>()) != cudaSuccess)
         return 0;
     return n;
 }
@@ -1229,7 +1246,7 @@ cudaError_t launch_sweep(Plan& P, cudaStream_t st)
         a.src = P.X;
         a.src_stride = P.N;
         sweep_kernel<double, kSrcPlain, true, false>
-            <<<P.sweep_grid, kSweepPairs * 64, sweep_smem<double, kSrcPlain>(), st>>>(a, SweepBatch<double>{});
+            <<<P.sweep_grid, sweep_threads<double, kSrcPlain>(), sweep_smem<double, kSrcPlain>(), st>>>(a, SweepBatch<double>{});
         return cudaGetLastError();
     }
     if (P.fp32 && P.pt && P.X_f) {
@@ -1241,7 +1258,7 @@ cudaError_t launch_sweep(Plan& P, cudaStream_t st)
         a.src_stride = P.N;
         a.sigt = P.sigt_d;
         sweep_kernel<float, kSrcPlain, false, false>
-            <<<P.sweep_grid, kSweepPairs * 64, sweep_smem<float, kSrcPlain>(), st>>>(a, SweepBatch<float>{});
+            <<<P.sweep_grid, sweep_threads<float, kSrcPlain>(), sweep_smem<float, kSrcPlain>(), st>>>(a, SweepBatch<float>{});
         return cudaGetLastError();
     }
     if (P.fp32) {
@@ -1271,7 +1288,7 @@ cudaError_t launch_sweep_pt_into_t(Plan& P, const void* src, const void* iold, v
     a.I = static_cast<T*>(out);
     a.inflow = nullptr;
     sweep_kernel<T, kSrcPseudoTime, PRE, false>
-        <<<P.sweep_grid, kSweepPairs * 64, sweep_smem<T, kSrcPseudoTime>(), st>>>(a, SweepBatch<T>{});
+        <<<P.sweep_grid, sweep_threads<T, kSrcPseudoTime>(), sweep_smem<T, kSrcPseudoTime>(), st>>>(a, SweepBatch<T>{});
     return cudaGetLastError();
 }
 

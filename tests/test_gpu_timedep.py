@@ -130,3 +130,35 @@ def test_full_size_equilibrium_is_preserved(gs):
     assert r["status"] == gs.GSIS_OK
     assert np.abs(r["rho"].cpu().numpy() / (4 * math.pi * eq) - 1).max() < 1e-5
     assert np.abs(r["T"].cpu().numpy() / T0 - 1).max() < 1e-5
+
+
+@pytest.fixture(scope="module")
+def full_size_first_step():
+    """The oracle's first backward-Euler step of the headline workload
+    (1024^2 S16, the x4 channel, cold start T = 0.1, dt = 1e-3) with two GSIS
+    iterations (sparse LU of the synthetic system)."""
+    from oracle import gsis as G
+    p = W.config_timedep()
+    td = W.TIMEDEP
+    tp = TD.TimeParams(dt=td["dt"], c=td["c"], a=td["a"], cv=td["cv"])
+    T0 = np.full(p.N, td["T0"])
+    rho0 = td["a"] * td["c"] * T0 ** 4
+    G.use_threads(True)   # the oracle's C sweeps on every host core (the same bits as one thread)
+    try:
+        o = TD.gsis_time_step(p, tp, rho0, T0, TD.isotropic(p, rho0), fixed_iters=2)
+    finally:
+        G.use_threads(False)
+    return p, tp, rho0, T0, o
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_full_size_first_step_matches_oracle(gs, full_size_first_step, prec):
+    """The headline workload itself: the first step's two GSIS iterations,
+    synthetic system solved to 1e-14, against the oracle's: 1e-9 (FP64
+    sweeps), 1e-5 (FP32 sweeps)."""
+    p, tp, rho0, T0, o = full_size_first_step
+    r = _solve(gs, p, tp, 1, rho0, T0, precision=gs.FP64 if prec == "fp64" else gs.FP32_SWEEP, fixed_iters=2,
+               max_iter=2, synth_rtol=1e-14, synth_max_iter=3000)
+    tol = 1e-9 if prec == "fp64" else 1e-5
+    assert rel(r["rho"].cpu().numpy(), o["rho"]) < tol
+    assert rel(r["T"].cpu().numpy(), o["T"]) < tol
