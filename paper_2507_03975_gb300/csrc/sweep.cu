@@ -345,10 +345,9 @@ struct SweepSmem {
     static constexpr size_t bar_bytes = 64;                   // full[NBUF], empty[NBUF]
     static constexpr size_t pair_bytes = bar_bytes + NBUF * buf_bytes;
     // pairs per CTA: 8 (two chains per SM sub-partition), or in the WIDE
-    // form (the batched sweep) as many as the shared memory holds up to
-    // kSweepMaxPairs: the batch's short units gain from more chains in
-    // flight (64 problems: 0.69 -> 0.55 ms), the long units of one large
-    // problem lose (1024^2 S16 FP64: 1.33 -> 1.50 ms)
+    // form as many as the shared memory holds up to kSweepMaxPairs (the
+    // batched sweep: 64 problems 0.69 -> 0.55 ms; with staged write-out,
+    // the FP64 sweep of a problem with many units, below)
     static constexpr size_t kFit = kSweepSmemCap / pair_bytes;
     static constexpr size_t kWant = WIDE ? (size_t)kSweepMaxPairs : (size_t)8;
     static constexpr int PAIRS = (int)(kFit < kWant ? kFit : kWant);
@@ -377,16 +376,18 @@ struct SweepSmem {
 // to I, and the last lane also to this band's hand-off row, then arrives on
 // "empty".  Every wait is bounded; on time-out kErrTimeout is raised and the
 // warp leaves after its copies in flight have landed.
-template <typename T, int MODE, bool PRE, bool BATCH>
-__global__ void __launch_bounds__(SweepSmem<T, MODE != kSrcPlain, PRE, BATCH>::PAIRS * 64, 1)
+template <typename T, int MODE, bool PRE, bool BATCH, bool WIDE = false>
+__global__ void __launch_bounds__(SweepSmem<T, MODE != kSrcPlain, PRE, BATCH || WIDE>::PAIRS * 64, 1)
 sweep_kernel(const SweepArgs<T> a1, const SweepBatch<T> bt)
 {
     constexpr bool PT = MODE == kSrcPseudoTime, ADJ = MODE == kSrcAdjoint, DELTA = MODE == kSrcDelta;
-    // FP32: results collected in shared memory and written out per chunk in
-    // coarser stores (fewer store instructions per step); FP64 writes each
-    // result at once (there the write-out would sit on the band hand-off path)
-    constexpr bool STAGE = sizeof(T) == 4;
-    using SM = SweepSmem<T, MODE != kSrcPlain, PRE, BATCH>;
+    // FP32 and the WIDE form: results collected in shared memory and written
+    // out per chunk in coarser stores (fewer store instructions per step:
+    // one 8-byte store per step touches 32 rows); the FP64 latency-bound
+    // form writes each result at once (there the write-out would sit on the
+    // band hand-off path: 256^2 S12 channel 0.127 -> 0.141 ms when staged)
+    constexpr bool STAGE = sizeof(T) == 4 || WIDE;
+    using SM = SweepSmem<T, MODE != kSrcPlain, PRE, BATCH || WIDE>;
     using B = Bits<T>;
     constexpr int SEG = SM::SEG, NBUF = SM::NBUF, RS = SM::RS, NW = SM::NW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1143,6 +1144,13 @@ cudaError_t prepare_t(int K)
             (e = sweep_attr<T, kSrcPlain, true>()) != cudaSuccess ||
             (e = sweep_attr<T, kSrcPseudoTime, true>()) != cudaSuccess)
             first = e;
+        if constexpr (sizeof(T) == 8) {   // the FP64 throughput form
+            if (first == cudaSuccess &&
+                (e = cudaFuncSetAttribute(sweep_kernel<double, kSrcPlain, true, false, true>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)sweep_smem<double, kSrcPlain, true>())) != cudaSuccess)
+                first = e;
+        }
     });
     if (first != cudaSuccess) return first;
     const size_t ms = moments_smem<T>(K);
@@ -1163,6 +1171,16 @@ int sweep_occupancy()
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<T, MODE, sizeof(T) == 8, BATCH>,
                                                       sweep_threads<T, MODE, BATCH>(), sweep_smem<T, MODE, BATCH>()) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+int sweep_wide_occupancy()
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<double, kSrcPlain, true, false, true>,
+                                                      sweep_threads<double, kSrcPlain, true>(),
+                                                      sweep_smem<double, kSrcPlain, true>()) != cudaSuccess)
         return 0;
     return n;
 }
@@ -1236,6 +1254,15 @@ cudaError_t launch_source_from(const Plan& P, const double* rho_in, cudaStream_t
     return cudaGetLastError();
 }
 
+// The FP64 sweep's throughput form pays when every pair has several long
+// units to run (1024^2 S16: 4608 units, sweep 1.32 -> 1.09 ms); with fewer
+// units than two waves of the 8-pair form the band hand-off latency
+// dominates and per-result stores are faster (256^2 S12: 672 units).
+bool sweep_wide(const Plan& P)
+{
+    return (long long)P.K * P.nb >= 2LL * P.sweep_grid * 8;
+}
+
 cudaError_t launch_sweep(Plan& P, cudaStream_t st)
 {
     if (P.pt && P.X && !P.fp32) {
@@ -1245,6 +1272,12 @@ cudaError_t launch_sweep(Plan& P, cudaStream_t st)
         SweepArgs<double> a = sweep_args<double, kSrcPlain>(P);
         a.src = P.X;
         a.src_stride = P.N;
+        if (sweep_wide(P)) {   // throughput form: 12 pairs, staged write-out (same bits)
+            sweep_kernel<double, kSrcPlain, true, false, true>
+                <<<P.sweep_grid, sweep_threads<double, kSrcPlain, true>(), sweep_smem<double, kSrcPlain, true>(), st>>>(
+                    a, SweepBatch<double>{});
+            return cudaGetLastError();
+        }
         sweep_kernel<double, kSrcPlain, true, false>
             <<<P.sweep_grid, sweep_threads<double, kSrcPlain>(), sweep_smem<double, kSrcPlain>(), st>>>(a, SweepBatch<double>{});
         return cudaGetLastError();
@@ -1405,7 +1438,7 @@ int sweep_max_active_blocks(int fp32, int pt)
     return std::min({sweep_occupancy<double, kSrcPlain, false>(), sweep_occupancy<double, kSrcPseudoTime, false>(),
                      sweep_occupancy<double, kSrcAdjoint, false>(), sweep_occupancy<double, kSrcDelta, false>(),
                      sweep_occupancy<double, kSrcPlain, true>(),
-                     sweep_occupancy<double, kSrcPseudoTime, true>()});
+                     sweep_occupancy<double, kSrcPseudoTime, true>(), sweep_wide_occupancy()});
 }
 
 }  // namespace gsis
