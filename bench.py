@@ -163,7 +163,11 @@ def _clock_summary(proc, f, uuid, index):
 # while the sources that define the sweep launch (kernel, arguments, grid,
 # workspace layout) are the captured ones.
 SWEEP_SOURCES = ("sweep.cu", "gsis_internal.cuh", "host.h", "api.cu", "timedep.cu", "batch.cu")
-SWEEP_TRAFFIC = {}   # {workload: (sources digest, bytes per launch)}
+SWEEP_TRAFFIC = {   # {workload: (sources digest, bytes per launch)}
+    "timedep_fp64": ("071987afffbb36a4", 3_812_468_992),   # profiles/sweep_kernel_wide_td1024_fp64.md
+    "channel": ("071987afffbb36a4", 106_249_984),          # profiles/sweep_kernel_channel256.md
+    "batch": ("071987afffbb36a4", 932_471_552),            # profiles/sweep_kernel_batch64.md
+}
 
 
 def sweep_sources_digest() -> str:
@@ -918,6 +922,37 @@ def run_oracle_times(args):
     return 0
 
 
+PROFILE_CASES = {
+    # name: (mesh side, sweep precision); one backward-Euler step of the
+    # time-dependent channel workload from the cold start, two GSIS iterations
+    "td1024_fp64": (1024, "fp64"),
+    "td1024_fp32": (1024, "fp32"),
+    "td512_fp64": (512, "fp64"),
+}
+
+
+def run_profile_case(name):
+    """One small run of the headline workload for a profiler (ncu): the
+    first time step of the time-dependent channel problem on a side x side
+    mesh (S16, the channel scaled from the 256^2 mask), two GSIS iterations
+    at the benchmark's synthetic settings.  Nothing is timed."""
+    import torch
+
+    from paper_2507_03975_gb300 import gsis
+    side, prec = PROFILE_CASES[name]
+    torch.cuda.set_device(0)
+    p = W.config_timedep() if side == 1024 else W.channel_td_problem(side)
+    td = W.TIMEDEP
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    opt = td_options(gsis, precision=gsis.FP64 if prec == "fp64" else gsis.FP32_SWEEP, fixed_iters=2)
+    r = gsis.td_solve(p.dx, p.dy, p.mu, p.eta, p.w, t(p.sigma_a), t(p.sigma_s), t(p.q),
+                      t(np.full(p.N, td["a"] * td["c"] * td["T0"] ** 4)), t(np.full(p.N, td["T0"])), td["dt"], 1,
+                      c=td["c"], a=td["a"], cv=td["cv"], inflow=t(p.inflow.reshape(-1)), options=opt)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": name, "status": r["status"], "iters": r["step_iters"].tolist()}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -939,7 +974,11 @@ def main():
                     help="time the FP64 oracle itself on the host cores (CPU only) and exit")
     ap.add_argument("--oracle-td-steps", type=int, default=0,
                     help="with --oracle-times: time this many real oracle steps of the headline workload")
+    ap.add_argument("--profile-case", choices=sorted(PROFILE_CASES),
+                    help="run one small instance of the headline workload once (for ncu) and exit")
     args = ap.parse_args()
+    if args.profile_case:
+        return run_profile_case(args.profile_case)
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.oracle_times:
