@@ -256,11 +256,17 @@ def td_class_model(cls, prof, iters, upd, N, fp64_peak, hbm, fp64=True):
     microseconds stay in the total, so this slightly overstates the time).
     Algorithmic work (what the method must do, not what this implementation
     adds):
-      sweep:   2 FMA + 1 MUL per update (5 FLOP; FP64 binds: 5 FLOP at
-               1.25 TFLOP/s take 3x longer than its HBM bytes at peak);
-               bytes: read I^n once per update (8 B FP64, 4 B FP32) plus
-               64 B per cell (sigma_t, source in, six moments out);
-      moments: 3 FMA per update (rho, F_x, F_y);
+      sweep:   the upwind update I = (X + a I_W + b I_S) / d over the
+               time step's source X = S + I^n/(c dt): 2 FMA + 1 MUL per
+               update (5 FLOP; the FMA that forms X is the update class's;
+               FP64 binds: 5 FLOP at 1.25 TFLOP/s take 3x longer than the
+               HBM bytes at peak); bytes: read I^n once per update (8 B
+               FP64, 4 B FP32) plus 64 B per cell (sigma_t, source in, six
+               moments out);
+      moments: rho, F_x, F_y: over x-reflection pairs of one weight, 2 adds
+               + 3 FMA per two updates (4 FLOP per update; an add takes a
+               full FMA slot of the FP64 pipe, so the fraction is a lower
+               bound);
       synth:   36 B per cell from HBM per call (level coefficients, r0,
                guess, x) -- bound by barriers and latency;
       hot_rhs / update: 15 / 10 doubles per cell."""
@@ -275,7 +281,7 @@ def td_class_model(cls, prof, iters, upd, N, fp64_peak, hbm, fp64=True):
         if not fp64:
             work = hbm_bytes
     elif cls == "moments":
-        work, bound, peak, unit = 6.0 * upd, ("alu" if fp64 else "hbm"), (fp64_peak if fp64 else hbm), \
+        work, bound, peak, unit = 4.0 * upd, ("alu" if fp64 else "hbm"), (fp64_peak if fp64 else hbm), \
             ("GFLOP/s" if fp64 else "GB/s")
         if not fp64:
             work = ib * upd + 48.0 * N

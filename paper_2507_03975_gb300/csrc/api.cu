@@ -123,8 +123,8 @@ size_t layout(const Sizes& z, char* base, Plan* P)
     p.qmu = qbuf; p.qeta = qbuf ? qbuf + K : nullptr; p.qw = qbuf ? qbuf + 2 * K : nullptr;
     p.omu = qbuf ? qbuf + 3 * K : nullptr; p.oeta = qbuf ? qbuf + 4 * K : nullptr;
     p.ow = qbuf ? qbuf + 5 * K : nullptr;
-    int* ibuf = reinterpret_cast<int*>(take(2 * K * sizeof(int)));
-    p.perm = ibuf; p.sidx = ibuf ? ibuf + K : nullptr;
+    int* ibuf = reinterpret_cast<int*>(take(3 * K * sizeof(int)));
+    p.perm = ibuf; p.sidx = ibuf ? ibuf + K : nullptr; p.mpair = ibuf ? ibuf + 2 * K : nullptr;
     p.dx = reinterpret_cast<double*>(take(z.nx * sizeof(double)));
     p.dy = reinterpret_cast<double*>(take(z.ny * sizeof(double)));
     p.acoef = reinterpret_cast<double*>(take(K * z.nx * sizeof(double)));
@@ -329,7 +329,7 @@ int prepare(Plan& P, const gsis_mesh* mesh, const gsis_quadrature* quad, const g
                 if (kq == qd) perm.push_back(k);
             }
         std::vector<double> hq(6 * (size_t)K);
-        std::vector<int> hi(2 * (size_t)K);
+        std::vector<int> hi(3 * (size_t)K, -1);
         for (int s = 0; s < K; ++s) {
             hq[s] = quad->mu[perm[s]];
             hq[K + s] = quad->eta[perm[s]];
@@ -341,6 +341,26 @@ int prepare(Plan& P, const gsis_mesh* mesh, const gsis_quadrature* quad, const g
             hq[3 * K + k] = quad->mu[k];
             hq[4 * K + k] = quad->eta[k];
             hq[5 * K + k] = quad->w[k];
+        }
+        // x-reflection pairs (mu, eta) <-> (-mu, eta) with equal weights (every
+        // level-symmetric set): the moments then sum each pair once
+        P.has_mpair = K % 2 == 0;
+        {
+            int np = 0;
+            std::vector<char> used(K, 0);
+            for (int k = 0; k < K && P.has_mpair; ++k) {
+                if (used[k]) continue;
+                if (!(quad->mu[k] > 0.0)) { P.has_mpair = 0; break; }
+                int m = -1;
+                for (int t = 0; t < K; ++t)
+                    if (!used[t] && t != k && std::fabs(quad->mu[t] + quad->mu[k]) <= 1e-14 &&
+                        quad->eta[t] == quad->eta[k] && quad->w[t] == quad->w[k]) { m = t; break; }
+                if (m < 0) { P.has_mpair = 0; break; }
+                used[k] = used[m] = 1;
+                hi[2 * K + 2 * np] = k;
+                hi[2 * K + 2 * np + 1] = m;
+                ++np;
+            }
         }
         CK(cudaMemcpyAsync(const_cast<double*>(P.qmu), hq.data(), hq.size() * sizeof(double),
                            cudaMemcpyHostToDevice, st));

@@ -92,6 +92,8 @@ struct Plan {
     const double* omu; const double* oeta; const double* ow;   // original order
     const int* perm;                // s -> original k
     const int* sidx;                // original k -> s
+    const int* mpair;               // [K/2][2] original k of the x-reflection pairs (mu, eta), (-mu, eta), equal w
+    int has_mpair;                  // the quadrature has such pairs: moments take the paired sums
     // per-direction coefficients |mu_s|/dx_i [K][nx], |eta_s|/dy_j [K][ny]
     const double* acoef; const double* bcoef;
     const float* acoef_f; const float* bcoef_f;

@@ -222,6 +222,14 @@ __global__ void source_kernel(int N, const double* __restrict__ ss, const double
 // (Eqs. (RTE_d_increment), (delta_Iij), (RTE_d_mtx)): source = the residual
 // R[s][cell], zero increment on inflow faces, stored result I + corr + dI.
 constexpr int kSrcPlain = 0, kSrcPseudoTime = 1, kSrcAdjoint = 2, kSrcDelta = 3;
+// Windows per chunk buffer beyond the source (and the FP32 sigma_t): the
+// pseudo-time, adjoint and increment forms read two per-cell/per-ordinate
+// arrays more, the plain form none.  (A time-step form that read I^n and
+// the per-cell source, one window more, with 1/(c dt) as a constant, was
+// measured slower: 1024^2 S16 sweep 1.09 -> 1.92 ms against the 0.40 ms of
+// the per-ordinate source pass it saved; the sweep is bound by its copy
+// pipeline.)
+__host__ __device__ constexpr int sweep_xw(int mode) { return mode == kSrcPlain ? 0 : 2; }
 
 template <typename T>
 struct SweepArgs {
@@ -324,17 +332,17 @@ template <> struct Bits<float> {
 // updates in the chunk (padded rows: conflict-free column access), the
 // column coefficients of the SEG + 31 columns the skewed lanes touch, the
 // 1/d table rows of the chunk (FP64) and the SEG south values of lane 0.
-template <typename T, bool PT, bool PRE, bool WIDE = false>
+template <typename T, int XW, bool PRE, bool WIDE = false>
 struct SweepSmem {
     static constexpr int SEG = 64 / (int)sizeof(T);
     static constexpr int NBUF = 3;
     static constexpr int RS = SEG + 1;
     static constexpr int AW = SEG + 32;
-    static constexpr int NW = (PRE ? 1 : 2) + (PT ? 2 : 0);   // src, [sigt], [shift, I^m]
+    static constexpr int NW = (PRE ? 1 : 2) + XW;              // src, [sigt], [shift,] [I^m or I^n]
     static constexpr int W_SRC = 0;                           // window slots
     static constexpr int W_SIGT = 1;                          // FP32 only (no 1/d table)
-    static constexpr int W_SHIFT = PRE ? 1 : 2;               // pseudo-time only
-    static constexpr int W_IOLD = PRE ? 2 : 3;                // pseudo-time only
+    static constexpr int W_SHIFT = PRE ? 1 : 2;               // two extra windows only
+    static constexpr int W_IOLD = (PRE ? 1 : 2) + (XW >= 2 ? 1 : 0);   // extra windows only
     static constexpr int WIN = 32 * RS;
     static constexpr size_t r16(size_t b) { return (b + 15) / 16 * 16; }
     static constexpr size_t off_r = r16(sizeof(T) * (size_t)NW * WIN);
@@ -377,7 +385,7 @@ struct SweepSmem {
 // "empty".  Every wait is bounded; on time-out kErrTimeout is raised and the
 // warp leaves after its copies in flight have landed.
 template <typename T, int MODE, bool PRE, bool BATCH, bool WIDE = false>
-__global__ void __launch_bounds__(SweepSmem<T, MODE != kSrcPlain, PRE, BATCH || WIDE>::PAIRS * 64, 1)
+__global__ void __launch_bounds__(SweepSmem<T, sweep_xw(MODE), PRE, BATCH || WIDE>::PAIRS * 64, 1)
 sweep_kernel(const SweepArgs<T> a1, const SweepBatch<T> bt)
 {
     constexpr bool PT = MODE == kSrcPseudoTime, ADJ = MODE == kSrcAdjoint, DELTA = MODE == kSrcDelta;
@@ -387,7 +395,7 @@ sweep_kernel(const SweepArgs<T> a1, const SweepBatch<T> bt)
     // form writes each result at once (there the write-out would sit on the
     // band hand-off path: 256^2 S12 channel 0.127 -> 0.141 ms when staged)
     constexpr bool STAGE = sizeof(T) == 4 || WIDE;
-    using SM = SweepSmem<T, MODE != kSrcPlain, PRE, BATCH || WIDE>;
+    using SM = SweepSmem<T, sweep_xw(MODE), PRE, BATCH || WIDE>;
     using B = Bits<T>;
     constexpr int SEG = SM::SEG, NBUF = SM::NBUF, RS = SM::RS, NW = SM::NW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -732,7 +740,7 @@ sweep_kernel(const SweepArgs<T> a1, const SweepBatch<T> bt)
                             T rinv;
                             if (PRE) {
                                 if (PT) sv = fma(wb[SM::W_SHIFT * SM::WIN + tt], wb[SM::W_IOLD * SM::WIN + tt], sv);
-                                rinv = (T)rb[tt * 32];
+                                    rinv = (T)rb[tt * 32];
                             } else {
                                 T d = wb[SM::W_SIGT * SM::WIN + tt] + ai + bj;
                                 if (PT) {
@@ -803,6 +811,7 @@ struct MomArgs {
     double* Pxx; double* Pxy; double* Pyy;                  // may be null
     const double* rho_new;                                  // GSIS correction of P (or null)
     const int* done;
+    const int* pairs;   // [K/2][2] x-reflection pairs (original k, the first with mu > 0), or null
 };
 
 // Per cell, in original direction order k = 0..K-1:
@@ -814,6 +823,45 @@ __device__ __forceinline__ void moments_body(const MomArgs<T>& a, int bid, int n
     T* cf = reinterpret_cast<T*>(smem_raw);                     // [K][6]
     int* sk = reinterpret_cast<int*>(cf + 6 * a.K);             // [K]
     if (a.done && ld_volatile_int(a.done)) return;
+    if (!WITH_P && a.pairs) {
+        // Directions in x-reflection pairs k1 = (mu, eta), k2 = (-mu, eta)
+        // with one weight: rho += w (I1 + I2), F_x += w mu (I1 - I2),
+        // F_y += w eta (I1 + I2): five FP64 operations per pair instead of
+        // six (the FP64 pipe bounds this kernel).
+        const int np = a.K / 2;
+        T* cp = cf;                                             // [np][3]: w, w mu, w eta of k1
+        int* sp = reinterpret_cast<int*>(cf + 3 * np);          // [np][2]: sorted indices of k1, k2
+        for (int p = threadIdx.x; p < np; p += blockDim.x) {
+            const int k1 = a.pairs[2 * p], k2 = a.pairs[2 * p + 1];
+            const double w = a.w[k1];
+            cp[3 * p + 0] = (T)w;
+            cp[3 * p + 1] = (T)(w * a.mu[k1]);
+            cp[3 * p + 2] = (T)(w * a.eta[k1]);
+            sp[2 * p] = a.sidx[k1];
+            sp[2 * p + 1] = a.sidx[k2];
+        }
+        __syncthreads();
+        for (int c = bid * blockDim.x + threadIdx.x; c < a.N; c += nblk * blockDim.x) {
+            T r = T(0), fx = T(0), fy = T(0);
+#pragma unroll 4
+            for (int p = 0; p < np; ++p) {
+                const T v1 = a.I[(size_t)sp[2 * p] * a.N + c];
+                const T v2 = a.I[(size_t)sp[2 * p + 1] * a.N + c];
+                const T sum = v1 + v2;
+                r = fma(cp[3 * p + 0], sum, r);
+                if (WITH_F) {
+                    fx = fma(cp[3 * p + 1], v1 - v2, fx);
+                    fy = fma(cp[3 * p + 2], sum, fy);
+                }
+            }
+            if (a.rho) a.rho[c] = (double)r;
+            if (WITH_F) {
+                a.Fx[c] = (double)fx;
+                a.Fy[c] = (double)fy;
+            }
+        }
+        return;
+    }
     for (int k = threadIdx.x; k < a.K; k += blockDim.x) {
         const double w = a.w[k], m = a.mu[k], e = a.eta[k];
         cf[6 * k + 0] = (T)w;
@@ -964,7 +1012,7 @@ size_t sweep_smem();
 template <typename T, int MODE, bool BATCH = false>
 constexpr int sweep_threads()
 {
-    return SweepSmem<T, MODE != kSrcPlain, sizeof(T) == 8, BATCH>::PAIRS * 64;
+    return SweepSmem<T, sweep_xw(MODE), sizeof(T) == 8, BATCH>::PAIRS * 64;
 }
 
 template <typename T, int MODE>
@@ -1071,6 +1119,7 @@ cudaError_t launch_moments_t(const Plan& P, bool with_F, bool with_P, double* rh
     a.nx = P.nx; a.ny = P.ny; a.N = P.N; a.K = P.K;
     a.I = static_cast<const T*>(P.I);
     a.sidx = P.sidx;
+    a.pairs = P.has_mpair ? P.mpair : nullptr;
     a.mu = P.omu;
     a.eta = P.oeta;
     a.w = P.ow;
@@ -1105,7 +1154,7 @@ cudaError_t launch_moments_t(const Plan& P, bool with_F, bool with_P, double* rh
 template <typename T, int MODE, bool BATCH>
 size_t sweep_smem()
 {
-    return SweepSmem<T, MODE != kSrcPlain, sizeof(T) == 8, BATCH>::bytes;
+    return SweepSmem<T, sweep_xw(MODE), sizeof(T) == 8, BATCH>::bytes;
 }
 
 
@@ -1175,12 +1224,13 @@ int sweep_occupancy()
     return n;
 }
 
-int sweep_wide_occupancy()
+template <int MODE, bool WIDE>
+int sweep_fp64_occupancy()
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<double, kSrcPlain, true, false, true>,
-                                                      sweep_threads<double, kSrcPlain, true>(),
-                                                      sweep_smem<double, kSrcPlain, true>()) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<double, MODE, true, false, WIDE>,
+                                                      sweep_threads<double, MODE, WIDE>(),
+                                                      sweep_smem<double, MODE, WIDE>()) != cudaSuccess)
         return 0;
     return n;
 }
@@ -1385,6 +1435,7 @@ int mom_batch_rec_t(const Plan& P, bool with_F, void* out)
     r.m.nx = P.nx; r.m.ny = P.ny; r.m.N = P.N; r.m.K = P.K;
     r.m.I = static_cast<const T*>(P.I);
     r.m.sidx = P.sidx;
+    r.m.pairs = P.has_mpair ? P.mpair : nullptr;
     r.m.mu = P.omu; r.m.eta = P.oeta; r.m.w = P.ow;
     r.m.rho = P.rho_h;
     r.m.Fx = with_F ? P.Fx : nullptr;
@@ -1438,7 +1489,7 @@ int sweep_max_active_blocks(int fp32, int pt)
     return std::min({sweep_occupancy<double, kSrcPlain, false>(), sweep_occupancy<double, kSrcPseudoTime, false>(),
                      sweep_occupancy<double, kSrcAdjoint, false>(), sweep_occupancy<double, kSrcDelta, false>(),
                      sweep_occupancy<double, kSrcPlain, true>(),
-                     sweep_occupancy<double, kSrcPseudoTime, true>(), sweep_wide_occupancy()});
+                     sweep_occupancy<double, kSrcPseudoTime, true>(), sweep_fp64_occupancy<kSrcPlain, true>()});
 }
 
 }  // namespace gsis
