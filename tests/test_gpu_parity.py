@@ -81,6 +81,34 @@ def test_transport_sweep_parity(gs, name, make, prec):
         assert np.abs(r["bflux"].cpu().numpy() - o["fb"]).max() / scale < 1e-4
 
 
+def _rotated(p, angle):
+    """The same problem with its ordinates rotated about the z axis: a valid
+    quadrature (weights and moments kept) without (mu, eta) -> (-mu, eta)
+    pairs, so the moments take their plain per-direction sums."""
+    import dataclasses
+    c, s_ = math.cos(angle), math.sin(angle)
+    mu = c * p.mu - s_ * p.eta
+    eta = s_ * p.mu + c * p.eta
+    return dataclasses.replace(p, mu=mu, eta=eta, inflow=None)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_sweep_parity_without_reflection_pairs(gs, prec):
+    p = _rotated(W.random_problem(70, 45, order=6, seed=18), 0.1)
+    rng = np.random.Generator(np.random.PCG64(19))
+    rho_in = rng.uniform(0.0, 3.0, p.N)
+    o = oracle.transport_sweep(p, rho_in)
+    r = gs.transport_sweep(p.dx, p.dy, p.mu, p.eta, p.w, _t(p.sigma_a), _t(p.sigma_s), _t(p.q), _t(rho_in), None,
+                           gs.default_options(precision=gs.FP64 if prec == "fp64" else gs.FP32_SWEEP))
+    tol = TOL64 if prec == "fp64" else TOL32
+    assert rel(r["rho"].cpu().numpy(), o["rho"]) < tol
+    N = p.N
+    F = r["F"].cpu().numpy()
+    scale = np.abs(o["rho"]).max()
+    assert np.abs(F[:N] - o["Fx"]).max() / scale < (TOL64 if prec == "fp64" else 1e-4)
+    assert np.abs(F[N:] - o["Fy"]).max() / scale < (TOL64 if prec == "fp64" else 1e-4)
+
+
 def test_sweep_is_deterministic(gs):
     p = W.random_problem(70, 45, order=6, seed=1)
     rho_in = np.linspace(0, 1, p.N)
@@ -91,9 +119,11 @@ def test_sweep_is_deterministic(gs):
     assert bool((a["rho"] == b["rho"]).all()) and bool((a["F"] == b["F"]).all())
 
 
-# (320, 300): no strip plan fits a cluster's shared memory, so the
-# global-memory solver runs over a cooperative grid of every SM
-@pytest.mark.parametrize("seed,shape", [(11, (40, 37)), (12, (9, 70)), (13, (1, 5)), (14, (320, 300))])
+# (320, 300) and larger: no strip plan fits a cluster's shared memory, so
+# the tiled solver runs over a cooperative grid of every SM; (513, 290) and
+# (257, 600) have odd level sizes, ragged rectangles and sub-tiles
+@pytest.mark.parametrize("seed,shape", [(11, (40, 37)), (12, (9, 70)), (13, (1, 5)), (14, (320, 300)),
+                                        (15, (513, 290)), (16, (257, 600))])
 def test_synthetic_step_parity(gs, seed, shape):
     p = W.random_problem(shape[0], shape[1], order=6, seed=seed)
     rng = np.random.Generator(np.random.PCG64(seed))
