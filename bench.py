@@ -168,10 +168,6 @@ SWEEP_TRAFFIC = {   # {workload: (sources digest, bytes per launch)}
     "channel": ("693ef3047a7c1233", 106_245_888),          # profiles/sweep_kernel_channel256.md
     "batch": ("693ef3047a7c1233", 932_333_312),            # profiles/sweep_kernel_batch64.md
 }
-    "timedep_fp64": ("071987afffbb36a4", 3_812_468_992),   # profiles/sweep_kernel_wide_td1024_fp64.md
-    "channel": ("071987afffbb36a4", 106_249_984),          # profiles/sweep_kernel_channel256.md
-    "batch": ("071987afffbb36a4", 932_471_552),            # profiles/sweep_kernel_batch64.md
-}
 
 
 def sweep_sources_digest() -> str:
