@@ -113,7 +113,7 @@ struct MgArgs {
     Status* status;
     // grid-wide form: reduction slots [3][2][gridDim] and the barrier words
     double* gslots_d; float* gslots_f;
-    unsigned* gbar;                 // [0] arrivals, [1] generation
+    unsigned* gbar;                 // [0]: the grid barrier word (top bit flips per barrier)
     long long wait_cycles;
 };
 
@@ -245,36 +245,38 @@ class ClusterCtx {
 };
 
 // The same interface over a whole cooperative grid (one CTA per SM): the
-// fine levels spread over every SM.  The barrier is a counter and a
-// generation word in global memory; every wait is bounded, and after a
-// time-out (the status's timeout bit) later barriers return at once so that
-// every CTA finishes.  Sums: each CTA's partial in a rotating global table,
-// then every warp adds the table in a fixed order (same bits everywhere).
+// fine levels spread over every SM.  The barrier is one word in global
+// memory whose top bit flips once per completed barrier: CTA 0 adds
+// 2^31 - (G - 1), every other CTA adds 1, so the bit changes with the last
+// arrival whatever the order and the low bits return to zero.  Each CTA
+// reads the bit once at the start (no barrier of this launch can complete
+// before its own first arrival) and afterwards knows the value to wait for,
+// so an arrival is a release reduction without a reply and the wait polls
+// with acquire loads.  Every wait is bounded; after a time-out (the status's
+// timeout bit) later barriers return at once so that every CTA finishes,
+// and the word is valid again after the next status reset.  Sums: each
+// CTA's partial in a rotating global table, then every warp adds the table
+// in a fixed order (same bits everywhere).
 class GridCtx {
   public:
-    __device__ GridCtx(const MgArgs& a) : a_(a) {}
+    __device__ GridCtx(const MgArgs& a) : a_(a)
+    {
+        if (threadIdx.x == 0) phase_ = ld_acquire_u32(a_.gbar) & kFlip;
+    }
     __device__ void sync()
     {
         __syncthreads();
         if (threadIdx.x == 0 && !ld_volatile_int(&a_.status->error)) {
-            volatile unsigned* gen = a_.gbar + 1;
-            const unsigned g = *gen;
-            __threadfence();
-            if (atomicAdd(a_.gbar, 1u) == gridDim.x - 1) {
-                a_.gbar[0] = 0u;
-                __threadfence();
-                atomicAdd(a_.gbar + 1, 1u);
-            } else {
-                const long long t0 = clock64();
-                while (*gen == g) {
-                    if (clock64() - t0 > a_.wait_cycles) {
-                        atomicOr(&a_.status->error, kErrTimeout);
-                        break;
-                    }
-                    __nanosleep(32);
+            const unsigned inc = blockIdx.x == 0 ? kFlip - (gridDim.x - 1u) : 1u;
+            asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(a_.gbar), "r"(inc) : "memory");
+            phase_ ^= kFlip;
+            const long long t0 = clock64();
+            while ((ld_acquire_u32(a_.gbar) & kFlip) != phase_) {
+                if (clock64() - t0 > a_.wait_cycles) {
+                    atomicOr(&a_.status->error, kErrTimeout);
+                    break;
                 }
             }
-            __threadfence();
         }
         __syncthreads();
     }
@@ -294,12 +296,8 @@ class GridCtx {
             tab[2 * blockIdx.x + 1] = b;
         }
         sync();
-        const int lane = threadIdx.x & 31;
         float s0 = 0.f, s1 = 0.f;
-        for (int r = lane; r < (int)gridDim.x; r += 32) {
-            s0 += __ldcg(tab + 2 * r);
-            s1 += __ldcg(tab + 2 * r + 1);
-        }
+        table_sum(tab, s0, s1);
         for (int o = 16; o > 0; o >>= 1) {
             s0 += __shfl_xor_sync(kFull, s0, o);
             s1 += __shfl_xor_sync(kFull, s1, o);
@@ -318,12 +316,8 @@ class GridCtx {
             tab[2 * blockIdx.x + 1] = b;
         }
         sync();
-        const int lane = threadIdx.x & 31;
         double s0 = 0.0, s1 = 0.0;
-        for (int r = lane; r < (int)gridDim.x; r += 32) {
-            s0 += __ldcg(tab + 2 * r);
-            s1 += __ldcg(tab + 2 * r + 1);
-        }
+        table_sum(tab, s0, s1);
         for (int o = 16; o > 0; o >>= 1) {
             s0 += __shfl_xor_sync(kFull, s0, o);
             s1 += __shfl_xor_sync(kFull, s1, o);
@@ -334,6 +328,37 @@ class GridCtx {
     }
 
   private:
+    static constexpr unsigned kFlip = 0x80000000u;
+    __device__ static unsigned ld_acquire_u32(const unsigned* p)
+    {
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+        return v;
+    }
+    // Lane l adds the table's pairs l, l + 32, l + 64, ... in that order;
+    // each group of eight is loaded before any is added, so the L2 reads
+    // overlap instead of one round trip per pair.
+    template <typename T>
+    __device__ void table_sum(const T* tab, T& s0, T& s1)
+    {
+        constexpr int kG = 8;
+        const int lane = threadIdx.x & 31, n = gridDim.x;
+        for (int r0 = 0; r0 < n; r0 += 32 * kG) {
+            T v0[kG], v1[kG];
+#pragma unroll
+            for (int g = 0; g < kG; ++g) {
+                const int r = r0 + lane + 32 * g;
+                v0[g] = r < n ? __ldcg(tab + 2 * r) : T(0);
+                v1[g] = r < n ? __ldcg(tab + 2 * r + 1) : T(0);
+            }
+#pragma unroll
+            for (int g = 0; g < kG; ++g)
+                if (r0 + lane + 32 * g < n) {
+                    s0 += v0[g];
+                    s1 += v1[g];
+                }
+        }
+    }
     __device__ float blockf(float v)
     {
         __shared__ float w[32];
@@ -359,6 +384,7 @@ class GridCtx {
         return t;
     }
     const MgArgs& a_;
+    unsigned phase_ = 0;   // thread 0: the barrier word's top bit after the last completed barrier
 };
 
 __device__ __forceinline__ float apply_S(const MgLevelDev& L, const float* v, int c)
@@ -924,15 +950,35 @@ __device__ __forceinline__ void tile_load(TileView& v, float* base, int cells, c
 // S[l0].r, output S[l0].x.  The same cycle as vcycle_local (x2 from r in one
 // pass, the residual, the 2x2 restriction; coarsest x = r / d; x2 + alpha P
 // x_coarse and two Jacobi steps), with 1/d precomputed and no division in a
-// loop; levels of at most 64 cells run in warp 0 alone.
+// loop; levels of at most 64 cells run in warp 0 alone.  A level is a set
+// of float offsets into the dynamic shared memory, passed by value: held in
+// registers, its arrays are addressed as shared memory and no store inside a
+// loop can make the compiler reload them.
 struct LocalLevel {
     int nx, ny;
-    float *d, *cx, *cy, *id, *x, *t, *r;
+    int d, cx, cy, id, x, t, r;
+};
+
+// One array of a LocalLevel in the dynamic shared memory.
+struct LocalArr {
+    int off;
+    __device__ float& operator[](int c) const
+    {
+        extern __shared__ __align__(16) float mg_smem[];
+        return mg_smem[off + c];
+    }
+};
+struct LocalView {
+    int nx, ny;
+    LocalArr d, cx, cy, id, x, t, r;
+    __device__ explicit LocalView(const LocalLevel& L)
+        : nx(L.nx), ny(L.ny), d{L.d}, cx{L.cx}, cy{L.cy}, id{L.id}, x{L.x}, t{L.t}, r{L.r} {}
 };
 
 template <bool WARP>
-__device__ __forceinline__ void local_down(const LocalLevel& L, const LocalLevel& C, float om)
+__device__ __forceinline__ void local_down(const LocalLevel Ls, const LocalLevel Cs, float om)
 {
+    const LocalView L(Ls), C(Cs);
     const int tid = WARP ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
     const int nt = WARP ? 32 : (int)blockDim.x;
     auto sync = [] { if (WARP) __syncwarp(); else __syncthreads(); };
@@ -980,8 +1026,9 @@ __device__ __forceinline__ void local_down(const LocalLevel& L, const LocalLevel
 }
 
 template <bool WARP>
-__device__ __forceinline__ void local_up(const LocalLevel& L, const LocalLevel& C, float om, float alpha)
+__device__ __forceinline__ void local_up(const LocalLevel Ls, const LocalLevel Cs, float om, float alpha)
 {
+    const LocalView L(Ls), C(Cs);
     const int tid = WARP ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
     const int nt = WARP ? 32 : (int)blockDim.x;
     auto sync = [] { if (WARP) __syncwarp(); else __syncthreads(); };
@@ -1019,7 +1066,7 @@ __device__ void vcycle_local_fast(const LocalLevel* S, int l0, int nl, float om,
     for (int l = l0; l < wl; ++l) local_down<false>(S[l], S[l + 1], om);
     if (threadIdx.x < 32) {
         for (int l = wl; l < nl - 1; ++l) local_down<true>(S[l], S[l + 1], om);
-        const LocalLevel& B = S[nl - 1];
+        const LocalView B(S[nl - 1]);
         for (int c = threadIdx.x; c < B.nx * B.ny; c += 32) B.x[c] = B.r[c] * B.id[c];
         __syncwarp();
         for (int l = nl - 2; l >= wl; --l) local_up<true>(S[l], S[l + 1], om, alpha);
@@ -1047,7 +1094,7 @@ __global__ void __launch_bounds__(kTileBlock) mg_tile_grid_kernel(const TileArgs
             size_t off = 0;
             for (int l = lf; l < nl; ++l) {
                 const int n = a.lv[l].nx * a.lv[l].ny;
-                float* p = mg_smem + off;
+                const int p = (int)off;
                 S[l] = LocalLevel{a.lv[l].nx, a.lv[l].ny, p, p + n, p + 2 * n, p + 3 * n, p + 4 * n, p + 5 * n,
                                   p + 6 * n};
                 off += ((size_t)kLocalArrays * n + 3) & ~(size_t)3;
@@ -1056,12 +1103,13 @@ __global__ void __launch_bounds__(kTileBlock) mg_tile_grid_kernel(const TileArgs
         __syncthreads();
         for (int l = lf; l < nl; ++l) {
             const int n = a.lv[l].nx * a.lv[l].ny;
+            const LocalView V(S[l]);
             for (int c = tid; c < n; c += nt) {
                 const float d = a.lv[l].d[c];
-                S[l].d[c] = d;
-                S[l].id[c] = 1.f / d;
-                S[l].cx[c] = a.lv[l].cx[c];
-                S[l].cy[c] = a.lv[l].cy[c];
+                V.d[c] = d;
+                V.id[c] = 1.f / d;
+                V.cx[c] = a.lv[l].cx[c];
+                V.cy[c] = a.lv[l].cy[c];
             }
         }
         __syncthreads();
@@ -1192,17 +1240,32 @@ __global__ void __launch_bounds__(kTileBlock) mg_tile_grid_kernel(const TileArgs
         }
         if (b == 0) {   // restriction of level lf-1's residual, then the coarse V-cycle
             const MgLevelDev& F = a.lv[lf - 1];
-            const LocalLevel& Lc = S[lf];
+            const LocalView Lc(S[lf]);
             const int n = Lc.nx * Lc.ny;
-            for (int cc = tid; cc < n; cc += nt) {
-                const int J = cc / Lc.nx, I = cc - J * Lc.nx;
-                float sum = 0.f;
+            constexpr int kU = 2;   // coarse cells per thread whose 8 loads are in flight together
+            for (int c0 = 0; c0 < n; c0 += kU * nt) {
+                float v[kU][4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int gi = 2 * I + (q & 1), gj = 2 * J + (q >> 1);
-                    if (gi < F.nx && gj < F.ny) sum += __ldcg(F.t + gj * F.nx + gi);
+                for (int u = 0; u < kU; ++u) {
+                    const int cc = c0 + tid + u * nt;
+                    const int J = cc / Lc.nx, I = cc - J * Lc.nx;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int gi = 2 * I + (q & 1), gj = 2 * J + (q >> 1);
+                        v[u][q] = cc < n && gi < F.nx && gj < F.ny ? __ldcg(F.t + gj * F.nx + gi) : 0.f;
+                    }
                 }
-                Lc.r[cc] = sum;
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int cc = c0 + tid + u * nt;
+                    if (cc >= n) break;
+                    const int J = cc / Lc.nx, I = cc - J * Lc.nx;
+                    float sum = 0.f;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (2 * I + (q & 1) < F.nx && 2 * J + (q >> 1) < F.ny) sum += v[u][q];
+                    Lc.r[cc] = sum;
+                }
             }
             __syncthreads();
             vcycle_local_fast(S, lf, nl, om, alpha);

@@ -105,3 +105,27 @@ def test_time_dependent_steps_stall_at_fp32_floor_and_run_goes_on(gs):
     assert _rel(r["rho"].cpu().numpy(), o["rho"]) < 1e-5
     assert _rel(r["T"].cpu().numpy(), o["T"]) < 1e-5
     _context_still_works(gs)
+
+
+def test_grid_barrier_timeout_reports_and_next_call_recovers(gs):
+    """The synthetic solve over the whole grid (a 513 x 290 mesh: more cells
+    than one cluster holds) with its barrier waits bounded at 1 ns: CTAs that
+    arrive before the last one give up, the call reports
+    GSIS_ERR_DEVICE_TIMEOUT, and the next call (whose status reset clears the
+    barrier word) gives the oracle's answer."""
+    p = W.random_problem(513, 290, order=4, seed=71)
+    rng = np.random.Generator(np.random.PCG64(71))
+    rho_m = rng.uniform(0.0, 2.0, p.N)
+    sw = oracle.transport_sweep(p, rho_m)
+    gx, gy = oracle.alsm_gradient(p, sw["rho"])
+    hx, hy = oracle.high_order_terms(p, sw["Fx"], sw["Fy"], gx, gy)
+    b = oracle.synthetic_rhs(p, sw["rho"], hx, hy, sw["fb"])
+    rho_new = oracle.SyntheticSolver(p).solve(b)
+    F = np.concatenate([sw["Fx"], sw["Fy"]])
+    args = (p.dx, p.dy, _t(p.sigma_a), _t(p.sigma_s), _t(p.q), _t(sw["rho"]), _t(F), _t(sw["fb"]), None)
+    with pytest.raises(gs.GsisError) as ei:
+        gs.synthetic_step(*args, gs.default_options(synth_rtol=1e-14, synth_max_iter=3000, wait_limit_s=1e-9))
+    assert ei.value.status == gs.GSIS_ERR_DEVICE_TIMEOUT
+    for _ in range(2):
+        r = gs.synthetic_step(*args, gs.default_options(synth_rtol=1e-14, synth_max_iter=3000))
+        assert _rel(r["rho"].cpu().numpy(), rho_new) < 1e-10
