@@ -175,6 +175,10 @@ size_t layout(const Sizes& z, char* base, Plan* P)
             ly = (ly + 1) / 2;
         }
         g.nl = l;
+        g.direct = -1;
+        for (int k = 1; k < l; ++k)
+            if ((size_t)g.nx[k] * g.ny[k] <= (size_t)kDirectMax) { g.direct = k; break; }
+        g.cinv = reinterpret_cast<float*>(take((size_t)kDirectMax * kDirectMax * sizeof(float)));
         g.local_from = l - 1;
         for (int k = 0; k < l; ++k)
             if ((size_t)g.nx[k] * g.ny[k] <= 4 * (size_t)kMgBlock) { g.local_from = k; break; }
@@ -374,7 +378,7 @@ int prepare(Plan& P, const gsis_mesh* mesh, const gsis_quadrature* quad, const g
     }
     TIMED(GSIS_KCLASS_SETUP, P.fp32 ? 1 : 2, launch_cell_setup(P, opt->cfl_p, opt->beta, st));
     if (P.scheme == GSIS_SCHEME_GSIS || P.K == 0) {
-        TIMED(GSIS_KCLASS_SETUP, P.mg.nl, launch_mg_setup(P, st));
+        TIMED(GSIS_KCLASS_SETUP, mg_setup_launches(P), launch_mg_setup(P, st));
         CK(plan_synthetic(P));
     }
     return GSIS_OK;

@@ -18,6 +18,7 @@ constexpr size_t kSweepSmemCap = 231424; // dynamic shared memory a sweep CTA ma
 constexpr int kRedBlock = 256;          // threads per reduction / stencil block
 constexpr int kMaxCgBlocks = 1024;      // partials capacity of the fixed-order grid reductions
 constexpr int kMaxLevels = 24;          // multigrid levels (2x2 aggregation down to one cell)
+constexpr int kDirectMax = 64;          // cells of the multigrid level solved directly (grid solver)
 constexpr int kMgBlock = 1024;          // threads per CTA of the synthetic-solve cluster
 
 // device error bits (Status::error)
@@ -46,7 +47,7 @@ struct Status {
     long long synth_iters_total;      // summed over the solve
     double err;                       // last Err(rho)
     double synth_relres;              // last synthetic relative residual
-    unsigned int mg_bar[2];           // grid-wide synthetic solver barrier: arrivals, generation
+    unsigned int mg_bar[2];           // grid-wide synthetic solver barrier word ([0]; [1] unused)
 };
 
 // Multigrid hierarchy of the synthetic operator (level 0 = the mesh).
@@ -57,6 +58,8 @@ struct MgPlan {
     float* d[kMaxLevels]; float* cx[kMaxLevels]; float* cy[kMaxLevels];
     float* x[kMaxLevels]; float* t[kMaxLevels]; float* r[kMaxLevels];
     float* r0; float* dl; float* s; float* p; float* q;
+    int direct;      // first level of at most kDirectMax cells (-1: none)
+    float* cinv;     // its operator's inverse, row-major, FP32 (kDirectMax^2 floats)
 };
 
 // Everything a kernel needs, carved from the caller's workspace (device
@@ -170,6 +173,7 @@ cudaError_t launch_source_from(const Plan& P, const double* rho_in, cudaStream_t
 cudaError_t launch_hot_rhs(const Plan& P, const double* rho_h, const double* Fx, const double* Fy,
                            const double* fb, const double* guess, cudaStream_t st, bool fuse = false);
 cudaError_t launch_mg_setup(const Plan& P, cudaStream_t st);
+int mg_setup_launches(const Plan& P);   // kernels launch_mg_setup launches
 cudaError_t plan_synthetic(Plan& P);   // before the first solve launch (no runtime calls in the launch)
 cudaError_t launch_synthetic_solve(const Plan& P, const double* guess, double* out, cudaStream_t st);
 int mg_cluster_size();

@@ -92,6 +92,59 @@ __global__ void mg_coarsen_kernel(int nx, int ny, const double* __restrict__ d, 
     }
 }
 
+// Inverse of one coarse level's operator A (n = nx ny <= kDirectMax cells;
+// A = diag d, -cx between horizontal neighbours, -cy between vertical ones:
+// symmetric positive definite) by Gauss-Jordan elimination in place,
+// without pivoting (every pivot of an SPD matrix is positive), in FP32 like
+// the V-cycle it serves; stored as (A^-1 + A^-T) / 2, so the stored matrix
+// is exactly symmetric.  One CTA of 512 threads: thread (i0, j) holds the
+// elements (i0 + 8 m, j), m = 0..7; per pivot one barrier after the reads
+// of the pivot row and column, one after the update.  Once per operator.
+constexpr int kInvThreads = 512;
+__global__ void __launch_bounds__(kInvThreads) mg_direct_inverse_kernel(int nx, int ny, const double* __restrict__ d,
+                                                                        const double* __restrict__ cx,
+                                                                        const double* __restrict__ cy, float* inv)
+{
+    __shared__ float A[kDirectMax][kDirectMax];
+    const int n = nx * ny, j = threadIdx.x & (kDirectMax - 1), i0 = threadIdx.x / kDirectMax;
+    constexpr int kRows = kDirectMax / (kInvThreads / kDirectMax);
+    for (int m = 0; m < kRows; ++m) {
+        const int r = i0 + 8 * m;
+        if (r >= n || j >= n) continue;
+        const int ir = r % nx, jr = r / nx;
+        double v = 0.0;
+        if (j == r) v = d[r];
+        else if (j == r + 1 && ir + 1 < nx) v = -cx[r];
+        else if (j == r - 1 && ir > 0) v = -cx[j];
+        else if (j == r + nx && jr + 1 < ny) v = -cy[r];
+        else if (j == r - nx && jr > 0) v = -cy[j];
+        A[r][j] = (float)v;
+    }
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        const float p = 1.f / A[k][k];
+        float aik[kRows];
+#pragma unroll
+        for (int m = 0; m < kRows; ++m) aik[m] = i0 + 8 * m < n ? A[i0 + 8 * m][k] : 0.f;
+        const float rkj = j == k ? p : (j < n ? A[k][j] * p : 0.f);
+        __syncthreads();
+        if (j < n) {
+#pragma unroll
+            for (int m = 0; m < kRows; ++m) {
+                const int r = i0 + 8 * m;
+                if (r >= n) continue;
+                if (r == k) A[r][j] = rkj;
+                else A[r][j] = j == k ? -aik[m] * p : __fmaf_rn(-aik[m], rkj, A[r][j]);
+            }
+        }
+        __syncthreads();
+    }
+    for (int m = 0; m < kRows; ++m) {
+        const int r = i0 + 8 * m;
+        if (r < n && j < n) inv[r * n + j] = 0.5f * (A[r][j] + A[j][r]);
+    }
+}
+
 // ------------------------------------------------------------ solve
 struct MgLevelDev {
     int nx, ny;
@@ -115,6 +168,8 @@ struct MgArgs {
     double* gslots_d; float* gslots_f;
     unsigned* gbar;                 // [0]: the grid barrier word (top bit flips per barrier)
     long long wait_cycles;
+    const float* cinv;              // inverse of level `direct`'s operator (tiled form)
+    int direct;
 };
 
 // Work distribution of one level: the whole cluster, or CTA 0 alone.
@@ -946,11 +1001,12 @@ __device__ __forceinline__ void tile_load(TileView& v, float* base, int cells, c
     __syncthreads();
 }
 
-// V-cycle over the coarse levels [l0, nl) in CTA 0's shared memory: input
-// S[l0].r, output S[l0].x.  The same cycle as vcycle_local (x2 from r in one
-// pass, the residual, the 2x2 restriction; coarsest x = r / d; x2 + alpha P
-// x_coarse and two Jacobi steps), with 1/d precomputed and no division in a
-// loop; levels of at most 64 cells run in warp 0 alone.  A level is a set
+// The coarse levels in CTA 0's shared memory (tiled grid solver): the same
+// smoothing and transfers as vcycle_local (x2 from r in one pass, the
+// residual, the 2x2 restriction; x2 + alpha P x_coarse and two Jacobi steps),
+// with 1/d precomputed and no division in a loop, but the first level of at
+// most kDirectMax cells is solved exactly with its precomputed inverse
+// instead of being cycled on down to one cell.  A level is a set
 // of float offsets into the dynamic shared memory, passed by value: held in
 // registers, its arrays are addressed as shared memory and no store inside a
 // loop can make the compiler reload them.
@@ -975,13 +1031,11 @@ struct LocalView {
         : nx(L.nx), ny(L.ny), d{L.d}, cx{L.cx}, cy{L.cy}, id{L.id}, x{L.x}, t{L.t}, r{L.r} {}
 };
 
-template <bool WARP>
 __device__ __forceinline__ void local_down(const LocalLevel Ls, const LocalLevel Cs, float om)
 {
     const LocalView L(Ls), C(Cs);
-    const int tid = WARP ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
-    const int nt = WARP ? 32 : (int)blockDim.x;
-    auto sync = [] { if (WARP) __syncwarp(); else __syncthreads(); };
+    const int tid = threadIdx.x, nt = blockDim.x;
+    auto sync = [] { __syncthreads(); };
     const int nx = L.nx, ny = L.ny, n = nx * ny;
     auto x1 = [&](int c) { return om * L.r[c] * L.id[c]; };
     int i = tid % nx, j = tid / nx;
@@ -1025,13 +1079,11 @@ __device__ __forceinline__ void local_down(const LocalLevel Ls, const LocalLevel
     sync();
 }
 
-template <bool WARP>
 __device__ __forceinline__ void local_up(const LocalLevel Ls, const LocalLevel Cs, float om, float alpha)
 {
     const LocalView L(Ls), C(Cs);
-    const int tid = WARP ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
-    const int nt = WARP ? 32 : (int)blockDim.x;
-    auto sync = [] { if (WARP) __syncwarp(); else __syncthreads(); };
+    const int tid = threadIdx.x, nt = blockDim.x;
+    auto sync = [] { __syncthreads(); };
     const int nx = L.nx, ny = L.ny, n = nx * ny, cnx = C.nx;
     auto y0 = [&](int c, int i, int j) { return L.x[c] + alpha * C.x[(j >> 1) * cnx + (i >> 1)]; };
     int i = tid % nx, j = tid / nx;
@@ -1059,20 +1111,41 @@ __device__ __forceinline__ void local_up(const LocalLevel Ls, const LocalLevel C
     sync();
 }
 
-__device__ void vcycle_local_fast(const LocalLevel* S, int l0, int nl, float om, float alpha)
+// x = A^-1 r on the direct level (n <= kDirectMax cells) from its inverse
+// at float offset cinv (row-major n x n): warp w forms rows 4w..4w+3, lane l
+// the products of columns l and l + 32, then a butterfly sum.
+__device__ __forceinline__ void local_direct(const LocalLevel Bs, int cinv)
 {
-    int wl = l0;   // first level of at most 64 cells
-    while (wl < nl - 1 && S[wl].nx * S[wl].ny > 64) ++wl;
-    for (int l = l0; l < wl; ++l) local_down<false>(S[l], S[l + 1], om);
-    if (threadIdx.x < 32) {
-        for (int l = wl; l < nl - 1; ++l) local_down<true>(S[l], S[l + 1], om);
-        const LocalView B(S[nl - 1]);
-        for (int c = threadIdx.x; c < B.nx * B.ny; c += 32) B.x[c] = B.r[c] * B.id[c];
-        __syncwarp();
-        for (int l = nl - 2; l >= wl; --l) local_up<true>(S[l], S[l + 1], om, alpha);
+    extern __shared__ __align__(16) float mg_smem[];
+    const LocalView B(Bs);
+    const int n = B.nx * B.ny, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const float r0 = lane < n ? B.r[lane] : 0.f, r1 = lane + 32 < n ? B.r[lane + 32] : 0.f;
+    for (int c0 = 4 * (int)(threadIdx.x >> 5); c0 < n; c0 += 4 * nw) {
+        float acc[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int row = cinv + min(c0 + u, n - 1) * n;
+            float v = lane < n ? mg_smem[row + lane] * r0 : 0.f;
+            if (lane + 32 < n) v = __fmaf_rn(mg_smem[row + lane + 32], r1, v);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+            acc[u] = v;
+        }
+        if (lane == 0)
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (c0 + u < n) B.x[c0 + u] = acc[u];
     }
     __syncthreads();
-    for (int l = wl - 1; l >= l0; --l) local_up<false>(S[l], S[l + 1], om, alpha);
+}
+
+// V-cycle over the coarse levels [l0, ld] in CTA 0's shared memory: input
+// S[l0].r, output S[l0].x; level ld is solved exactly.
+__device__ void vcycle_local_direct(const LocalLevel* S, int l0, int ld, int cinv, float om, float alpha)
+{
+    for (int l = l0; l < ld; ++l) local_down(S[l], S[l + 1], om);
+    local_direct(S[ld], cinv);
+    for (int l = ld - 1; l >= l0; --l) local_up(S[l], S[l + 1], om, alpha);
 }
 
 __global__ void __launch_bounds__(kTileBlock) mg_tile_grid_kernel(const TileArgs ta)
@@ -1084,24 +1157,29 @@ __global__ void __launch_bounds__(kTileBlock) mg_tile_grid_kernel(const TileArgs
     __shared__ LocalLevel S[kMaxLevels];
     extern __shared__ __align__(16) float mg_smem[];
     if (ld_volatile_int(&a.status->done)) return;   // same value in every CTA (set by an earlier kernel)
-    const int nl = a.nl, lf = a.local_from;
+    const int lf = a.local_from;
     const float om = a.omega, alpha = a.alpha;
     const int b = blockIdx.x;                         // 0: coarse levels; 1..px*py: rectangles
     const bool worker = b >= 1 && b <= ta.px * ta.py;
     const int tid = threadIdx.x, nt = blockDim.x;
-    if (b == 0) {   // the coarse levels in shared memory, with 1/d
+    const int ld = a.direct;   // levels lf..ld in CTA 0, ld solved with its inverse
+    int cinv = 0;              // float offset of the inverse, after the levels
+    for (int l = lf; l <= ld; ++l) cinv += (kLocalArrays * a.lv[l].nx * a.lv[l].ny + 3) & ~3;
+    if (b == 0) {   // the coarse levels in shared memory, with 1/d, and the inverse
         if (tid == 0) {
-            size_t off = 0;
-            for (int l = lf; l < nl; ++l) {
+            int off = 0;
+            for (int l = lf; l <= ld; ++l) {
                 const int n = a.lv[l].nx * a.lv[l].ny;
-                const int p = (int)off;
+                const int p = off;
                 S[l] = LocalLevel{a.lv[l].nx, a.lv[l].ny, p, p + n, p + 2 * n, p + 3 * n, p + 4 * n, p + 5 * n,
                                   p + 6 * n};
-                off += ((size_t)kLocalArrays * n + 3) & ~(size_t)3;
+                off += (kLocalArrays * n + 3) & ~3;
             }
         }
+        const int nd = a.lv[ld].nx * a.lv[ld].ny;
+        for (int e = tid; e < nd * nd; e += nt) mg_smem[cinv + e] = a.cinv[e];
         __syncthreads();
-        for (int l = lf; l < nl; ++l) {
+        for (int l = lf; l <= ld; ++l) {
             const int n = a.lv[l].nx * a.lv[l].ny;
             const LocalView V(S[l]);
             for (int c = tid; c < n; c += nt) {
@@ -1268,7 +1346,7 @@ __global__ void __launch_bounds__(kTileBlock) mg_tile_grid_kernel(const TileArgs
                 }
             }
             __syncthreads();
-            vcycle_local_fast(S, lf, nl, om, alpha);
+            vcycle_local_direct(S, lf, ld, cinv, om, alpha);
             for (int c = tid; c < n; c += nt) a.lv[lf].t[c] = Lc.x[c];
         }
         cx.sync();
@@ -1996,7 +2074,20 @@ cudaError_t launch_mg_setup(const Plan& P, cudaStream_t st)
             P.mg.d64[l + 1], P.mg.cx64[l + 1], P.mg.cy64[l + 1], P.mg.d[l + 1], P.mg.cx[l + 1], P.mg.cy[l + 1]);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
+    if (mg_setup_launches(P) > P.mg.nl) {
+        const int l = P.mg.direct;
+        mg_direct_inverse_kernel<<<1, kInvThreads, 0, st>>>(P.mg.nx[l], P.mg.ny[l], P.mg.d64[l], P.mg.cx64[l],
+                                                    P.mg.cy64[l], P.mg.cinv);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     return cudaSuccess;
+}
+
+// Kernels launch_mg_setup launches: the fine copy, one coarsening per level,
+// and for meshes the grid solver may take the direct level's inverse.
+int mg_setup_launches(const Plan& P)
+{
+    return P.mg.nl + (P.mg.direct >= 1 && (long long)P.N > kGridMinCells ? 1 : 0);
 }
 
 namespace {
@@ -2136,12 +2227,15 @@ size_t tile_smem_cap()
 // rectangle would not fit.
 bool tile_plan(const Plan& P, int G, TileArgs& t, size_t& smem)
 {
-    const int lf = P.mg.local_from;
+    const int lf = P.mg.local_from, ld = P.mg.direct;
     const size_t cap = tile_smem_cap();
-    size_t local_bytes = 0;   // CTA 0's coarse levels (kLocalArrays arrays each, 16-byte aligned)
-    for (int l = lf; l < P.mg.nl; ++l)
+    if (lf < 2 || ld < lf || G < 2) return false;
+    // CTA 0's coarse levels lf..ld (kLocalArrays arrays each, 16-byte
+    // aligned) and the inverse of level ld's operator
+    size_t local_bytes = (size_t)P.mg.nx[ld] * P.mg.ny[ld] * P.mg.nx[ld] * P.mg.ny[ld] * sizeof(float);
+    for (int l = lf; l <= ld; ++l)
         local_bytes += (((size_t)kLocalArrays * P.mg.nx[l] * P.mg.ny[l] + 3) & ~(size_t)3) * sizeof(float);
-    if (lf < 2 || G < 2 || cap < local_bytes) return false;
+    if (cap < local_bytes) return false;
     const int A = 1 << (lf - 1);
     const int gx = (P.nx + A - 1) / A, gy = (P.ny + A - 1) / A;
     long best = -1;
@@ -2209,6 +2303,8 @@ MgArgs fallback_args(const Plan& P, const double* guess, double* out, size_t& sm
     a.gslots_f = P.mg_gslots_f;
     a.gbar = P.status->mg_bar;
     a.wait_cycles = P.wait_cycles;
+    a.cinv = P.mg.cinv;
+    a.direct = P.mg.direct;
     int off = 0;
     for (int l = P.mg.local_from; l < P.mg.nl; ++l) {
         a.loff[l] = off;

@@ -293,7 +293,7 @@ int run_step(Plan& P, const gsis_time_params* tp, const gsis_options* opt, int g
     CK(cudaMemsetAsync(P.status, 0, sizeof(Status), st));
     TIMED(GSIS_KCLASS_SETUP, 1, launch_td_begin(a, g, st));
     if (gsis)   // multigrid hierarchy of the step's operator (coupling at T^n): 1 + nl kernels
-        TIMED(GSIS_KCLASS_SETUP, 1 + P.mg.nl, launch_td_step_operator(P, a, g, st));
+        TIMED(GSIS_KCLASS_SETUP, 1 + mg_setup_launches(P), launch_td_step_operator(P, a, g, st));
     TIMED(GSIS_KCLASS_SETUP, 1, launch_td_source(a, g, st));
     if (P.X || P.X_f) TIMED(GSIS_KCLASS_SETUP, 1, launch_ordinate_source(P, st));
     if (stalled) *stalled = false;
