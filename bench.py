@@ -164,9 +164,9 @@ def _clock_summary(proc, f, uuid, index):
 # workspace layout) are the captured ones.
 SWEEP_SOURCES = ("sweep.cu", "gsis_internal.cuh", "host.h", "api.cu", "timedep.cu", "batch.cu")
 SWEEP_TRAFFIC = {   # {workload: (sources digest, bytes per launch)}
-    "timedep_fp64": ("693ef3047a7c1233", 3_812_327_808),   # profiles/sweep_kernel_wide_td1024_fp64.md
-    "channel": ("693ef3047a7c1233", 106_245_888),          # profiles/sweep_kernel_channel256.md
-    "batch": ("693ef3047a7c1233", 932_333_312),            # profiles/sweep_kernel_batch64.md
+    "timedep_fp64": ("fa9b129bd3031441", 3_813_159_296),   # profiles/sweep_kernel_wide_td1024_fp64.md
+    "channel": ("fa9b129bd3031441", 106_320_384),          # profiles/sweep_kernel_channel256.md
+    "batch": ("fa9b129bd3031441", 932_085_504),            # profiles/sweep_kernel_batch64.md
 }
 
 

@@ -48,3 +48,14 @@ def test_clock_samples_are_matched_by_uuid():
     c = bench.parse_clock_samples(rows, index=0)
     assert c["samples"] == 2 and c["reasons"] == ["hw_slowdown"] and c["matched_by"] == "index"
     assert bench.parse_clock_samples(rows, uuid="cccc") is None
+
+
+def test_sweep_traffic_table_is_one_capture():
+    """bench.py imports, and its table of captured sweep traffic holds one
+    entry per workload, all from one capture of one set of sources."""
+    import bench
+    t = bench.SWEEP_TRAFFIC
+    assert set(t) == {"timedep_fp64", "channel", "batch"}
+    assert len({d for d, _ in t.values()}) == 1
+    assert all(isinstance(b, int) and b > 0 for _, b in t.values())
+    assert len(bench.sweep_sources_digest()) == 16
