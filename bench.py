@@ -53,6 +53,10 @@ BETA = 10.0        # local pseudo-time control (Sec. 4.3) the steady 2000/0.2 op
 SYNTH_CAP = 2      # inner iterations of the synthetic solve per GSIS iteration, steady channel (Sec. 4.2)
 TD_SYNTH_CAP = 5   # the same cap on the time-dependent workload (measured: 4 -> 864, 5 -> 680, 6 -> 705 GSIS iterations)
 TD_CHECK_EVERY = 4
+# first iterate of every time step: quadratic extrapolation in time of the last
+# three steps' (rho, T) (gsis_time_params::predictor; 0 would start from the
+# previous step, as the paper's loop does)
+TD_PREDICTOR = 2
 FP32_STALL = (2, 5)   # check_every, stall_window: an FP32 step ends after 10 iterations without a new minimum
 
 
@@ -221,12 +225,12 @@ class TdWorkload:
         self.sa, self.ss, self.q, self.inflow, self.T0, self.rho0 = (t(a) for a in self.host)
         self.upd = p.N * p.K
 
-    def run(self, gsis, opt, nsteps=None, workspace=None, stream=None, inputs=None):
+    def run(self, gsis, opt, nsteps=None, workspace=None, stream=None, inputs=None, predictor=TD_PREDICTOR):
         p, tp = self.p, self.tp
         sa, ss, q, inflow, T0, rho0 = inputs or (self.sa, self.ss, self.q, self.inflow, self.T0, self.rho0)
         return gsis.td_solve(p.dx, p.dy, p.mu, p.eta, p.w, sa, ss, q, rho0, T0, tp["dt"],
                              nsteps or tp["nsteps"], c=tp["c"], a=tp["a"], cv=tp["cv"], inflow=inflow,
-                             options=opt, workspace=workspace, stream=stream)
+                             options=opt, workspace=workspace, stream=stream, predictor=predictor)
 
 
 def td_options(gsis, scheme=None, precision=None, tol=TOL, **kw):
@@ -242,6 +246,9 @@ def _td_config(p, tp):
                 scheme="gsis", precision="fp64", tol=TOL, tol_applies_to="Err(rho) of every time step",
                 synthetic=f"rho-T system with T eliminated (Newton about T^m); FP64 iterative refinement, FP32 "
                           f"multigrid-CG inner iterations capped at {TD_SYNTH_CAP} per GSIS iteration",
+                predictor="each step starts from the quadratic extrapolation in time of the last three steps' "
+                          "(rho, T) (linear at step 1, the previous step at step 0); every step still iterates "
+                          "to the tolerance" if TD_PREDICTOR == 2 else f"order {TD_PREDICTOR}",
                 l2="inputs larger than L2 (two FP64 K x N intensity arrays of 1.2 GB per time step); L2 also "
                    "flushed (512 MiB write) before every run",
                 step="one complete 100-time-step gsis_td_solve call from the cold start",
@@ -349,7 +356,8 @@ def td_adjoint_measure(gsis, torch, stream, wl, nsteps=None):
         e1.synchronize()
         return r, e0.elapsed_time(e1) * 1e-3
 
-    f, s_fwd = timed(lambda: wl.run(gsis, opt, nsteps=n, stream=stream))
+    # the forward run the adjoint differentiates (and recomputes): steps started from the previous one
+    f, s_fwd = timed(lambda: wl.run(gsis, opt, nsteps=n, stream=stream, predictor=0))
     adj = lambda ws=None: gsis.td_adjoint(p.dx, p.dy, p.mu, p.eta, p.w, wl.sa, wl.ss, wl.q, wl.rho0, wl.T0,
                                           tp["dt"], n, dJ_drho=g, c=tp["c"], a=tp["a"], cv=tp["cv"],
                                           inflow=wl.inflow, options=opt, workspace=ws, stream=stream)

@@ -256,10 +256,19 @@ typedef struct {
     double a;       /* radiation constant, > 0 */
     double cv;      /* volumetric heat capacity C_v, > 0 */
     int nsteps;     /* backward-Euler steps, >= 1 */
+    /* First iterate of each step's iteration: 0 = the previous step's result
+     * (rho^n, T^n), as the paper's time loop starts it; 1 = linear, 2 =
+     * quadratic extrapolation in time from the last two or three steps'
+     * results (fewer steps so far: the highest order they allow), each value
+     * kept >= half the previous step's (rho >= 0, T > 0).  Only the starting
+     * point changes: every step still iterates to Err < tol, so the result
+     * is the same implicit solution within the tolerance, in fewer
+     * iterations on smooth transients.  gsis_td_adjoint takes 0 only. */
+    int predictor;
 } gsis_time_params;
 
 /* Bytes of device workspace for gsis_td_solve (the gsis_solve layout plus the
- * previous step's intensities and seven per-cell arrays). */
+ * previous step's intensities and eleven per-cell arrays). */
 int gsis_td_workspace_bytes(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis_options* opt,
                             size_t* bytes);
 

@@ -150,6 +150,8 @@ struct Plan {
         double* cnext;                  // the correction of the current iterate (becomes cn)
         double* qeff;                   // volume source of the synthetic equation
         double* diag0;                  // synthetic diagonal without the time and coupling terms
+        double* hr1; double* hr2;       // rho of the previous two steps (predictor history)
+        double* ht1; double* ht2;       // T of the previous two steps
     } td;
 };
 

@@ -46,6 +46,8 @@ struct TdArgs {
     double* T; double* T_n; double* rho_n;
     double* cn; double* cnext;
     double* qeff; double* diag; const double* diag0;
+    double* hr1; double* hr2; double* ht1; double* ht2;   // predictor history (null: none kept)
+    int pred;                                             // this step's extrapolation order
     double* src; float* src_f;
     double inv_cdt, ac, cv_dt;    // 1/(c dt), a c, C_v / dt
     int gsis;
@@ -119,6 +121,23 @@ __global__ void td_begin_kernel(TdArgs a)
         a.T_n[c] = t;
         a.cn[c] = a.cnext[c];
         a.cnext[c] = 0.0;
+        if (a.hr1) {   // first iterate extrapolated from the last steps' results
+            const double r1 = a.hr1[c], t1 = a.ht1[c];
+            double rp = r, tq = t;
+            if (a.pred == 1) {
+                rp = r + (r - r1);
+                tq = t + (t - t1);
+            } else if (a.pred == 2) {
+                rp = fma(3.0, r - r1, a.hr2[c]);
+                tq = fma(3.0, t - t1, a.ht2[c]);
+            }
+            a.rho_m[c] = fmax(rp, 0.5 * r);
+            a.T[c] = fmax(tq, 0.5 * t);
+            a.hr2[c] = r1;
+            a.ht2[c] = t1;
+            a.hr1[c] = r;
+            a.ht1[c] = t;
+        }
     }
 }
 
@@ -271,6 +290,7 @@ int check_tp(const gsis_time_params* tp, const gsis_options* opt)
     for (double v : {tp->dt, tp->c, tp->a, tp->cv})
         if (!(v > 0.0) || !std::isfinite(v)) return fail(GSIS_ERR_ARG, "dt, c, a and cv must be finite and > 0");
     if (tp->nsteps < 1 || tp->nsteps > 100000000) return fail(GSIS_ERR_ARG, "nsteps out of range");
+    if (tp->predictor < 0 || tp->predictor > 2) return fail(GSIS_ERR_ARG, "predictor must be 0, 1 or 2");
     if (opt->cfl_p > 0.0 || opt->beta > 0.0)
         return fail(GSIS_ERR_ARG, "the time-dependent solve takes no pseudo-time (cfl_p, beta <= 0)");
     if (opt->spatial_order != 1) return fail(GSIS_ERR_ARG, "the time-dependent solve runs first-order upwind face values");
@@ -282,14 +302,20 @@ int check_tp(const gsis_time_params* tp, const gsis_options* opt)
 // (I = I^{m+1/2}, rho_h, rho_m, T, cnext) and its status in S.  With
 // opt->stall_window > 0 (and no fixed iteration count) the step also ends
 // when Err has not reached a new minimum for that many checks; *stalled
-// says so (the FP32 kinetic step has a floor of Err near 1e-8).
+// says so (the FP32 kinetic step has a floor of Err near 1e-8).  pred >= 0
+// keeps the last steps' results and starts the step from their
+// extrapolation of order pred (gsis_time_params::predictor); -1 keeps none.
 int run_step(Plan& P, const gsis_time_params* tp, const gsis_options* opt, int gsis, Status& S, cudaStream_t st,
-             bool* stalled = nullptr)
+             bool* stalled = nullptr, int pred = -1)
 {
     int rc;
     const int g = grid_for(P.N, kRedBlock, P.num_sms * 8);
     const int nmax = opt->fixed_iters > 0 ? opt->fixed_iters : opt->max_iter;
-    const TdArgs a = td_args(P, tp, gsis);
+    TdArgs a = td_args(P, tp, gsis);
+    if (pred >= 0) {   // keep the predictor's history; extrapolate with order pred
+        a.hr1 = P.td.hr1; a.hr2 = P.td.hr2; a.ht1 = P.td.ht1; a.ht2 = P.td.ht2;
+        a.pred = pred;
+    }
     CK(cudaMemsetAsync(P.status, 0, sizeof(Status), st));
     TIMED(GSIS_KCLASS_SETUP, 1, launch_td_begin(a, g, st));
     if (gsis)   // multigrid hierarchy of the step's operator (coupling at T^n): 1 + nl kernels
@@ -427,6 +453,8 @@ int check_td_adjoint(const gsis_mesh* mesh, const gsis_quadrature* quad, const g
     if ((rc = check_mesh(mesh)) || (rc = check_quad(quad)) || (rc = check_opt(opt)) || (rc = check_tp(tp, opt)))
         return rc;
     if (opt->scheme != GSIS_SCHEME_GSIS) return fail(GSIS_ERR_ARG, "the adjoint is that of the GSIS time steps");
+    if (tp->predictor != 0)
+        return fail(GSIS_ERR_ARG, "the adjoint's recomputed steps start from the previous step: predictor 0");
     if (checkpoint_every < 1) return fail(GSIS_ERR_ARG, "checkpoint_every must be >= 1");
     if (!uniform_spacing(mesh->dx, mesh->nx) || !uniform_spacing(mesh->dy, mesh->ny))
         return fail(GSIS_ERR_ARG, "the adjoint needs a uniform mesh (transposed sweep = reflected sweep)");
@@ -487,7 +515,8 @@ int gsis_td_solve(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis
     for (int n = 0; n < tp->nsteps; ++n) {
         if (n > 0) std::swap(P.I, P.In);   // I^n = the last sweep's intensities (+ cn)
         bool stalled = false;
-        if ((rc = run_step(P, tp, opt, gsis, S, st, &stalled))) return rc;
+        const int pred = tp->predictor > 0 ? std::min(tp->predictor, n) : -1;
+        if ((rc = run_step(P, tp, opt, gsis, S, st, &stalled, pred))) return rc;
         if (step_iters) step_iters[n] = S.iter;
         if (step_err) step_err[n] = S.err;
         if (stalled) {   // the step ends at its floor of Err; the run goes on

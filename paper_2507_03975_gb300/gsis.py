@@ -504,7 +504,7 @@ def batch_autotune(problems, options: Options | None = None, trial_iters: int = 
 # ------------------------------------------------------------ time-dependent
 class TimeParams(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("c", ctypes.c_double), ("a", ctypes.c_double),
-                ("cv", ctypes.c_double), ("nsteps", ctypes.c_int)]
+                ("cv", ctypes.c_double), ("nsteps", ctypes.c_int), ("predictor", ctypes.c_int)]
 
 
 def _td_load():
@@ -531,8 +531,10 @@ def td_workspace_bytes(dx, dy, mu, eta, w, options: Options | None = None) -> in
 
 
 def td_solve(dx, dy, mu, eta, w, sigma_a, sigma_s, q, rho0, T0, dt, nsteps, c=1.0, a=1.0, cv=1.0,
-             inflow=None, options: Options | None = None, workspace=None, stream=None):
-    """gsis_td_solve: returns dict(rho, T, F, step_iters, step_err, status, workspace)."""
+             inflow=None, options: Options | None = None, workspace=None, stream=None, predictor=0):
+    """gsis_td_solve: returns dict(rho, T, F, step_iters, step_err, status, workspace).
+    predictor: first iterate of each step (0 previous step, 1 linear, 2
+    quadratic extrapolation in time; gsis_time_params)."""
     import torch
     args = _Args(dx, dy, mu, eta, w)
     o = options or default_options()
@@ -543,7 +545,7 @@ def td_solve(dx, dy, mu, eta, w, sigma_a, sigma_s, q, rho0, T0, dt, nsteps, c=1.
     F = torch.empty(2 * N, dtype=torch.float64, device=dev)
     its = (ctypes.c_int * nsteps)()
     errs = np.zeros(nsteps)
-    tp = TimeParams(dt, c, a, cv, nsteps)
+    tp = TimeParams(dt, c, a, cv, nsteps, predictor)
     workspace = _workspace(td_workspace_bytes(args.dx, args.dy, args.mu, args.eta, args.w, o), workspace, dev)
     rc = _td_load().gsis_td_solve(
         ctypes.byref(args.mesh), ctypes.byref(args.quad), ctypes.byref(o), ctypes.byref(tp),

@@ -154,6 +154,25 @@ def test_td_adjoint_binding_rejects_before_device_use(gs):
     rc = lib.gsis_td_adjoint(ctypes.byref(a.mesh), ctypes.byref(a.quad), ctypes.byref(gs.default_options()),
                              ctypes.byref(tp), 2, *([dummy] * 14), its, None, ctypes.c_size_t(0), None)
     assert rc == gs.GSIS_ERR_WORKSPACE
+    tp.predictor = 2   # the adjoint recomputes steps from the previous step only
+    rc = lib.gsis_td_adjoint(ctypes.byref(a.mesh), ctypes.byref(a.quad), ctypes.byref(gs.default_options()),
+                             ctypes.byref(tp), 2, *([dummy] * 14), its, None, ctypes.c_size_t(0), None)
+    assert rc == gs.GSIS_ERR_ARG and "predictor" in gs.last_error()
+
+
+def test_td_solve_rejects_predictor_out_of_range(gs):
+    """gsis_time_params::predictor is 0, 1 or 2; anything else is
+    GSIS_ERR_ARG before any device pointer is touched."""
+    mu, eta, w = gs.quadrature_level_symmetric(4)
+    a = gs._Args(np.full(8, 0.125), np.full(8, 0.125), mu, eta, w)
+    dummy = ctypes.c_void_p(0x1000)   # never dereferenced
+    its = (ctypes.c_int * 3)()
+    lib = gs._td_load()
+    for bad in (-1, 3):
+        tp = gs.TimeParams(0.1, 1.0, 1.0, 1.0, 3, bad)
+        rc = lib.gsis_td_solve(ctypes.byref(a.mesh), ctypes.byref(a.quad), ctypes.byref(gs.default_options()),
+                               ctypes.byref(tp), *([dummy] * 9), its, None, None, ctypes.c_size_t(0), None)
+        assert rc == gs.GSIS_ERR_ARG and "predictor" in gs.last_error()
 
 
 def test_mesh_size_limits(gs):

@@ -39,11 +39,12 @@ def rel(a, b):
     return np.abs(a - b).max() / np.abs(b).max()
 
 
-def _solve(gs, p, tp, nsteps, rho0, T0, **kw):
+def _solve(gs, p, tp, nsteps, rho0, T0, predictor=0, **kw):
     opt = gs.default_options(**kw)
     return gs.td_solve(p.dx, p.dy, p.mu, p.eta, p.w, _t(p.sigma_a), _t(p.sigma_s), _t(p.q), _t(rho0), _t(T0),
                        tp.dt, nsteps, c=tp.c, a=tp.a, cv=tp.cv,
-                       inflow=None if p.inflow is None else _t(p.inflow.reshape(-1)), options=opt)
+                       inflow=None if p.inflow is None else _t(p.inflow.reshape(-1)), options=opt,
+                       predictor=predictor)
 
 
 def _case(seed, nx=20, ny=16, order=4):
@@ -74,6 +75,30 @@ def test_converged_steps_match_oracle(gs, name, make, tp, scheme):
     assert rel(r["rho"].cpu().numpy(), o["rho"]) < 1e-9
     assert rel(r["T"].cpu().numpy(), o["T"]) < 1e-9
     assert np.abs(r["step_iters"] - o["iters"]).max() <= 1
+
+
+@pytest.mark.parametrize("scheme", ["gsis", "si"])
+def test_predictor_reaches_the_same_steps_in_fewer_iterations(gs, scheme):
+    """Steps started from a linear or quadratic extrapolation of the last
+    steps' (rho, T) converge to the oracle's implicit solution (which starts
+    every step from the previous one) and take no more iterations in all
+    than starting from the previous step."""
+    p = W.channel_td_problem(64, 4, base=64, width=2, sigma_bulk=200.0)
+    rho0, T0 = np.full(p.N, 1e-4), np.full(p.N, 0.1)
+    tp = TD.TimeParams(dt=1e-3 * 16)
+    nsteps = 8
+    o = TD.run(p, tp, nsteps, rho0, T0, scheme=scheme, tol=1e-13)
+    kw = dict(scheme=gs.SCHEME_GSIS if scheme == "gsis" else gs.SCHEME_SI, tol=1e-13, max_iter=5000,
+              synth_rtol=1e-14, synth_max_iter=3000, check_every=8)
+    total = {}
+    for pred in (0, 1, 2):
+        r = _solve(gs, p, tp, nsteps, rho0, T0, predictor=pred, **kw)
+        assert r["status"] == gs.GSIS_OK
+        assert rel(r["rho"].cpu().numpy(), o["rho"]) < 1e-9, pred
+        assert rel(r["T"].cpu().numpy(), o["T"]) < 1e-9, pred
+        total[pred] = int(r["step_iters"].sum())
+    assert abs(total[0] - int(o["iters"].sum())) <= nsteps
+    assert total[1] <= total[0] and total[2] <= total[0], total
 
 
 def test_fixed_inner_iterations_match_oracle(gs):
