@@ -51,7 +51,7 @@ UNIT = "cell-direction updates/s"
 TOL = 1e-8
 BETA = 10.0        # local pseudo-time control (Sec. 4.3) the steady 2000/0.2 opacity jump needs
 SYNTH_CAP = 2      # inner iterations of the synthetic solve per GSIS iteration, steady channel (Sec. 4.2)
-TD_SYNTH_CAP = 5   # the same cap on the time-dependent workload (measured: 4 -> 864, 5 -> 680, 6 -> 705 GSIS iterations)
+TD_SYNTH_CAP = 6   # the cap on the time-dependent workload, with the quadratic predictor (measured: 4 -> 776, 5 -> 598, 6 -> 560, 7 -> 549, 8 -> 547 GSIS iterations; 1.84, 1.78, 1.79, 1.84 s at 5-8)
 TD_CHECK_EVERY = 4
 # first iterate of every time step: quadratic extrapolation in time of the last
 # three steps' (rho, T) (gsis_time_params::predictor; 0 would start from the
@@ -168,9 +168,9 @@ def _clock_summary(proc, f, uuid, index):
 # workspace layout) are the captured ones.
 SWEEP_SOURCES = ("sweep.cu", "gsis_internal.cuh", "host.h", "api.cu", "timedep.cu", "batch.cu")
 SWEEP_TRAFFIC = {   # {workload: (sources digest, bytes per launch)}
-    "timedep_fp64": ("fa9b129bd3031441", 3_813_159_296),   # profiles/sweep_kernel_wide_td1024_fp64.md
-    "channel": ("fa9b129bd3031441", 106_320_384),          # profiles/sweep_kernel_channel256.md
-    "batch": ("fa9b129bd3031441", 932_085_504),            # profiles/sweep_kernel_batch64.md
+    "timedep_fp64": ("9a5f0fb8e8902c3b", 3_814_152_704),   # profiles/sweep_kernel_wide_td1024_fp64.md
+    "channel": ("9a5f0fb8e8902c3b", 106_591_232),          # profiles/sweep_kernel_channel256.md
+    "batch": ("9a5f0fb8e8902c3b", 932_065_536),            # profiles/sweep_kernel_batch64.md
 }
 
 
