@@ -268,7 +268,7 @@ typedef struct {
 } gsis_time_params;
 
 /* Bytes of device workspace for gsis_td_solve (the gsis_solve layout plus the
- * previous step's intensities and eleven per-cell arrays). */
+ * previous step's intensities and fourteen per-cell arrays). */
 int gsis_td_workspace_bytes(const gsis_mesh* mesh, const gsis_quadrature* quad, const gsis_options* opt,
                             size_t* bytes);
 

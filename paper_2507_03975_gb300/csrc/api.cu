@@ -218,7 +218,8 @@ size_t layout(const Sizes& z, char* base, Plan* P)
     if (z.td) {
         p.In = take(K * N * Ts);
         double** td[] = {&p.td.rho_n, &p.td.T_n, &p.td.T,   &p.td.cn,  &p.td.cnext, &p.td.qeff,
-                         &p.td.diag0, &p.td.hr1, &p.td.hr2, &p.td.ht1, &p.td.ht2};
+                         &p.td.diag0, &p.td.hr1, &p.td.hr2, &p.td.ht1, &p.td.ht2, &p.td.ckap,
+                         &p.td.cphi,  &p.td.cf};
         for (double** d : td) *d = reinterpret_cast<double*>(take(N * sizeof(double)));
     }
     return off;

@@ -152,6 +152,7 @@ struct Plan {
         double* diag0;                  // synthetic diagonal without the time and coupling terms
         double* hr1; double* hr2;       // rho of the previous two steps (predictor history)
         double* ht1; double* ht2;       // T of the previous two steps
+        double* ckap; double* cphi; double* cf;   // kappa, phi, f at T^m (coefficient -> material update)
     } td;
 };
 

@@ -47,9 +47,10 @@ struct TdArgs {
     double* cn; double* cnext;
     double* qeff; double* diag; const double* diag0;
     double* hr1; double* hr2; double* ht1; double* ht2;   // predictor history (null: none kept)
+    double* ckap; double* cphi; double* cf;               // GSIS: kappa, phi, f of td_coef_kernel at T^m
     int pred;                                             // this step's extrapolation order
     double* src; float* src_f;
-    double inv_cdt, ac, cv_dt;    // 1/(c dt), a c, C_v / dt
+    double inv_cdt, ac, cv_dt, dt_cv;   // 1/(c dt), a c, C_v / dt, dt / C_v
     int gsis;
     double* partials; double* hist; Status* status;
     double tol; int fixed_iters, max_iter;
@@ -161,6 +162,10 @@ __global__ void td_coef_kernel(TdArgs a)
         const double phi = a.ac * pow4(t);
         a.qeff[c] = fma(a.rho_n[c], a.inv_cdt, fma(f * sa, fma(kap, a.T_n[c] - t, phi), a.q[c]));
         a.diag[c] = fma(V, a.inv_cdt + fma(f, sa, -sa), a.diag0[c]);
+        // the material update of this iteration linearises about the same T^m
+        a.ckap[c] = kap;
+        a.cphi[c] = phi;
+        a.cf[c] = f;
     }
 }
 
@@ -180,11 +185,11 @@ __global__ void __launch_bounds__(kRedBlock) td_update_kernel(TdArgs a)
         if (a.gsis) {
             nw = a.x[c];
             const double sa = a.sigma_a[c];
-            const double kap = 4.0 * a.ac * t * t * t;
-            const double D2 = fma(kap, sa, a.cv_dt);
-            const double phi = a.ac * pow4(t);
+            // kappa, phi and 1/(C_v/dt + kappa sigma_a) = f dt/C_v at T^m, as
+            // td_coef_kernel formed them in this iteration (no FP64 division here)
+            const double kap = a.ckap[c], phi = a.cphi[c];
             const double tn = a.T_n[c];
-            t = tn + sa * fma(kap, t - tn, nw - phi) / D2;
+            t = tn + sa * fma(kap, t - tn, nw - phi) * (a.cf[c] * a.dt_cv);
             a.T[c] = t;
             a.cnext[c] = (nw - a.rho_h[c]) * kInvFourPi;
         } else {
@@ -268,6 +273,8 @@ TdArgs td_args(const Plan& P, const gsis_time_params* tp, int gsis)
     a.inv_cdt = 1.0 / (tp->c * tp->dt);
     a.ac = tp->a * tp->c;
     a.cv_dt = tp->cv / tp->dt;
+    a.dt_cv = tp->dt / tp->cv;
+    a.ckap = P.td.ckap; a.cphi = P.td.cphi; a.cf = P.td.cf;
     a.gsis = gsis;
     a.partials = P.partials + (size_t)9 * kMaxCgBlocks;
     a.hist = P.hist;
