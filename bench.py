@@ -324,7 +324,8 @@ def td_fp32_measure(gsis, torch, stream, wl, ref64, ws=None):
     e1.synchronize()
     s = e0.elapsed_time(e1) * 1e-3
     its, err = r["step_iters"], r["step_err"]
-    return {"precision": "fp32 sweeps (fp32 intensities), fp64 moments / synthetic / material / Err",
+    return {"precision": "fp32 sweeps and moment accumulation (fp32 intensities and accumulators), fp64 HoT / "
+                              "synthetic solve / material update / Err",
             "tol": TOL, "stall": f"a step ends after {ce * sw} iterations without a new minimum of Err",
             "s": s, "status": r["status"], "iters_total": int(its.sum()),
             "iters_per_step_mean": float(its.mean()), "updates_per_s": float(its.sum()) * wl.upd / s,
