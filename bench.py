@@ -357,11 +357,12 @@ def td_adjoint_measure(gsis, torch, stream, wl, nsteps=None):
         e1.synchronize()
         return r, e0.elapsed_time(e1) * 1e-3
 
-    # the forward run the adjoint differentiates (and recomputes): steps started from the previous one
-    f, s_fwd = timed(lambda: wl.run(gsis, opt, nsteps=n, stream=stream, predictor=0))
+    # the forward run the adjoint differentiates (and recomputes from its checkpoints)
+    f, s_fwd = timed(lambda: wl.run(gsis, opt, nsteps=n, stream=stream))
     adj = lambda ws=None: gsis.td_adjoint(p.dx, p.dy, p.mu, p.eta, p.w, wl.sa, wl.ss, wl.q, wl.rho0, wl.T0,
                                           tp["dt"], n, dJ_drho=g, c=tp["c"], a=tp["a"], cv=tp["cv"],
-                                          inflow=wl.inflow, options=opt, workspace=ws, stream=stream)
+                                          inflow=wl.inflow, options=opt, workspace=ws, stream=stream,
+                                          predictor=TD_PREDICTOR)
     r, s_adj = timed(adj)
     gsis.profile_enable(True)
     r2, _ = timed(lambda: adj(r["workspace"]))

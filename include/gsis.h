@@ -263,7 +263,8 @@ typedef struct {
      * kept >= half the previous step's (rho >= 0, T > 0).  Only the starting
      * point changes: every step still iterates to Err < tol, so the result
      * is the same implicit solution within the tolerance, in fewer
-     * iterations on smooth transients.  gsis_td_adjoint takes 0 only. */
+     * iterations on smooth transients.  gsis_td_adjoint keeps the history with
+ * each checkpoint, so its recomputed steps repeat the forward run's. */
     int predictor;
 } gsis_time_params;
 

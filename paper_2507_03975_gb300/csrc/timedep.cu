@@ -403,14 +403,15 @@ __global__ void add_f_kernel(float* out, const float* __restrict__ a, const floa
 // Storage of the time-step adjoint after the solve layout: the transposed
 // solve of the carried intensities (chi) and the carry (phi), a zero source,
 // the FP32 transposed-sweep diagonal, six per-cell vectors, the checkpoints
-// (every C-th step's input state: In, cnext, rho, T) and the records of one
+// (every C-th step's input state: In, cnext, rho, T and the predictor's
+// history of the last two steps' rho and T) and the records of one
 // segment of C steps (each step's I^{m+1/2}, rho^{m+1/2}, rho, T).
 struct AdjStore {
     void* chi; void* carry; void* zero;
     float* sigt_shift_f;
     double* sig_eff; double* c0; double* rb_extra; double* ybar_rho; double* ybar_T; double* sphi;
     std::vector<void*> ck_I, rec_I;
-    std::vector<double*> ck_v, rec_v;   // 3 N doubles each
+    std::vector<double*> ck_v, rec_v;   // 7 N (checkpoint) and 3 N (record) doubles each
 };
 
 size_t adj_store(const Sizes& z, int nck, int seg, char* base, AdjStore* A)
@@ -435,7 +436,7 @@ size_t adj_store(const Sizes& z, int nck, int seg, char* base, AdjStore* A)
     a.ck_v.assign(nck, nullptr);
     for (int i = 0; i < nck; ++i) {
         a.ck_I[i] = take(K * N * Ts);
-        a.ck_v[i] = reinterpret_cast<double*>(take(3 * N * sizeof(double)));
+        a.ck_v[i] = reinterpret_cast<double*>(take(7 * N * sizeof(double)));
     }
     a.rec_I.assign(seg, nullptr);
     a.rec_v.assign(seg, nullptr);
@@ -460,8 +461,6 @@ int check_td_adjoint(const gsis_mesh* mesh, const gsis_quadrature* quad, const g
     if ((rc = check_mesh(mesh)) || (rc = check_quad(quad)) || (rc = check_opt(opt)) || (rc = check_tp(tp, opt)))
         return rc;
     if (opt->scheme != GSIS_SCHEME_GSIS) return fail(GSIS_ERR_ARG, "the adjoint is that of the GSIS time steps");
-    if (tp->predictor != 0)
-        return fail(GSIS_ERR_ARG, "the adjoint's recomputed steps start from the previous step: predictor 0");
     if (checkpoint_every < 1) return fail(GSIS_ERR_ARG, "checkpoint_every must be >= 1");
     if (!uniform_spacing(mesh->dx, mesh->nx) || !uniform_spacing(mesh->dy, mesh->ny))
         return fail(GSIS_ERR_ARG, "the adjoint needs a uniform mesh (transposed sweep = reflected sweep)");
@@ -599,8 +598,14 @@ int gsis_td_adjoint(const gsis_mesh* mesh, const gsis_quadrature* quad, const gs
         CK(cudaMemcpyAsync(v, P.td.cnext, Nd, cudaMemcpyDeviceToDevice, st));
         CK(cudaMemcpyAsync(v + N, P.rho_m, Nd, cudaMemcpyDeviceToDevice, st));
         CK(cudaMemcpyAsync(v + 2 * N, P.td.T, Nd, cudaMemcpyDeviceToDevice, st));
+        if (tp->predictor > 0) {   // the history the next step extrapolates from
+            double* const h[] = {P.td.hr1, P.td.hr2, P.td.ht1, P.td.ht2};
+            for (int k = 0; k < 4; ++k)
+                CK(cudaMemcpyAsync(v + (3 + k) * N, h[k], Nd, cudaMemcpyDeviceToDevice, st));
+        }
         return GSIS_OK;
     };
+    auto step_pred = [&](int n) { return tp->predictor > 0 ? std::min(tp->predictor, n) : -1; };
     for (int n = 0; n < nsteps; ++n) {
         if (n > 0) std::swap(P.I, P.In);
         if (n % C == 0) {
@@ -608,7 +613,7 @@ int gsis_td_adjoint(const gsis_mesh* mesh, const gsis_quadrature* quad, const gs
             if ((rc = save_state(A.ck_v[n / C]))) return rc;
         }
         bool stalled = false;   // a stalled step ends at its floor, as in gsis_td_solve
-        if ((rc = run_step(P, tp, opt, 1, S, st, &stalled))) return rc;
+        if ((rc = run_step(P, tp, opt, 1, S, st, &stalled, step_pred(n)))) return rc;
         if (!stalled && (rc = step_result(S, n))) return rc;
     }
     if (rho) CK(cudaMemcpyAsync(rho, P.rho_m, Nd, cudaMemcpyDeviceToDevice, st));
@@ -642,11 +647,16 @@ int gsis_td_adjoint(const gsis_mesh* mesh, const gsis_quadrature* quad, const gs
         CK(cudaMemcpyAsync(P.td.cnext, A.ck_v[sg], Nd, cudaMemcpyDeviceToDevice, st));
         CK(cudaMemcpyAsync(P.rho_m, A.ck_v[sg] + N, Nd, cudaMemcpyDeviceToDevice, st));
         CK(cudaMemcpyAsync(P.td.T, A.ck_v[sg] + 2 * N, Nd, cudaMemcpyDeviceToDevice, st));
+        if (tp->predictor > 0) {
+            double* const h[] = {P.td.hr1, P.td.hr2, P.td.ht1, P.td.ht2};
+            for (int k = 0; k < 4; ++k)
+                CK(cudaMemcpyAsync(h[k], A.ck_v[sg] + (3 + k) * N, Nd, cudaMemcpyDeviceToDevice, st));
+        }
         for (int r = 0; r < n1 - n0; ++r) {
             P.In = r == 0 ? A.ck_I[sg] : A.rec_I[r - 1];
             P.I = A.rec_I[r];
             bool stalled = false;
-            if ((rc = run_step(P, tp, opt, 1, S, st, &stalled))) return rc;
+            if ((rc = run_step(P, tp, opt, 1, S, st, &stalled, step_pred(n0 + r)))) return rc;
             if (!stalled && (rc = step_result(S, n0 + r))) return rc;
             double* rv = A.rec_v[r];
             CK(cudaMemcpyAsync(rv, P.rho_h, Nd, cudaMemcpyDeviceToDevice, st));

@@ -586,7 +586,7 @@ def td_adjoint_workspace_bytes(dx, dy, mu, eta, w, dt, nsteps, checkpoint_every,
 
 def td_adjoint(dx, dy, mu, eta, w, sigma_a, sigma_s, q, rho0, T0, dt, nsteps, dJ_drho=None, dJ_dT=None,
                checkpoint_every=None, c=1.0, a=1.0, cv=1.0, inflow=None, options: Options | None = None,
-               workspace=None, stream=None):
+               workspace=None, stream=None, predictor=0):
     """gsis_td_adjoint: gradient of dJ_drho . rho^N + dJ_dT . T^N after a
     time-dependent GSIS run with respect to sigma_a, sigma_s, rho^0, T^0.
     checkpoint_every defaults to ceil(sqrt(nsteps)).  Returns dict(grad_sigma_a,
@@ -603,7 +603,7 @@ def td_adjoint(dx, dy, mu, eta, w, sigma_a, sigma_s, q, rho0, T0, dt, nsteps, dJ
     out = {k: torch.empty(N, dtype=torch.float64, device=dev)
            for k in ("rho", "T", "grad_sigma_a", "grad_sigma_s", "grad_rho0", "grad_T0")}
     its = (ctypes.c_int * nsteps)()
-    tp = TimeParams(dt, c, a, cv, nsteps)
+    tp = TimeParams(dt, c, a, cv, nsteps, predictor)
     workspace = _workspace(td_adjoint_workspace_bytes(ar.dx, ar.dy, ar.mu, ar.eta, ar.w, dt, nsteps,
                                                       checkpoint_every, c, a, cv, o), workspace, dev)
     rc = _td_adj_load().gsis_td_adjoint(

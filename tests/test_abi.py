@@ -132,9 +132,12 @@ def test_td_adjoint_checks_and_storage(gs):
     with pytest.raises(gs.GsisError):
         nb(4, 0)
     KN8 = len(w) * 16 * 16 * 8
-    # one more checkpoint or one more segment step costs one intensity array (plus per-cell vectors)
+    # one more checkpoint or one more segment step costs one intensity array plus per-cell
+    # vectors: 7 in a checkpoint (state and the predictor's history), 3 in a step record
+    N8 = 16 * 16 * 8
     assert KN8 <= nb(9, 3) - nb(6, 3) < 2 * KN8          # 3 -> 2 checkpoints
-    assert KN8 <= nb(12, 6) - nb(12, 4) < 2 * KN8        # 2 checkpoints + 6 steps vs 3 + 4: one array more
+    d = nb(12, 6) - nb(12, 4)                            # 2 checkpoints + 6 steps vs 3 + 4
+    assert KN8 + (2 * 3 - 7) * N8 <= d < KN8 + 2 * N8    # one array more, one checkpoint's vectors fewer
     assert nb(5, 5) == nb(5, 9)                           # the segment never exceeds the run
 
 
@@ -154,7 +157,11 @@ def test_td_adjoint_binding_rejects_before_device_use(gs):
     rc = lib.gsis_td_adjoint(ctypes.byref(a.mesh), ctypes.byref(a.quad), ctypes.byref(gs.default_options()),
                              ctypes.byref(tp), 2, *([dummy] * 14), its, None, ctypes.c_size_t(0), None)
     assert rc == gs.GSIS_ERR_WORKSPACE
-    tp.predictor = 2   # the adjoint recomputes steps from the previous step only
+    tp.predictor = 2   # accepted: the checkpoints carry the predictor's history
+    rc = lib.gsis_td_adjoint(ctypes.byref(a.mesh), ctypes.byref(a.quad), ctypes.byref(gs.default_options()),
+                             ctypes.byref(tp), 2, *([dummy] * 14), its, None, ctypes.c_size_t(0), None)
+    assert rc == gs.GSIS_ERR_WORKSPACE
+    tp.predictor = 3
     rc = lib.gsis_td_adjoint(ctypes.byref(a.mesh), ctypes.byref(a.quad), ctypes.byref(gs.default_options()),
                              ctypes.byref(tp), 2, *([dummy] * 14), its, None, ctypes.c_size_t(0), None)
     assert rc == gs.GSIS_ERR_ARG and "predictor" in gs.last_error()

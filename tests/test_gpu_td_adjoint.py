@@ -71,10 +71,11 @@ def _opts(gs, prec, tol):
                               check_every=4, max_iter=400)
 
 
-def _gpu(gs, p, tp, nsteps, rho0, T0, g_rho, g_T, opt, C=None):
+def _gpu(gs, p, tp, nsteps, rho0, T0, g_rho, g_T, opt, C=None, predictor=0):
     return gs.td_adjoint(p.dx, p.dy, p.mu, p.eta, p.w, _t(p.sigma_a), _t(p.sigma_s), _t(p.q), _t(rho0), _t(T0),
                          tp.dt, nsteps, dJ_drho=_t(g_rho), dJ_dT=_t(g_T), checkpoint_every=C, c=tp.c, a=tp.a,
-                         cv=tp.cv, inflow=None if p.inflow is None else _t(p.inflow.reshape(-1)), options=opt)
+                         cv=tp.cv, inflow=None if p.inflow is None else _t(p.inflow.reshape(-1)), options=opt,
+                         predictor=predictor)
 
 
 @pytest.fixture(scope="module")
@@ -127,6 +128,29 @@ def test_checkpoint_interval_does_not_change_the_gradient(gs):
         for k in ("grad_sigma_a", "grad_sigma_s", "grad_rho0", "grad_T0", "rho", "T"):
             assert np.array_equal(r[k].cpu().numpy(), runs[0][k].cpu().numpy()), k
         assert np.array_equal(r["adj_iters"], runs[0]["adj_iters"])
+
+
+def test_predictor_run_gradient_matches_oracle_for_every_checkpoint_interval(gs, oracle_results):
+    """The adjoint of a run whose steps start from the quadratic predictor:
+    the checkpoints carry the predictor's history, so the recomputed steps
+    repeat the forward run bit for bit whatever the interval, and the
+    converged steps (hence the gradient) equal the oracle's, whose steps
+    start from the previous one."""
+    name, make, tp, nsteps = CASES[0]
+    p = make()
+    rho0, T0, g_rho, g_T = _state(p, 7)
+    o = oracle_results[name]
+    opt = _opts(gs, "fp64", 1e-13)
+    runs = [_gpu(gs, p, tp, nsteps, rho0, T0, g_rho, g_T, opt, C=C, predictor=2) for C in (1, 2, nsteps)]
+    r = runs[0]
+    assert r["status"] == gs.GSIS_OK
+    assert _rel(r["rho"].cpu().numpy(), o["recs"][-1]["rho"]) < 1e-9
+    for k, key in (("grad_sa", "grad_sigma_a"), ("grad_ss", "grad_sigma_s"), ("grad_rho0", "grad_rho0"),
+                   ("grad_T0", "grad_T0")):
+        assert _rel(r[key].cpu().numpy(), o[k]) < TOL64, k
+    for q in runs[1:]:
+        for k in ("grad_sigma_a", "grad_sigma_s", "grad_rho0", "grad_T0", "rho", "T"):
+            assert np.array_equal(q[k].cpu().numpy(), r[k].cpu().numpy()), k
 
 
 def test_full_size_directional_derivative(gs):
