@@ -842,6 +842,13 @@ __device__ __forceinline__ void mg_cp_async4(void* smem, const void* gmem)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(smem)), "l"(gmem) : "memory");
 }
 
+// 16 bytes, L2 only (data other CTAs wrote earlier in the kernel); both
+// addresses 16-byte aligned.
+__device__ __forceinline__ void mg_cp_async16_cg(void* smem, const void* gmem)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem)), "l"(gmem) : "memory");
+}
+
 // Cells k = tid, tid + nt, ... of a w-wide row-major block, as (i, j): one
 // division per thread, then steps with a carry.
 struct CellWalk {
@@ -1320,8 +1327,39 @@ __global__ void __launch_bounds__(kTileBlock) mg_tile_grid_kernel(const TileArgs
             const MgLevelDev& F = a.lv[lf - 1];
             const LocalView Lc(S[lf]);
             const int n = Lc.nx * Lc.ny;
+            // stage level lf-1's residual through the coarse level's x and t
+            // (free until its V-cycle) in chunks of whole fine-row pairs: one
+            // L2 round trip per chunk instead of one per two coarse cells
+            const int stage = S[lf].x;                  // float offset; x and t are adjacent
+            const int prows = (2 * n / F.nx) & ~1;      // fine rows per chunk
+            const bool staged = F.nx % 4 == 0 && stage % 4 == 0 && prows >= 2 &&
+                                (reinterpret_cast<size_t>(F.t) & 15) == 0;
+            if (staged) {
+                extern __shared__ __align__(16) float mg_smem_stage[];
+                float* const buf = mg_smem_stage + stage;
+                const int q4 = F.nx / 4;                // 16-byte pieces per fine row
+                for (int r0 = 0; r0 < F.ny; r0 += prows) {
+                    const int nr = min(prows, F.ny - r0);
+                    for (int k = tid; k < nr * q4; k += nt)
+                        mg_cp_async16_cg(buf + 4 * k, F.t + (size_t)r0 * F.nx + 4 * k);
+                    asm volatile("cp.async.wait_all;" ::: "memory");
+                    __syncthreads();
+                    const int J0 = r0 >> 1, J1 = min(Lc.ny, (r0 + nr + 1) >> 1);
+                    for (int k = tid; k < (J1 - J0) * Lc.nx; k += nt) {
+                        const int J = J0 + k / Lc.nx, I = k - (J - J0) * Lc.nx;
+                        float sum = 0.f;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int gi = 2 * I + (q & 1), gj = 2 * J + (q >> 1);
+                            if (gi < F.nx && gj < F.ny) sum += buf[(gj - r0) * F.nx + gi];
+                        }
+                        Lc.r[J * Lc.nx + I] = sum;
+                    }
+                    __syncthreads();
+                }
+            }
             constexpr int kU = 2;   // coarse cells per thread whose 8 loads are in flight together
-            for (int c0 = 0; c0 < n; c0 += kU * nt) {
+            for (int c0 = 0; !staged && c0 < n; c0 += kU * nt) {
                 float v[kU][4];
 #pragma unroll
                 for (int u = 0; u < kU; ++u) {
