@@ -52,7 +52,7 @@ TOL = 1e-8
 BETA = 10.0        # local pseudo-time control (Sec. 4.3) the steady 2000/0.2 opacity jump needs
 SYNTH_CAP = 2      # inner iterations of the synthetic solve per GSIS iteration, steady channel (Sec. 4.2)
 TD_SYNTH_CAP = 6   # the cap on the time-dependent workload, with the quadratic predictor (measured: 4 -> 776, 5 -> 598, 6 -> 560, 7 -> 549, 8 -> 547 GSIS iterations; 1.84, 1.78, 1.79, 1.84 s at 5-8)
-TD_CHECK_EVERY = 4
+TD_CHECK_EVERY = 5   # status read every 5 iterations (measured, 100-step run: 3 -> 1.752, 4 -> 1.760, 5 -> 1.749, 6 -> 1.753, 8 -> 1.760 s)
 # first iterate of every time step: quadratic extrapolation in time of the last
 # three steps' (rho, T) (gsis_time_params::predictor; 0 would start from the
 # previous step, as the paper's loop does)
