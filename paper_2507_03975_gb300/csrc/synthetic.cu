@@ -93,6 +93,7 @@ struct RhsArgs {
     double* partials;   // [2][gridDim]
     double* norms;      // out: [0] = r0.r0, [1] = b.b
     Status* status;
+    int resid;          // 0: b only (the planned synthetic solver forms its own first residual)
 };
 
 // b, then r0 = b - D guess (five-point D) and the fixed-order sums r0.r0, b.b
@@ -135,6 +136,7 @@ __device__ __forceinline__ void rhs_body(const RhsArgs& a, int bid, int nblk)
         if (j == 0) v -= fma(hx, fb[2 * ny + i], -(bf[2 * ny + i] * rh));
         if (j == ny - 1) v -= fma(hx, fb[2 * ny + nx + i], -(bf[2 * ny + nx + i] * rh));
         a.b[c] = v;
+        if (!a.resid) continue;
         const double* g = a.guess;
         double dg = a.diag[c] * g[c];
         if (i + 1 < nx) dg = fma(-a.cx[c], g[c + 1], dg);
@@ -146,6 +148,7 @@ __device__ __forceinline__ void rhs_body(const RhsArgs& a, int bid, int nblk)
         lrr = fma(rv, rv, lrr);
         lbb = fma(v, v, lbb);
     }
+    if (!a.resid) return;   // uniform over the launch
     lrr = block_sum(lrr, sm);
     lbb = block_sum(lbb, sm);
     if (threadIdx.x == 0) {
@@ -278,6 +281,9 @@ RhsArgs rhs_args(const Plan& P, const double* rho_h, const double* fb, const dou
     a.partials = P.partials;
     a.norms = P.partials + (size_t)4 * kMaxCgBlocks;
     a.status = P.status;
+    // only the cluster solver reads r0 and the norms; the tiled grid solver
+    // (planned: P.synth_tiled) forms its first residual itself
+    a.resid = P.synth_grid > 0 && P.synth_tiled ? 0 : 1;
     return a;
 }
 
