@@ -803,8 +803,11 @@ __global__ void __launch_bounds__(kMgBlock) mg_solve_grid_kernel(const MgArgs a)
 //    0..local_from-1): the level-0 rectangles of a px x py block grid, with
 //    boundaries at multiples of 2^(local_from-1), divided by 2^l on level l,
 //    so a rectangle's 2x2 restriction is the next level's rectangle.  CTA 0
-//    owns no rectangle; it runs the levels from local_from down in its
-//    shared memory.
+//    owns no rectangle; it runs the levels from local_from down to the
+//    first level of at most kDirectMax cells in its shared memory and
+//    solves that level with its inverse (`mg_direct_inverse_kernel`).
+//  * Barrier: one word whose top bit flips per completed barrier (see
+//    GridCtx); reductions read their per-CTA table eight slots per lane.
 //  * Down phase of level l, per sub-tile of the rectangle (one sub-tile on
 //    the workloads' meshes): the sub-tile and a two-cell halo of r and of the
 //    level's coefficients go to shared memory, x1 = omega r / d and x2 = one
