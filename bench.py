@@ -168,9 +168,9 @@ def _clock_summary(proc, f, uuid, index):
 # workspace layout) are the captured ones.
 SWEEP_SOURCES = ("sweep.cu", "gsis_internal.cuh", "host.h", "api.cu", "timedep.cu", "batch.cu")
 SWEEP_TRAFFIC = {   # {workload: (sources digest, bytes per launch)}
-    "timedep_fp64": ("510dc50c31724c93", 3_812_449_920),   # profiles/sweep_kernel_wide_td1024_fp64.md
-    "channel": ("510dc50c31724c93", 106_336_000),          # profiles/sweep_kernel_channel256.md
-    "batch": ("510dc50c31724c93", 932_011_776),            # profiles/sweep_kernel_batch64.md
+    "timedep_fp64": ("a03f3ba1fdf55726", 3_812_679_040),   # profiles/sweep_kernel_wide_td1024_fp64.md
+    "channel": ("a03f3ba1fdf55726", 106_284_800),          # profiles/sweep_kernel_channel256.md
+    "batch": ("a03f3ba1fdf55726", 932_232_448),            # profiles/sweep_kernel_batch64.md
 }
 
 

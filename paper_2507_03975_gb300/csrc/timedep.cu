@@ -122,13 +122,18 @@ __global__ void td_begin_kernel(TdArgs a)
         a.T_n[c] = t;
         a.cn[c] = a.cnext[c];
         a.cnext[c] = 0.0;
-        if (a.hr1) {   // first iterate extrapolated from the last steps' results
+        if (a.hr1 && a.pred == 0) {   // the history's first entry (step 0)
+            a.hr1[c] = r;
+            a.hr2[c] = r;
+            a.ht1[c] = t;
+            a.ht2[c] = t;
+        } else if (a.hr1) {   // first iterate extrapolated from the last steps' results
             const double r1 = a.hr1[c], t1 = a.ht1[c];
-            double rp = r, tq = t;
+            double rp, tq;
             if (a.pred == 1) {
                 rp = r + (r - r1);
                 tq = t + (t - t1);
-            } else if (a.pred == 2) {
+            } else {
                 rp = fma(3.0, r - r1, a.hr2[c]);
                 tq = fma(3.0, t - t1, a.ht2[c]);
             }
@@ -221,11 +226,16 @@ __global__ void td_end_si_kernel(TdArgs a)
     }
 }
 
-cudaError_t launch_td_coef_hot_rhs(const Plan& P, const TdArgs& a, int g, cudaStream_t st)
+// coef = false: the coefficients already hold this T^m (the step's first
+// iteration, right after the step operator formed them at the same T^m)
+cudaError_t launch_td_coef_hot_rhs(const Plan& P, const TdArgs& a, int g, cudaStream_t st, bool coef)
 {
-    td_coef_kernel<<<g, kRedBlock, 0, st>>>(a);
-    const cudaError_t e = cudaGetLastError();
-    return e != cudaSuccess ? e : launch_hot_rhs(P, P.rho_h, P.Fx, P.Fy, P.fb, P.rho_m, st);
+    if (coef) {
+        td_coef_kernel<<<g, kRedBlock, 0, st>>>(a);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return launch_hot_rhs(P, P.rho_h, P.Fx, P.Fy, P.fb, P.rho_m, st);
 }
 
 cudaError_t launch_td_update(const Plan& P, const TdArgs& a, cudaStream_t st)
@@ -340,7 +350,8 @@ int run_step(Plan& P, const gsis_time_params* tp, const gsis_options* opt, int g
             TIMED(GSIS_KCLASS_MOMENTS, P.order == 2 ? 2 : 1,
                   launch_moments_to(P, gsis, false, P.rho_h, nullptr, nullptr, false, P.fb, false, st));
             if (gsis) {
-                TIMED(GSIS_KCLASS_HOT_RHS, 3, launch_td_coef_hot_rhs(P, a, g, st));
+                const bool coef = launched + b > 0;
+                TIMED(GSIS_KCLASS_HOT_RHS, coef ? 3 : 2, launch_td_coef_hot_rhs(P, a, g, st, coef));
                 TIMED(GSIS_KCLASS_SYNTH, 1, launch_synthetic_solve(P, P.rho_m, P.x, st));
             }
             TIMED(GSIS_KCLASS_UPDATE, 1, launch_td_update(P, a, st));
