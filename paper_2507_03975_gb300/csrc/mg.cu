@@ -2010,7 +2010,7 @@ __device__ __forceinline__ void strip_body(const SArgs& a)
             cx.sum2<double>(lrr, 0.0, v2, slots_d, rotd, wsm_d);
             rr = v2[0];
         }
-        // stop test in one thread (FP64 is slow here; every thread reads the verdict)
+        // stop test in one thread (FP64 is slow here; every thread reads the decision)
         if (threadIdx.x == 0) {
             relres = bb > 0.0 ? sqrt(rr / bb) : 0.0;
             stop_now = (rr <= a.rtol * a.rtol * bb || total >= a.max_iter) ? 1 : 0;
