@@ -115,12 +115,13 @@ def test_fixed_inner_iterations_match_oracle(gs):
     assert rel(r["T"].cpu().numpy(), T) < 1e-10
 
 
-def test_fp32_sweeps_match_oracle(gs):
+@pytest.mark.parametrize("predictor", [0, 2])
+def test_fp32_sweeps_match_oracle(gs, predictor):
     p, rho0, T0 = _case(4, 40, 30, 6)
     tp = TD.TimeParams(dt=0.05)
     o = TD.run(p, tp, 3, rho0, T0, scheme="gsis", tol=1e-12)
-    r = _solve(gs, p, tp, 3, rho0, T0, precision=gs.FP32_SWEEP, tol=1e-6, max_iter=500, synth_rtol=1e-13,
-               synth_max_iter=3000)
+    r = _solve(gs, p, tp, 3, rho0, T0, predictor=predictor, precision=gs.FP32_SWEEP, tol=1e-6, max_iter=500,
+               synth_rtol=1e-13, synth_max_iter=3000)
     assert r["status"] == gs.GSIS_OK
     assert rel(r["rho"].cpu().numpy(), o["rho"]) < 1e-5
     assert rel(r["T"].cpu().numpy(), o["T"]) < 1e-5
